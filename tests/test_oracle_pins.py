@@ -1,0 +1,324 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test states the passage or the closed form it checks.  None of them
+calls the CUDA library.
+"""
+import numpy as np
+import pytest
+from scipy import special
+from scipy.integrate import quad_vec, quad
+from scipy.interpolate import CubicSpline
+
+from paper_2505_20968_gb300 import inputs
+from oracle.faddeeva import wofz, voigt_faraday
+from oracle.spline import NaturalSpline
+from oracle.geometry import angular_grid, theta_classes
+from oracle import redistribution as RD
+from oracle.problem import Problem, delo_coeffs, gmres
+from oracle.constants import MU_B_OVER_H, GAUSS
+from oracle.atom import states
+
+
+# ---------------------------------------------------------------- Faddeeva
+def test_faddeeva_closed_forms():
+    y = np.geomspace(1e-4, 30, 200)
+    np.testing.assert_allclose(wofz(1j * y), special.erfcx(y), rtol=2e-14)
+    x = np.linspace(-6, 6, 241)
+    np.testing.assert_allclose(wofz(x).real, np.exp(-x * x), atol=2e-15)
+    np.testing.assert_allclose(wofz(x).imag, 2 / np.sqrt(np.pi) * special.dawsn(x), atol=2e-15)
+    z = 300.0 * np.exp(1j * np.linspace(0.01, np.pi - 0.01, 50))
+    np.testing.assert_allclose(wofz(z), 1j / (np.sqrt(np.pi) * z) * (1 + 0.5 / z ** 2 + 0.75 / z ** 4),
+                               rtol=1e-10)
+
+
+def test_faddeeva_vs_scipy():
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-60, 60, 20000)
+    y = 10 ** rng.uniform(-6, 1.5, 20000)
+    z = x + 1j * y
+    ref = special.wofz(z)
+    assert np.max(np.abs(wofz(z) - ref) / np.abs(ref)) < 1e-13
+
+
+# ---------------------------------------------------------------- spline
+def test_spline_natural_vs_scipy_and_linear_exactness():
+    rng = np.random.default_rng(1)
+    u = np.sort(rng.uniform(-5, 5, 17))
+    y = rng.normal(size=17)
+    s = NaturalSpline(u)
+    xs = np.linspace(u[0], u[-1], 400)
+    np.testing.assert_allclose(s(y, xs), CubicSpline(u, y, bc_type="natural")(xs), atol=1e-12)
+    np.testing.assert_allclose(s(2.0 - 0.3 * u, xs), 2.0 - 0.3 * xs, atol=1e-12)
+    # constant extension outside the grid
+    assert s(y, np.array([u[0] - 3.0]))[0] == y[0] and s(y, np.array([u[-1] + 1.0]))[0] == y[-1]
+
+
+# ---------------------------------------------------------------- angles
+def test_number_of_scattering_angles_paper_grid():
+    """Sect. 6.2: 2 x 6 GL mu x 9 chi gives N_Theta = 205 (with Theta = 0)."""
+    mu, chi, w = angular_grid(6, 9)
+    th, _ = theta_classes(mu, chi)
+    assert th.size == 205
+    assert abs(w.sum() - 1.0) < 1e-14
+    assert 4 * 70 * 210 * mu.size == 6350400     # "N ~ 6e6" (Sect. 6.2)
+
+
+# ---------------------------------------------------------------- F kernel
+@pytest.mark.parametrize("theta", [0.1, 0.7, 1.6, 2.6, 0.9 * np.pi, np.pi - 1e-3, np.pi])
+@pytest.mark.parametrize("a", [1e-2, 1e-4])
+def test_F_marginal_is_complex_voigt(theta, a):
+    """int F(Theta, x', x) dx' = sqrt(pi) W(a, x) for every Theta: the complex
+    form of Hummer's R_II-A marginal (R_II-A = Re F / pi, Sect. 2.3)."""
+    for x in (0.0, 0.8, -2.5, 4.0):
+        g = 2 * np.sin(theta / 2)
+        pts = sorted([x, -x])
+        val, _ = quad_vec(lambda xp: np.array([RD.F_kernel(theta, xp, x, a).real,
+                                               RD.F_kernel(theta, xp, x, a).imag]),
+                          x - 7 * g, x + 7 * g, points=[p for p in pts if abs(p - x) < 7 * g],
+                          epsabs=1e-13, epsrel=1e-12, limit=5000)
+        ref = np.sqrt(np.pi) * voigt_faraday(a, x)
+        assert abs(val[0] + 1j * val[1] - ref) < 2e-9 * max(1.0, abs(ref))
+
+
+def test_F_symmetry_and_pi_limit():
+    xp = np.linspace(-3, 3, 13)
+    for theta in (0.3, 1.9, 3.0):
+        np.testing.assert_allclose(RD.F_kernel(theta, xp, 0.7, 1e-3), RD.F_kernel(theta, 0.7, xp, 1e-3),
+                                   rtol=1e-13)
+    # Theta -> pi approaches the exact limit kernel
+    f_lim = RD.F_kernel(np.pi, xp, 0.4, 1e-2)
+    f_near = RD.F_kernel(np.pi - 1e-6, xp, 0.4, 1e-2)
+    np.testing.assert_allclose(f_near, f_lim, rtol=2e-5)
+
+
+def test_small_theta_tile_tends_to_delta_form():
+    """App. C rule i: F(0,u,u') = sqrt(pi) delta(u-u') W(a,u')."""
+    t = -1.0 + np.arange(21) / 10.0
+    u = 8.0 * np.sinh(3 * t) / np.sinh(3)
+    s = NaturalSpline(u)
+    T0 = RD.tile(s, 0.0, 1e-3, 0.01, -0.02)
+    Ts = RD.tile(s, 2e-4, 1e-3, 0.01, -0.02)
+    assert np.max(np.abs(Ts - T0)) < 1e-3 * np.max(np.abs(T0))
+
+
+def test_composite_quadrature_vs_adaptive_gk_fig1():
+    """Fig. 1 setting (a = 0.01, Theta = 0.9 pi, u_{ku,kl} = -11.1,
+    u_{ku,kl'} = -11.2); the paper's grids reach 1e-8, the oracle's 1e-10."""
+    u = np.linspace(-25.0, 25.0, 61) + 11.15
+    s = NaturalSpline(u)
+    theta, a, s_in, s_out = 0.9 * np.pi, 0.01, -11.1, -11.2
+    for un in (u[5], 11.15 - 0.3, 11.2, u[40]):
+        row = RD.tile_row(s, theta, a, s_in, s_out, un)
+        x = un + s_out
+        g = 2 * np.sin(theta / 2)
+        L, R = x - s_in - 6.5 * g, x - s_in + 6.5 * g
+        pts = [p for p in list(u) + [-x - s_in] if L < p < R]
+
+        def f(up):
+            v = RD.F_kernel(theta, np.array([up + s_in]), x, a)[0] * s.basis(np.array([up]))[0]
+            return np.concatenate([v.real, v.imag])
+        ref, _ = quad_vec(f, L, R, points=sorted(pts), epsabs=1e-14, epsrel=1e-12, limit=20000)
+        ref = ref[:u.size] + 1j * ref[u.size:]
+        assert np.max(np.abs(row - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_r3_weights_vs_adaptive():
+    u = np.linspace(-12, 12, 31)
+    s = NaturalSpline(u)
+    r = RD.r3_in_weights(s, 3e-3, 0.3, -0.2)
+    for m in (0, 7, 15, 30):
+        e = np.zeros(u.size)
+        e[m] = 1.0
+        f = lambda x: (voigt_faraday(3e-3, x + 0.3) + np.conj(voigt_faraday(3e-3, x - 0.2))) * s(e, np.array([x]))[0]
+        re = quad(lambda x: f(x).real, u[0], u[-1], points=list(u[1:-1]) + [-0.3, 0.2], limit=2000,
+                  epsabs=1e-14)[0]
+        im = quad(lambda x: f(x).imag, u[0], u[-1], points=list(u[1:-1]) + [-0.3, 0.2], limit=2000,
+                  epsabs=1e-14)[0]
+        assert abs(r[m] - (re + 1j * im)) < 1e-11
+
+
+# ---------------------------------------------------------------- DELO
+def test_delo_constant_source_exact():
+    """DELO-linear reproduces I = S (1 - e^-tau) + I0 e^-tau for constant S."""
+    d = np.array([1e-6, 1e-4, 1e-3, 0.3, 2.0, 40.0])
+    e, al, be = delo_coeffs(d)
+    np.testing.assert_allclose(e + al + be, 1.0, atol=1e-15)
+    # linear source S = t: exact solution of dI/dt = -I + t over one step
+    I0 = 0.4
+    exact = I0 * np.exp(-d) + (d - 1.0) + np.exp(-d)   # S(t)=t from t=0 to d
+    np.testing.assert_allclose(e * I0 + al * 0.0 + be * d, exact, rtol=1e-12, atol=1e-18)
+
+
+# ---------------------------------------------------------------- atom / K
+def test_paschen_back_levels():
+    """Sect. 2.2: at B = 0 the two-term upper levels sit at the Table-1
+    energies; the dipole strengths sum to one per upper state."""
+    cfg = inputs.mgii(n_z=2)
+    Eu, D, El = states(cfg["atom"], 0.0)
+    E = np.array(cfg["atom"]["E_u_cm"]) * 2.99792458e10
+    nu0 = (2 * E[0] + 4 * E[1]) / 6
+    np.testing.assert_allclose(np.sort(Eu), np.sort([E[0] - nu0] * 2 + [E[1] - nu0] * 4), rtol=1e-12)
+    np.testing.assert_allclose((D ** 2).sum(axis=(0, 2)), 1.0, rtol=1e-12)
+    # weak field: Zeeman splitting with Lande factors 2/3 (P1/2) and 4/3 (P3/2)
+    Eu1, _, _ = states(cfg["atom"], 1.0)
+    nuL = MU_B_OVER_H * GAUSS
+    split = np.sort(Eu1 - np.sort(Eu))
+    assert abs(np.ptp(np.sort(Eu1)[:2]) - 2 * (2 / 3) * 0.5 * nuL) < 1e-3 * nuL
+
+
+def test_weak_field_stokes_V():
+    """V(lambda) = -dlambda_B g cos(theta_B) dI/dlambda (weak field, LL04 Ch. 9):
+    in reduced frequency eta_V = -(nu_L/dnu_D) g cos(theta_B) d eta_I/du."""
+    cfg = inputs.twolevel_slab(n_z=2, n_x=9)
+    cfg["atm"]["B_G"][:] = 10.0
+    P = Problem(cfg)
+    u = np.linspace(-4, 4, 801)
+    for mu in (0.8, -0.35):
+        K = P.K_from_kappa(P.kappa(0, P.amplitudes(0, mu, 0.3), 0.0, u))
+        pred = -(MU_B_OVER_H * GAUSS * 10.0 / P.dnuD[0]) * mu * np.gradient(K[:, 0, 0], u)
+        assert np.max(np.abs(K[:, 3, 0] - pred)) < 1e-3 * np.max(np.abs(pred))
+
+
+# ---------------------------------------------------------------- phase matrices
+def _integrated_phase(P, iz, amp_o, amp_i, subset=None, hanle=True):
+    """Frequency-integrated R^II: 3/(4(2S+1)) sum Tr(...) alpha/alpha_0 (Eq. RQIIKKp
+    with int int [G(k_u') + G(k_u)^*] du' du = 2 pi)."""
+    nu_ = P.nu_states
+    ks = range(nu_) if subset is None else subset
+    al = P.alpha[iz] / P.alpha[iz][0, 0].real
+    M = np.zeros((4, 4), dtype=complex)
+    for kl in range(P.nl_states):
+        for klp in range(P.nl_states):
+            for ku in ks:
+                for kv in ks:
+                    M += P._tr(amp_o, amp_i, ku, kv, kl, klp) * (al[ku, kv] if hanle else 1.0)
+    M *= 3.0 / (4.0 * P.S2)
+    assert np.max(np.abs(M.imag)) < 1e-12
+    return M.real
+
+
+def test_rayleigh_and_polarisabilities():
+    """Zero-field polarisability W2 (Sect. 2.2 atoms): 90-degree scattering of
+    unpolarised light gives Q/I = 3 W2 / (4 - W2): W2 = 1 for J 0->1 and for
+    the spinless-limit two-term atom, 1/2 for J_u = 3/2, 0 for J_u = 1/2."""
+    cfg = inputs.twolevel_slab(n_z=2, n_x=5)
+    P = Problem(cfg)
+    ao, ai = P.amplitudes(0, 0.0, 0.0), P.amplitudes(0, 1.0, 0.0)   # out: +x, in: +z
+    M = _integrated_phase(P, 0, ao, ai)
+    assert abs(M[1, 0] / M[0, 0] - 1.0) < 1e-12      # W2 = 1
+    # Theta-averaged I->I coefficient is 1 (normalisation of App. E)
+    mu, chi, w = angular_grid(4, 8)
+    tot = sum(wi * _integrated_phase(P, 0, ao, P.amplitudes(0, m, c))[0, 0] for m, c, wi in zip(mu, chi, w))
+    assert abs(tot - 1.0) < 1e-12
+    cfg2 = inputs.mgii(n_z=2, n_core_each=3, n_wing=6, n_mu_half=1, n_chi=2)
+    cfg2["atm"]["B_G"][:] = 0.0
+    P2 = Problem(cfg2)
+    ao, ai = P2.amplitudes(0, 0.0, 0.0), P2.amplitudes(0, 1.0, 0.0)
+    Eu, _, _ = states(cfg2["atom"], 0.0)
+    j12 = [k for k in range(6) if Eu[k] < 0]
+    j32 = [k for k in range(6) if Eu[k] > 0]
+    M32 = _integrated_phase(P2, 0, ao, ai, j32, hanle=False)
+    M12 = _integrated_phase(P2, 0, ao, ai, j12, hanle=False)
+    Mall = _integrated_phase(P2, 0, ao, ai, None, hanle=False)
+    assert abs(M32[1, 0] / M32[0, 0] - 3 * 0.5 / (4 - 0.5)) < 1e-12
+    assert abs(M12[1, 0] / M12[0, 0]) < 1e-12
+    assert abs(Mall[1, 0] / Mall[0, 0] - 1.0) < 1e-12   # spin as spectator
+
+
+def test_hanle_rotation_and_depolarisation():
+    """Hanle effect of the J 0->1 atom (Sect. 1), 90-degree scattering with B
+    along the line of sight: (Q + iU)/I = 1/(1 + 2 i H), H = 2 pi nu_L / Gamma,
+    i.e. |p| = 1/sqrt(1 + 4H^2), |U/Q| = 2H."""
+    cfg = inputs.twolevel_slab(n_z=2, n_x=5, a=1e-2)
+    cfg["atm"]["B_G"][:] = 3.0
+    cfg["atm"]["thetaB"][:] = np.pi / 2
+    cfg["atm"]["chiB"][:] = 0.0
+    P = Problem(cfg)
+    H = 2 * np.pi * MU_B_OVER_H * GAUSS * 3.0 / (4 * np.pi * P.dnuD[0] * P.a[0])
+    M = _integrated_phase(P, 0, P.amplitudes(0, 0.0, 0.0), P.amplitudes(0, 1.0, 0.0))
+    q, uu = M[1, 0] / M[0, 0], M[2, 0] / M[0, 0]
+    assert abs(np.hypot(q, uu) - 1 / np.sqrt(1 + 4 * H * H)) < 1e-12
+    assert abs(abs(uu / q) - 2 * H) < 1e-10
+
+
+# ---------------------------------------------------------------- operator-level pins
+def _static_twolevel(n_z=3, n_x=11, B=0.0, r_el=1e-9, eps=1e-3, n_mu_half=2, n_chi=4):
+    cfg = inputs.twolevel_slab(n_z=n_z, n_x=n_x, n_mu_half=n_mu_half, n_chi=n_chi, r_el=r_el, eps=eps)
+    cfg["atm"]["B_G"][:] = B
+    cfg["atm"]["thetaB"][:] = 0.7
+    cfg["atm"]["chiB"][:] = 1.1
+    return cfg
+
+
+def test_kirchhoff_normalisation_is_one_at_zero_field():
+    """App. E: at B = 0, v = 0 and with an angular rule exact for P_2, the
+    discrete Sigma applied to (W_T, 0, 0, 0) already gives (1-eps) W_T eta_I,
+    so f = 1 (R_III is switched off: its incident integral stops at the grid
+    edges)."""
+    P = Problem(_static_twolevel())
+    assert np.max(np.abs(P.f - 1.0)) < 1e-9
+
+
+def test_generalised_kirchhoff_all_stokes_magnetic():
+    """App. E (generalised Kirchhoff law, LL04 Sect. 9.1): for an isotropic
+    unpolarised W_T field eps_sc = (1-eps) W_T (eta_I, eta_Q, eta_U, eta_V), in
+    a magnetic field as well; this ties the scattering amplitudes of R to the
+    absorption matrix K.  Checked away from the two outermost frequencies."""
+    P = Problem(_static_twolevel(B=40.0, n_x=15))
+    for iz in range(P.nz):
+        Il = np.zeros((P.nO, P.nN, 4))
+        Il[..., 0] = P.WT[iz]
+        num = (P.sigma_matrix(iz, normalised=False) @ Il.ravel()).reshape(P.nO, P.nN, 4)
+        ref = (1 - P.eps[iz]) * P.WT[iz] * P.K[iz][..., :, 0]
+        sl = slice(2, -2)
+        assert np.max(np.abs(num[:, sl] - ref[:, sl])) < 1e-8 * np.max(np.abs(ref[..., 0]))
+
+
+def test_crd_limit():
+    """r_E -> 1 (alpha = 0): R = (1-eps) phi(u') phi(u) x Rayleigh (Sect. 2.3):
+    the I->I part of Sigma_bar is rank one in frequency."""
+    P = Problem(_static_twolevel(r_el=1 - 1e-12, n_x=9))
+    blk = P.block(1, 0, 5)[:, 0, :, 0]
+    sv = np.linalg.svd(blk, compute_uv=False)
+    assert sv[1] < 1e-9 * sv[0]
+
+
+def test_zero_field_1d_symmetries():
+    """Static, unmagnetised 1D slab: U = V = 0 and no chi dependence."""
+    cfg = inputs.twolevel_slab(n_z=8, n_x=9, n_mu_half=2, n_chi=4, eps=1e-2)
+    P = Problem(cfg)
+    x, _ = P.solve(tol=1e-12)
+    assert np.max(np.abs(x[..., 2:])) < 1e-12 * np.max(np.abs(x[..., 0]))
+    xi = x.reshape(P.nz, 4, 4, P.nN, 4)          # [z, mu, chi, n, s]
+    assert np.max(np.abs(xi - xi[:, :, :1])) < 1e-10 * np.max(np.abs(x))
+
+
+def test_gmres_matches_dense_solve():
+    """Brute force on a tiny grid: assemble A column by column, solve by LU."""
+    cfg = inputs.mgii(n_z=4, n_core_each=5, n_wing=6, n_mu_half=1, n_chi=2, seed=11)
+    P = Problem(cfg)
+    n = int(np.prod(P.shape()))
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = P.apply_A(e.reshape(P.shape())).ravel()
+    b = P.rhs().ravel()
+    xd = np.linalg.solve(A, b)
+    xg, hist = P.solve(tol=1e-13)
+    assert np.max(np.abs(xg.ravel() - xd)) < 1e-10 * np.max(np.abs(xd))
+
+
+@pytest.mark.slow
+def test_sqrt_eps_law():
+    """Isothermal CRD two-level atmosphere, constant eps: S(0) = sqrt(eps) B
+    (the sqrt(eps) law, exact for isotropic scattering in a semi-infinite
+    medium); 8 % allows for the Rayleigh phase matrix and the discretisation."""
+    eps = 1e-2
+    cfg = inputs.twolevel_slab(n_z=60, n_x=15, n_mu_half=2, n_chi=4, eps=eps, r_el=1 - 1e-12,
+                               tau_min=1e-5, tau_max=1e5)
+    P = Problem(cfg)
+    x, _ = P.solve(tol=1e-11)
+    S = (P.apply_sigma(x) + P.eps_th)[..., 0] / P.eta1
+    assert abs(S[-1, 0, P.nN // 2] / np.sqrt(eps) - 1.0) < 0.08
+    assert abs(S[0, 0, P.nN // 2] - 1.0) < 0.01          # thermalised at depth
