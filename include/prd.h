@@ -1,0 +1,164 @@
+/*
+ * prd.h -- C ABI of the GB300 (sm_103a) library for the matrix-free AD-PRD
+ * operator of polarised non-LTE radiative transfer with a fixed lower-level
+ * population (Riva et al., arXiv 2505.20968).
+ *
+ * The unknown is the discrete Stokes field I[z][Omega][nu][s] (s = I,Q,U,V;
+ * Sect. 2.6: N = 4 N_r N_nu N_Omega), heights ascending, directions ordered
+ * Omega = i_mu * N_chi + i_chi with mu ascending, frequencies ascending in the
+ * reduced frequency u = (nu0 - nu)/dnu_D.  The library solves
+ *     (Id - Lambda Sigma) I = Lambda eps_th + t                (Eq. linear_system)
+ * with Lambda the DELO-linear formal solution (Sect. 3) and Sigma the
+ * comoving-frame R_II-AD + R_III scattering operator (Eqs. eps_sc_l,
+ * RQIIKKp, RIIIQKKp, eps_sc_bar; Sect. 4; App. B, E).
+ *
+ * Conventions of every call:
+ *   - returns PRD_OK (0) or a negative PRD_E_* code; prd_last_error() gives a
+ *     one-line reason.  No C++ exception crosses this boundary.
+ *   - host arrays are read during the call and copied; the caller keeps them.
+ *   - "device" pointers are caller-owned CUDA allocations on the ctx's device,
+ *     contiguous, layout [z][Omega][nu][4], element type double for
+ *     PRD_FP64 and float for PRD_FP32.  The library never frees them.
+ *   - the library owns its workspace (cudaMalloc at prd_setup, freed at
+ *     prd_destroy or at the next prd_setup).
+ *   - work is issued on the ctx stream (prd_set_stream, default: the legacy
+ *     stream) and is asynchronous, except prd_setup, prd_solve and calls that
+ *     return host scalars, which synchronise the stream.
+ *   - a ctx is not thread-safe: use one ctx per host thread.
+ */
+#ifndef PRD_H
+#define PRD_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PRD_OK = 0,
+  PRD_E_ARG = -1,        /* invalid argument (null pointer, size, range)   */
+  PRD_E_STATE = -2,      /* call out of order (e.g. apply before setup)    */
+  PRD_E_CUDA = -3,       /* CUDA runtime error                              */
+  PRD_E_NOMEM = -4,      /* device allocation failed                        */
+  PRD_E_NOCONV = -5,     /* solver hit max_iter before tol                  */
+  PRD_E_BREAKDOWN = -6,  /* Arnoldi breakdown (h_{j+1,j} ~ 0)               */
+  PRD_E_NAN = -7,        /* NaN/Inf in a solver quantity                    */
+  PRD_E_TIMEOUT = -8     /* a bounded device wait expired                   */
+};
+
+enum { PRD_FP64 = 0, PRD_FP32 = 1 };
+enum { PRD_TWO_LEVEL = 0, PRD_TWO_TERM = 1 };
+enum { PRD_GRID_LAMBDA = 0, PRD_GRID_X = 1 };
+enum { PRD_MU_GL_HEMISPHERES = 0, PRD_MU_GL_FULL = 1 };
+enum { PRD_MODE_AD = 0, PRD_MODE_AA = 1 };
+
+typedef struct prd_ctx prd_ctx;
+
+/* Atomic model (Sect. 2.2, Table 1).  Lower term L=0 (unpolarised, sharp),
+ * upper term L=1 with spin S = twoS/2 (twoS = 0: two-level atom J 0->1;
+ * twoS = 1: S_1/2 -> P_1/2,3/2 two-term atom with J-state interference and
+ * Paschen-Back levels).  E_u_cm: upper J-level energies in cm^-1 (J = L-S
+ * first; for twoS = 0 only E_u_cm[0] is used).  nu0_hz = 0 selects the
+ * (2J+1)-weighted centroid as the reference frequency nu0 (Sect. 2.3). */
+typedef struct {
+  int kind;          /* PRD_TWO_LEVEL or PRD_TWO_TERM (must agree with twoS) */
+  int twoS;          /* 0 or 1 */
+  double E_u_cm[2];
+  double mass_amu;   /* atomic mass, Doppler width (Sect. 6.1) */
+  double g_s;        /* electron spin g factor (2.0) */
+  double nu0_hz;     /* 0 -> centroid */
+} prd_atom;
+
+/* Create a context on CUDA device `device` with arithmetic `precision`
+ * (PRD_FP64 or PRD_FP32).  *out receives the handle (NULL on failure). */
+int prd_create(prd_ctx** out, int device, int precision);
+/* Free the context and all library-owned device memory.  NULL is a no-op. */
+int prd_destroy(prd_ctx* ctx);
+/* Static one-line description of the last error on this ctx (never NULL). */
+const char* prd_last_error(const prd_ctx* ctx);
+/* Issue all further work on this cudaStream_t (passed as a pointer). */
+int prd_set_stream(prd_ctx* ctx, void* cuda_stream);
+
+/* Sect. 2.2 / Table 1. */
+int prd_set_atom(prd_ctx* ctx, const prd_atom* atom);
+
+/* Atmosphere on nz >= 2 heights (Sects. 2.3, 2.5, 6.1), each array of
+ * length nz except v_kms [nz][3]:
+ *   z_km ascending; T_K; xi_kms microturbulence; a damping constant
+ *   (Gamma_R+Gamma_I+Gamma_E)/(4 pi dnu_D); eps = Gamma_I/(Gamma_R+Gamma_I)
+ *   (photon destruction); r_el = Gamma_E/(Gamma_R+Gamma_I+Gamma_E) (< 1);
+ *   k_line: frequency-integrated line absorption coefficient of the fixed
+ *   lower population in km^-1 per unit reduced frequency (eta_I = k_line phi(u)
+ *   at B = 0); W_T Wien (Planck) function; B_G field strength in gauss,
+ *   thetaB/chiB its inclination/azimuth (rad, vertical z axis); v_kms bulk
+ *   velocity (x, y, z). */
+int prd_set_atmosphere(prd_ctx* ctx, int nz, const double* z_km, const double* T_K,
+                       const double* xi_kms, const double* a, const double* eps,
+                       const double* r_el, const double* k_line, const double* W_T,
+                       const double* B_G, const double* thetaB, const double* chiB,
+                       const double* v_kms);
+
+/* Frequency and angular quadrature (Sects. 2.5, 4.2).  grid: nnu ascending
+ * values, vacuum wavelengths in Angstrom (PRD_GRID_LAMBDA) or reduced
+ * frequencies x with nu = nu0 - x dnu_D(z_0) (PRD_GRID_X).  mu_rule
+ * PRD_MU_GL_HEMISPHERES puts n_mu_half Gauss-Legendre nodes on each of
+ * [-1,0] and [0,1]; PRD_MU_GL_FULL puts 2 n_mu_half nodes on [-1,1].  chi is
+ * the trapezoidal rule with n_chi nodes chi_k = 2 pi k/n_chi.  mode
+ * PRD_MODE_AD (angle-dependent R_II) or PRD_MODE_AA (Eq. R_AA). */
+int prd_set_quadrature(prd_ctx* ctx, int nnu, const double* grid, int grid_kind,
+                       int n_mu_half, int n_chi, int mu_rule, int mode);
+
+/* Build every table and the R_II tiles on the device (setup, Sect. 4; App. C,
+ * E, F): Doppler widths, Paschen-Back states, branching ratios (App. B),
+ * propagation matrices, DELO-linear weights, redistribution tiles against the
+ * natural-spline basis, Kirchhoff normalisation f (App. E), block-Jacobi
+ * inverses (App. F).  Synchronous.  Re-callable after set_* changes. */
+int prd_setup(prd_ctx* ctx);
+
+/* Problem sizes after setup: heights, directions, frequencies, scattering-
+ * angle classes (incl. Theta = 0) and the vector length n = 4 nz nO nnu. */
+int prd_sizes(const prd_ctx* ctx, int* nz, int* n_omega, int* nnu, int* n_theta,
+              int64_t* n);
+/* Copy the direction grid (mu, chi, weights; host arrays of length n_omega). */
+int prd_directions(const prd_ctx* ctx, double* mu, double* chi, double* w);
+/* Bytes of device memory the library holds after setup (tiles + tables). */
+int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes);
+
+/* b = Lambda eps_th + t  (right-hand side of Eq. linear_system). */
+int prd_rhs(prd_ctx* ctx, void* b_dev);
+/* eps = Sigma x: normalised line scattering emissivity (Eq. eps_sc_l in the
+ * comoving frame, Eq. eps_sc_bar; intensity scaled by f, App. E). */
+int prd_apply_sigma(prd_ctx* ctx, const void* x_dev, void* eps_dev);
+/* out = Lambda eps: DELO-linear formal solution, zero boundary (Sect. 3). */
+int prd_apply_lambda(prd_ctx* ctx, const void* eps_dev, void* out_dev);
+/* y = (Id - Lambda Sigma) x  (one operator apply, Eq. linear_system). */
+int prd_apply_operator(prd_ctx* ctx, const void* x_dev, void* y_dev);
+/* x = P^-1 y, P = Id - Lambda* Sigma* on Stokes I (identity on Q,U,V):
+ * Sigma* unpolarised, unmagnetised PRD-AA; m_in block-Jacobi-preconditioned
+ * Richardson sweeps from zero (Sect. 5.2, App. F). */
+int prd_apply_preconditioner(prd_ctx* ctx, const void* y_dev, void* x_dev);
+/* Set the number of inner sweeps m_in (>= 1, default 2) of the preconditioner. */
+int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
+
+/* Left-preconditioned restarted GMRES(restart) (Sect. 5.1-5.2) from x0_dev
+ * (NULL = zero) into x_dev; stops when the unpreconditioned relative residual
+ * ||b - A x||/||b|| < tol (checked in FP64).  *iters receives the number of
+ * operator applies, *true_rel_res the final FP64 residual; res_history (NULL
+ * or max_iter+1 doubles) the preconditioned residual estimate per iteration.
+ * Returns PRD_E_NOCONV if max_iter is reached, PRD_E_BREAKDOWN /
+ * PRD_E_NAN on those events (x_dev then holds the last iterate). */
+int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x0_dev,
+              void* x_dev, int* iters, double* true_rel_res, double* res_history);
+
+/* Emergent Stokes vectors at z_max along nlos lines of sight (mu > 0, any
+ * chi) that need not be on the grid (Sect. 6.2, extra formal solution):
+ * a scattering emissivity is built for each new direction from the solution
+ * x_dev, then one DELO sweep.  out_dev: [nlos][nnu][4] device array. */
+int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu,
+                        const double* chi, void* out_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRD_H */

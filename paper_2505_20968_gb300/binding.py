@@ -1,0 +1,204 @@
+"""Thin Python binding of libprd.so (include/prd.h): argument marshalling only.
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+operator runs in the library's CUDA kernels.  There is no CPU fallback: if the
+shared library is missing or cannot be loaded this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libprd.so")
+
+PRD_OK = 0
+ERRORS = {-1: "PRD_E_ARG", -2: "PRD_E_STATE", -3: "PRD_E_CUDA", -4: "PRD_E_NOMEM", -5: "PRD_E_NOCONV",
+          -6: "PRD_E_BREAKDOWN", -7: "PRD_E_NAN", -8: "PRD_E_TIMEOUT"}
+PRD_FP64, PRD_FP32 = 0, 1
+
+
+class PrdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Atom(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("twoS", ctypes.c_int), ("E_u_cm", ctypes.c_double * 2),
+                ("mass_amu", ctypes.c_double), ("g_s", ctypes.c_double), ("nu0_hz", ctypes.c_double)]
+
+
+_lib = None
+EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd_set_atom",
+           "prd_set_atmosphere", "prd_set_quadrature", "prd_setup", "prd_sizes", "prd_directions",
+           "prd_workspace_bytes", "prd_rhs", "prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator",
+           "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes"]
+
+
+def lib():
+    """Load libprd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not found: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        DP = ctypes.POINTER(ctypes.c_double)
+        L.prd_create.argtypes = [ctypes.POINTER(P), I, I]
+        L.prd_destroy.argtypes = [P]
+        L.prd_last_error.argtypes = [P]
+        L.prd_last_error.restype = ctypes.c_char_p
+        L.prd_set_stream.argtypes = [P, P]
+        L.prd_set_atom.argtypes = [P, ctypes.POINTER(_Atom)]
+        L.prd_set_atmosphere.argtypes = [P, I] + [DP] * 12
+        L.prd_set_quadrature.argtypes = [P, I, DP, I, I, I, I, I]
+        L.prd_setup.argtypes = [P]
+        L.prd_sizes.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]
+        L.prd_directions.argtypes = [P, DP, DP, DP]
+        L.prd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        for f in ("prd_rhs",):
+            getattr(L, f).argtypes = [P, P]
+        for f in ("prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator", "prd_apply_preconditioner"):
+            getattr(L, f).argtypes = [P, P, P]
+        L.prd_set_precond_sweeps.argtypes = [P, I]
+        L.prd_solve.argtypes = [P, D, I, I, P, P, ctypes.POINTER(I), DP, DP]
+        L.prd_emergent_stokes.argtypes = [P, P, I, DP, DP, P]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class PRD:
+    """One library context: a configured problem resident on one GPU."""
+
+    def __init__(self, cfg, precision=None, device=0, mode=None, setup=True):
+        L = lib()
+        prec = cfg.get("precision", "fp32") if precision is None else precision
+        self.prec = PRD_FP64 if prec in ("fp64", PRD_FP64) else PRD_FP32
+        self.dtype = torch.float64 if self.prec == PRD_FP64 else torch.float32
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        self._check(L.prd_create(ctypes.byref(h), device, self.prec), None)
+        self.h = h
+        atom = cfg["atom"]
+        A = _Atom(atom["kind"], atom["twoS"], (ctypes.c_double * 2)(*atom["E_u_cm"]), atom["mass_amu"],
+                  atom.get("g_s", 2.0), atom.get("nu0_hz", 0.0))
+        self._check(L.prd_set_atom(self.h, ctypes.byref(A)))
+        atm = cfg["atm"]
+        keep = [_dp(atm[k]) for k in ("z_km", "T_K", "xi_kms", "a", "eps", "r_el", "k_line", "W_T", "B_G",
+                                      "thetaB", "chiB", "v_kms")]
+        self._check(L.prd_set_atmosphere(self.h, len(atm["z_km"]), *[p for _, p in keep]))
+        q = cfg["quad"]
+        g, gp = _dp(q["grid"])
+        self._check(L.prd_set_quadrature(self.h, len(g), gp, q["grid_kind"], q["n_mu_half"], q["n_chi"],
+                                         q.get("mu_rule", 0), q.get("mode", 0) if mode is None else mode))
+        if setup:
+            self.setup()
+
+    def _check(self, rc, h=0):
+        if rc != PRD_OK:
+            msg = lib().prd_last_error(self.h if h == 0 else h)
+            raise PrdError(rc, msg.decode() if msg else "")
+
+    def setup(self):
+        self._check(lib().prd_setup(self.h))
+        nz, nO, nN, nT = (ctypes.c_int() for _ in range(4))
+        n = ctypes.c_int64()
+        self._check(lib().prd_sizes(self.h, ctypes.byref(nz), ctypes.byref(nO), ctypes.byref(nN),
+                                    ctypes.byref(nT), ctypes.byref(n)))
+        self.nz, self.nO, self.nN, self.n_theta, self.n = nz.value, nO.value, nN.value, nT.value, n.value
+        self.shape = (self.nz, self.nO, self.nN, 4)
+        mu, chi, w = (np.zeros(self.nO) for _ in range(3))
+        self._check(lib().prd_directions(self.h, mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         chi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        self.mu, self.chi, self.w = mu, chi, w
+
+    def workspace_bytes(self):
+        b = ctypes.c_int64()
+        self._check(lib().prd_workspace_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self._check(lib().prd_set_stream(self.h, ctypes.c_void_p(s)))
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+
+    def _vec(self, x):
+        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous() and tuple(x.shape) == self.shape
+        return ctypes.c_void_p(x.data_ptr())
+
+    def rhs(self, out=None):
+        self._stream()
+        out = self.empty() if out is None else out
+        self._check(lib().prd_rhs(self.h, self._vec(out)))
+        return out
+
+    def apply_sigma(self, x, out=None):
+        self._stream()
+        out = self.empty() if out is None else out
+        self._check(lib().prd_apply_sigma(self.h, self._vec(x), self._vec(out)))
+        return out
+
+    def apply_lambda(self, eps, out=None):
+        self._stream()
+        out = self.empty() if out is None else out
+        self._check(lib().prd_apply_lambda(self.h, self._vec(eps), self._vec(out)))
+        return out
+
+    def apply_operator(self, x, out=None):
+        self._stream()
+        out = self.empty() if out is None else out
+        self._check(lib().prd_apply_operator(self.h, self._vec(x), self._vec(out)))
+        return out
+
+    def apply_preconditioner(self, y, out=None):
+        self._stream()
+        out = self.empty() if out is None else out
+        self._check(lib().prd_apply_preconditioner(self.h, self._vec(y), self._vec(out)))
+        return out
+
+    def set_precond_sweeps(self, m):
+        self._check(lib().prd_set_precond_sweeps(self.h, m))
+
+    def solve(self, tol=1e-6, max_iter=200, restart=30, x0=None, out=None, history=False, check=True):
+        self._stream()
+        out = self.empty() if out is None else out
+        it = ctypes.c_int()
+        res = ctypes.c_double()
+        hist = np.zeros(max_iter + 2)
+        rc = lib().prd_solve(self.h, tol, max_iter, restart, None if x0 is None else self._vec(x0),
+                             self._vec(out), ctypes.byref(it), ctypes.byref(res),
+                             hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if check:
+            self._check(rc)
+        info = dict(iters=it.value, true_rel_res=res.value, rc=rc, history=hist[:max(it.value, 1)])
+        return out, info
+
+    def emergent_stokes(self, x, mu, chi, out=None):
+        self._stream()
+        mu, mup = _dp(mu)
+        chi, chip = _dp(chi)
+        out = torch.empty((len(mu), self.nN, 4), dtype=self.dtype, device=self.device) if out is None else out
+        self._check(lib().prd_emergent_stokes(self.h, self._vec(x), len(mu), mup, chip, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().prd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,324 @@
+// C ABI entry points (include/prd.h): argument checks, ordering, setup
+// orchestration.  No exception leaves this file.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include "prd_internal.h"
+
+namespace prd {
+
+int fail(Ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int dalloc(Ctx* c, DBuf& b, size_t bytes) {
+  dfree(b);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(c, PRD_E_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return PRD_OK;
+}
+
+void dfree(DBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int upload(Ctx* c, DBuf& b, const void* host, size_t bytes) {
+  int rc = dalloc(c, b, bytes);
+  if (rc) return rc;
+  PRD_CUDA_TRY(c, cudaMemcpy(b.p, host, bytes, cudaMemcpyHostToDevice));
+  return PRD_OK;
+}
+
+static void free_all(Ctx* c) {
+  DBuf* bufs[] = {&c->tiles, &c->Y, &c->r3w, &c->r3in, &c->r3out, &c->r3prof, &c->r3J, &c->r3ab, &c->kt,
+                  &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk, &c->cls_dev, &c->dmu,
+                  &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
+                  &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots};
+  for (DBuf* b : bufs) dfree(*b);
+  for (auto& b : c->krylov) dfree(b);
+  c->krylov.clear();
+  for (void* p : c->owned) cudaFree(p);
+  c->owned.clear();
+}
+
+Ctx::~Ctx() { free_all(this); }
+
+int launch_precond_setup(Ctx* c);
+
+static int setup(Ctx* c) {
+  c->ready = false;
+  free_all(c);
+  int rc = build_host_tables(c);
+  if (rc) return rc;
+  // memory check for the tiles
+  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntrip * c->nnu * 2 * c->nnu * c->esz;
+  size_t fr = 0, tot = 0;
+  PRD_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
+  if (tile_bytes > fr * 0.9)
+    return fail(c, PRD_E_NOMEM, "R_II tiles need " + std::to_string(tile_bytes >> 20) + " MiB, device has " +
+                                    std::to_string(fr >> 20) + " MiB free");
+  if ((rc = dalloc(c, c->tiles, tile_bytes))) return rc;
+  const int nq = c->nu_st * c->nu_st * c->nl_st;
+  if ((rc = dalloc(c, c->r3w, (size_t)c->nz * nq * 2 * c->nnu * c->esz))) return rc;
+  if ((rc = upload(c, c->dmu, c->mu.data(), c->mu.size() * 8))) return rc;
+  if ((rc = build_device_tables(c))) return rc;
+  if ((rc = dalloc(c, c->gm_t, nvec(c) * c->esz))) return rc;
+  if ((rc = launch_tiles(c))) return rc;
+  if ((rc = compute_normalisation(c))) return rc;
+  if ((rc = launch_precond_setup(c))) return rc;
+  PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->ready = true;
+  return PRD_OK;
+}
+
+}  // namespace prd
+
+using prd::Ctx;
+using prd::fail;
+
+struct prd_ctx {
+  Ctx c;
+};
+
+#define CTX_OR_ARG(ctx)                 \
+  if (!(ctx)) return PRD_E_ARG;         \
+  Ctx* c = &(ctx)->c;                   \
+  cudaSetDevice(c->device);
+
+#define NEED_READY()                                              \
+  if (!c->ready) return fail(c, PRD_E_STATE, "call prd_setup first");
+
+extern "C" {
+
+int prd_create(prd_ctx** out, int device, int precision) {
+  if (!out) return PRD_E_ARG;
+  *out = nullptr;
+  if (precision != PRD_FP64 && precision != PRD_FP32) return PRD_E_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return PRD_E_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return PRD_E_CUDA;
+  prd_ctx* h = new (std::nothrow) prd_ctx();
+  if (!h) return PRD_E_NOMEM;
+  h->c.device = device;
+  h->c.prec = precision;
+  h->c.esz = precision == PRD_FP64 ? 8 : 4;
+  *out = h;
+  return PRD_OK;
+}
+
+int prd_destroy(prd_ctx* ctx) {
+  if (!ctx) return PRD_OK;
+  cudaSetDevice(ctx->c.device);
+  delete ctx;
+  return PRD_OK;
+}
+
+const char* prd_last_error(const prd_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null ctx"; }
+
+int prd_set_stream(prd_ctx* ctx, void* stream) {
+  CTX_OR_ARG(ctx);
+  c->stream = (cudaStream_t)stream;
+  return PRD_OK;
+}
+
+int prd_set_atom(prd_ctx* ctx, const prd_atom* atom) {
+  CTX_OR_ARG(ctx);
+  if (!atom) return fail(c, PRD_E_ARG, "atom is NULL");
+  if (!(atom->twoS == 0 || atom->twoS == 1)) return fail(c, PRD_E_ARG, "twoS must be 0 or 1");
+  if (atom->kind != (atom->twoS == 0 ? PRD_TWO_LEVEL : PRD_TWO_TERM))
+    return fail(c, PRD_E_ARG, "kind must be PRD_TWO_LEVEL for twoS=0 and PRD_TWO_TERM for twoS=1");
+  if (!(atom->mass_amu > 0) || !(atom->E_u_cm[0] > 0) || (atom->twoS == 1 && !(atom->E_u_cm[1] > 0)))
+    return fail(c, PRD_E_ARG, "mass and energies must be positive");
+  c->atom = *atom;
+  if (c->atom.g_s == 0.0) c->atom.g_s = 2.0;
+  c->have_atom = true;
+  c->ready = false;
+  return PRD_OK;
+}
+
+int prd_set_atmosphere(prd_ctx* ctx, int nz, const double* z_km, const double* T_K, const double* xi_kms,
+                       const double* a, const double* eps, const double* r_el, const double* k_line,
+                       const double* W_T, const double* B_G, const double* thetaB, const double* chiB,
+                       const double* v_kms) {
+  CTX_OR_ARG(ctx);
+  if (nz < 2) return fail(c, PRD_E_ARG, "nz must be >= 2");
+  const double* arrs[] = {z_km, T_K, xi_kms, a, eps, r_el, k_line, W_T, B_G, thetaB, chiB, v_kms};
+  for (const double* p : arrs)
+    if (!p) return fail(c, PRD_E_ARG, "atmosphere array is NULL");
+  for (int i = 0; i < nz; ++i) {
+    if (i > 0 && !(z_km[i] > z_km[i - 1])) return fail(c, PRD_E_ARG, "z_km must be strictly ascending");
+    if (!(T_K[i] > 0) || !(a[i] > 0) || !(k_line[i] > 0) || !(W_T[i] >= 0) || !(eps[i] >= 0 && eps[i] < 1) ||
+        !(r_el[i] >= 0 && r_el[i] < 1) || !(B_G[i] >= 0) || !std::isfinite(xi_kms[i]))
+      return fail(c, PRD_E_ARG, "atmosphere value out of range at height " + std::to_string(i));
+  }
+  c->nz = nz;
+  c->z.assign(z_km, z_km + nz);
+  c->T.assign(T_K, T_K + nz);
+  c->xi.assign(xi_kms, xi_kms + nz);
+  c->a.assign(a, a + nz);
+  c->eps.assign(eps, eps + nz);
+  c->rE.assign(r_el, r_el + nz);
+  c->k.assign(k_line, k_line + nz);
+  c->WT.assign(W_T, W_T + nz);
+  c->B.assign(B_G, B_G + nz);
+  c->thB.assign(thetaB, thetaB + nz);
+  c->chB.assign(chiB, chiB + nz);
+  c->v.assign(v_kms, v_kms + 3 * nz);
+  c->have_atm = true;
+  c->ready = false;
+  return PRD_OK;
+}
+
+int prd_set_quadrature(prd_ctx* ctx, int nnu, const double* grid, int grid_kind, int n_mu_half, int n_chi,
+                       int mu_rule, int mode) {
+  CTX_OR_ARG(ctx);
+  if (nnu < 4 || nnu > 256 || !grid) return fail(c, PRD_E_ARG, "nnu must be in [4, 256] and grid non-NULL");
+  if (grid_kind != PRD_GRID_LAMBDA && grid_kind != PRD_GRID_X) return fail(c, PRD_E_ARG, "bad grid_kind");
+  if (n_mu_half < 1 || n_mu_half > 32 || n_chi < 1 || n_chi > 64) return fail(c, PRD_E_ARG, "bad angular sizes");
+  if (mu_rule != PRD_MU_GL_HEMISPHERES && mu_rule != PRD_MU_GL_FULL) return fail(c, PRD_E_ARG, "bad mu_rule");
+  if (mode != PRD_MODE_AD && mode != PRD_MODE_AA) return fail(c, PRD_E_ARG, "bad mode");
+  for (int i = 1; i < nnu; ++i)
+    if (!(grid[i] > grid[i - 1])) return fail(c, PRD_E_ARG, "grid must be strictly ascending");
+  c->nnu = nnu;
+  c->grid.assign(grid, grid + nnu);
+  c->grid_kind = grid_kind;
+  c->n_mu_half = n_mu_half;
+  c->n_chi = n_chi;
+  c->mu_rule = mu_rule;
+  c->mode = mode;
+  c->have_quad = true;
+  c->ready = false;
+  return PRD_OK;
+}
+
+int prd_setup(prd_ctx* ctx) {
+  CTX_OR_ARG(ctx);
+  if (!c->have_atom || !c->have_atm || !c->have_quad)
+    return fail(c, PRD_E_STATE, "set_atom, set_atmosphere and set_quadrature must precede setup");
+  if (c->grid_kind == PRD_GRID_LAMBDA && !(c->grid[0] > 0)) return fail(c, PRD_E_ARG, "wavelengths must be positive");
+  try {
+    return prd::setup(c);
+  } catch (const std::exception& e) {
+    return fail(c, PRD_E_NOMEM, std::string("host exception in setup: ") + e.what());
+  }
+}
+
+int prd_sizes(const prd_ctx* ctx, int* nz, int* n_omega, int* nnu, int* n_theta, int64_t* n) {
+  if (!ctx) return PRD_E_ARG;
+  const Ctx* c = &ctx->c;
+  if (!c->ready) return PRD_E_STATE;
+  if (nz) *nz = c->nz;
+  if (n_omega) *n_omega = c->nO;
+  if (nnu) *nnu = c->nnu;
+  if (n_theta) *n_theta = c->ncls;
+  if (n) *n = (int64_t)prd::nvec(c);
+  return PRD_OK;
+}
+
+int prd_directions(const prd_ctx* ctx, double* mu, double* chi, double* w) {
+  if (!ctx) return PRD_E_ARG;
+  const Ctx* c = &ctx->c;
+  if (!c->ready) return PRD_E_STATE;
+  for (int o = 0; o < c->nO; ++o) {
+    if (mu) mu[o] = c->mu[o];
+    if (chi) chi[o] = c->chi[o];
+    if (w) w[o] = c->wang[o];
+  }
+  return PRD_OK;
+}
+
+int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return PRD_E_ARG;
+  const Ctx* c = &ctx->c;
+  const prd::DBuf* bufs[] = {&c->tiles, &c->Y, &c->r3w, &c->r3in, &c->r3out, &c->r3prof, &c->r3J, &c->r3ab,
+                             &c->kt, &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk,
+                             &c->cls_dev, &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M,
+                             &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t};
+  int64_t s = 0;
+  for (auto* b : bufs) s += (int64_t)b->bytes;
+  *bytes = s;
+  return PRD_OK;
+}
+
+int prd_rhs(prd_ctx* ctx, void* b_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!b_dev) return fail(c, PRD_E_ARG, "b_dev is NULL");
+  return prd::rhs(c, b_dev);
+}
+
+int prd_apply_sigma(prd_ctx* ctx, const void* x_dev, void* eps_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !eps_dev || x_dev == eps_dev) return fail(c, PRD_E_ARG, "x_dev/eps_dev NULL or aliased");
+  return prd::apply_sigma(c, x_dev, eps_dev, true);
+}
+
+int prd_apply_lambda(prd_ctx* ctx, const void* eps_dev, void* out_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!eps_dev || !out_dev || eps_dev == out_dev) return fail(c, PRD_E_ARG, "eps_dev/out_dev NULL or aliased");
+  return prd::apply_lambda(c, eps_dev, out_dev, nullptr, false);
+}
+
+int prd_apply_operator(prd_ctx* ctx, const void* x_dev, void* y_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !y_dev || x_dev == y_dev) return fail(c, PRD_E_ARG, "x_dev/y_dev NULL or aliased");
+  return prd::apply_operator(c, x_dev, y_dev);
+}
+
+int prd_apply_preconditioner(prd_ctx* ctx, const void* y_dev, void* x_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !y_dev || x_dev == y_dev) return fail(c, PRD_E_ARG, "x_dev/y_dev NULL or aliased");
+  return prd::apply_precond(c, y_dev, x_dev);
+}
+
+int prd_set_precond_sweeps(prd_ctx* ctx, int m_in) {
+  CTX_OR_ARG(ctx);
+  if (m_in < 0 || m_in > 64) return fail(c, PRD_E_ARG, "m_in must be in [0, 64]");
+  c->m_in = m_in;
+  return PRD_OK;
+}
+
+int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x0_dev, void* x_dev, int* iters,
+              double* true_rel_res, double* res_history) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !(tol > 0) || max_iter < 1 || restart < 1) return fail(c, PRD_E_ARG, "bad solve arguments");
+  try {
+    return prd::solve(c, tol, max_iter, restart, x0_dev, x_dev, iters, true_rel_res, res_history);
+  } catch (const std::exception& e) {
+    return fail(c, PRD_E_NOMEM, std::string("host exception in solve: ") + e.what());
+  }
+}
+
+int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu, const double* chi,
+                        void* out_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !out_dev || nlos < 1 || !mu || !chi) return fail(c, PRD_E_ARG, "bad emergent_stokes arguments");
+  for (int i = 0; i < nlos; ++i)
+    if (!(mu[i] > 0 && mu[i] <= 1)) return fail(c, PRD_E_ARG, "line-of-sight mu must be in (0, 1]");
+  try {
+    return prd::emergent(c, x_dev, nlos, mu, chi, out_dev);
+  } catch (const std::exception& e) {
+    return fail(c, PRD_E_NOMEM, std::string("host exception: ") + e.what());
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,459 @@
+// Per-apply kernels of y = (Id - Lambda Sigma) x.
+//   S1  frame change observer -> comoving: natural spline of I(z,Omega',.)
+//       evaluated at u_m - u_b(z,Omega')                     (Sect. 4.1)
+//   S3+S4  R_II contraction over (Theta class, Omega', triple, frequency)
+//       with the Stokes-route coefficients folded in          (Eq. RQIIKKp)
+//   S5  R_III, separable in incident and outgoing frequency  (Eq. RIIIQKKp)
+//   S6  frame change back (u_n + u_b(z,Omega)) and Kirchhoff factor f (App. E)
+//   S7+S8  DELO-linear sweep per ray, y = x - Lambda eps      (Sect. 3)
+#include <cstdio>
+#include "prd_internal.h"
+#include "device_common.cuh"
+
+namespace prd {
+
+// ------------------------------------------------------------------ splines
+// Second derivatives of the natural spline of every (z, Omega, s) row.
+template <typename T>
+__global__ void spline_M_kernel(const T* __restrict__ y, T* __restrict__ M, const double* __restrict__ sp,
+                                int nz, int nO, int N) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;   // (z, o, s)
+  if (row >= nz * nO * 4) return;
+  const int s = row & 3, zo = row >> 2, iz = zo / nO;
+  const double* h = sp + (size_t)iz * 3 * N;
+  const double* cp = h + N;
+  const double* den = cp + N;
+  const T* yr = y + (size_t)zo * N * 4 + s;
+  T* Mr = M + (size_t)zo * N * 4 + s;
+  Mr[0] = (T)0;
+  Mr[(size_t)(N - 1) * 4] = (T)0;
+  if (N <= 2) return;
+  // forward sweep: g_r stored in M[i], i = r + 1
+  double gprev = 0.0;
+  double y0 = (double)yr[0], y1 = (double)yr[4];
+  for (int r = 0; r < N - 2; ++r) {
+    const int i = r + 1;
+    const double y2 = (double)yr[(size_t)(i + 1) * 4];
+    const double rhs = 6.0 * ((y2 - y1) / h[i] - (y1 - y0) / h[i - 1]);
+    const double sub = (r > 0) ? h[i - 1] : 0.0;
+    const double g = (rhs - sub * gprev) / den[r];
+    Mr[(size_t)i * 4] = (T)g;
+    gprev = g;
+    y0 = y1;
+    y1 = y2;
+  }
+  double mnext = 0.0;
+  for (int r = N - 3; r >= 0; --r) {
+    const int i = r + 1;
+    const double m = (double)Mr[(size_t)i * 4] - cp[r] * mnext;
+    Mr[(size_t)i * 4] = (T)m;
+    mnext = m;
+  }
+}
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+// Evaluate the spline of every (z, Omega) row at the tabulated points; the
+// intensity component is multiplied by fI (nullable).
+template <typename T>
+__global__ void spline_eval_kernel(const T* __restrict__ y, const T* __restrict__ M, const int* __restrict__ kidx,
+                                   const double* __restrict__ tt, const double* __restrict__ sp,
+                                   const T* __restrict__ fI, T* __restrict__ out, int nz, int nO, int N) {
+  using V = typename V4<T>::type;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (z, o, n)
+  if (pt >= (long long)nz * nO * N) return;
+  const int zo = (int)(pt / N), iz = zo / nO;
+  const int k = kidx[pt];
+  const V* yr = reinterpret_cast<const V*>(y) + (size_t)zo * N;
+  const V* Mr = reinterpret_cast<const V*>(M) + (size_t)zo * N;
+  V r;
+  if (k < 0) r = yr[0];
+  else if (k >= N - 1) r = yr[N - 1];
+  else {
+    const double t = tt[pt], omt = 1.0 - t;
+    const double h = sp[(size_t)iz * 3 * N + k];
+    const double k6 = h * h / 6.0;
+    const T c0 = (T)omt, c1 = (T)t, c2 = (T)(k6 * (omt * omt * omt - omt)), c3 = (T)(k6 * (t * t * t - t));
+    const V a = yr[k], b = yr[k + 1], ma = Mr[k], mb = Mr[k + 1];
+    r.x = c0 * a.x + c1 * b.x + c2 * ma.x + c3 * mb.x;
+    r.y = c0 * a.y + c1 * b.y + c2 * ma.y + c3 * mb.y;
+    r.z = c0 * a.z + c1 * b.z + c2 * ma.z + c3 * mb.z;
+    r.w = c0 * a.w + c1 * b.w + c2 * ma.w + c3 * mb.w;
+  }
+  if (fI) r.x *= fI[pt];
+  reinterpret_cast<V*>(out)[pt] = r;
+}
+
+// ------------------------------------------------------------------ R_III
+// J[z][ku kv] += sum_{o', j} rin[z][o'][q][j] * sum_m r3w[z][q][m] I~[z][o'][m][j]
+template <typename T>
+__global__ void r3_J_kernel(const T* __restrict__ Ic, const T* __restrict__ r3w, const T* __restrict__ rin,
+                            double* __restrict__ J, int nO, int N, int nq, int nl) {
+  const int q = blockIdx.x, iz = blockIdx.y;
+  const T* w = r3w + ((size_t)iz * nq + q) * 2 * N;
+  double accr = 0.0, acci = 0.0;
+  for (int idx = threadIdx.x; idx < nO * N; idx += blockDim.x) {
+    const int o = idx / N, m = idx - o * N;
+    const T* iv = Ic + (((size_t)iz * nO + o) * N + m) * 4;
+    const T* ri = rin + (((size_t)iz * nO + o) * nq + q) * 8;
+    const double wr = (double)w[m], wi = (double)w[N + m];
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      sr += (double)ri[2 * j] * (double)iv[j];
+      si += (double)ri[2 * j + 1] * (double)iv[j];
+    }
+    accr += wr * sr - wi * si;
+    acci += wr * si + wi * sr;
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = accr;
+  red[1][threadIdx.x] = acci;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int uv = q / nl;
+    atomicAdd(&J[((size_t)iz * (nq / nl) + uv) * 2], red[0][0]);
+    atomicAdd(&J[((size_t)iz * (nq / nl) + uv) * 2 + 1], red[1][0]);
+  }
+}
+
+// eps_bar[z][o][n][i] = Re sum_uv ab[uv] J[uv] sum_kl' O_i(o; uv, kl') prof[uv][kl'][n]
+template <typename T>
+__global__ void r3_out_kernel(const double* __restrict__ J, const T* __restrict__ ab, const T* __restrict__ rout,
+                              const T* __restrict__ prof, T* __restrict__ eb, int nz, int nO, int N, int nuv,
+                              int nl) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= (long long)nz * nO * N) return;
+  const int n = (int)(pt % N);
+  const int zo = (int)(pt / N), iz = zo / nO;
+  double acc[4] = {0, 0, 0, 0};
+  for (int uv = 0; uv < nuv; ++uv) {
+    const double jr = J[((size_t)iz * nuv + uv) * 2], ji = J[((size_t)iz * nuv + uv) * 2 + 1];
+    const double ar = (double)ab[((size_t)iz * nuv + uv) * 2], ai = (double)ab[((size_t)iz * nuv + uv) * 2 + 1];
+    const double cr = ar * jr - ai * ji, ci = ar * ji + ai * jr;
+    for (int lp = 0; lp < nl; ++lp) {
+      const T* pp = prof + ((((size_t)iz * nuv + uv) * nl + lp) * N + n) * 2;
+      const double pr = (double)pp[0], pi = (double)pp[1];
+      const double dr = cr * pr - ci * pi, di = cr * pi + ci * pr;
+      const T* ro = rout + (((size_t)zo * nuv + uv) * nl + lp) * 8;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] += (double)ro[2 * i] * dr - (double)ro[2 * i + 1] * di;
+    }
+  }
+  T* o = eb + pt * 4;
+  for (int i = 0; i < 4; ++i) o[i] = (T)acc[i];
+}
+
+// ------------------------------------------------------------------ R_II (SIMT)
+// One CTA per (z, class, chunk of 16 output directions).  Over the triples t
+// and blocks of 16 incident frequencies m it builds, in shared memory,
+//   Z_t[m][(o,i)] = sum_{o' : Theta(o,o') = class} sum_j Y_t,ij(o,o') I~_j(o', m)
+// and accumulates  eps_bar[n][(o,i)] += sum_m Re(T_t[n][m] Z_t[m][(o,i)])
+// with the tile T_t of (z, class) streamed from global memory.
+constexpr int kCW = 16;      // output directions per CTA
+constexpr int kMB = 16;      // incident-frequency block
+constexpr int kMaxRows = 16; // rows per thread (N <= 256)
+
+template <typename T>
+__global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tiles, const T* __restrict__ Y,
+                                                      const T* __restrict__ Ic, const int* __restrict__ cls,
+                                                      T* __restrict__ eb, int ncls, int ntrip, int nO, int N,
+                                                      int npairs) {
+  const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
+  const int* cout_ptr = cls;
+  const int* cout_dir = cls + ncls + 1;
+  const int ne_tot = cout_ptr[ncls];
+  const int* pair_ptr = cout_dir + ne_tot;
+  const int* pair_in = pair_ptr + ne_tot + 1;
+  const int e0 = cout_ptr[c] + chunk * kCW;
+  const int e_end = cout_ptr[c + 1];
+  if (e0 >= e_end) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T (*Zs)[2][kCW * 4] = reinterpret_cast<T (*)[2][kCW * 4]>(smraw);
+  T* Asb = reinterpret_cast<T*>(smraw + sizeof(T) * kMB * 2 * kCW * 4);
+  // As[h][n][mm] -> Asb[(h * N + n) * (kMB + 1) + mm]
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int e_mine = e0 + tx;
+  T acc[kMaxRows][4];
+#pragma unroll
+  for (int r = 0; r < kMaxRows; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[r][i] = (T)0;
+  const int nrows = (N + 15) / 16;
+  const size_t tile_sz = (size_t)N * 2 * N;
+  const T* tbase = tiles + ((size_t)iz * ncls + c) * ntrip * tile_sz;
+  // Z-building role: thread -> (e = tid & 15, m = tid >> 4)
+  const int ze = tid & 15, zm = tid >> 4;
+  const int e_z = e0 + ze;
+  for (int t = 0; t < ntrip; ++t) {
+    const T* tile = tbase + (size_t)t * tile_sz;
+    for (int m0 = 0; m0 < N; m0 += kMB) {
+      // ---- Z block
+      {
+        const int m = m0 + zm;
+        T zr[4] = {0, 0, 0, 0}, zi[4] = {0, 0, 0, 0};
+        if (e_z < e_end && m < N) {
+          for (int p = pair_ptr[e_z]; p < pair_ptr[e_z + 1]; ++p) {
+            const int op = pair_in[p];
+            const T* iv = Ic + (((size_t)iz * nO + op) * N + m) * 4;
+            const T* y = Y + (((size_t)iz * npairs + p) * ntrip + t) * 32;
+            const T i0 = iv[0], i1 = iv[1], i2 = iv[2], i3 = iv[3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const T* yi = y + i * 8;
+              zr[i] += yi[0] * i0 + yi[2] * i1 + yi[4] * i2 + yi[6] * i3;
+              zi[i] += yi[1] * i0 + yi[3] * i1 + yi[5] * i2 + yi[7] * i3;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          Zs[zm][0][ze * 4 + i] = zr[i];
+          Zs[zm][1][ze * 4 + i] = zi[i];
+        }
+      }
+      // ---- tile block: rows n, columns m0..m0+15 (Re and Im halves)
+      for (int idx = tid; idx < N * 2 * kMB; idx += 256) {
+        const int mm = idx % kMB;
+        const int h = (idx / kMB) & 1;
+        const int n = idx / (2 * kMB);
+        const int m = m0 + mm;
+        Asb[(h * N + n) * (kMB + 1) + mm] = (m < N) ? tile[(size_t)n * 2 * N + h * N + m] : (T)0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int mm = 0; mm < kMB; ++mm) {
+        T zr[4], zi[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          zr[i] = Zs[mm][0][tx * 4 + i];
+          zi[i] = Zs[mm][1][tx * 4 + i];
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxRows; ++r) {
+          if (r < nrows) {
+            const int n = ty + 16 * r;
+            if (n < N) {
+              const T ar = Asb[n * (kMB + 1) + mm], ai = Asb[(N + n) * (kMB + 1) + mm];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) acc[r][i] += ar * zr[i] - ai * zi[i];
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (e_mine < e_end) {
+    const int o = cout_dir[e_mine];
+#pragma unroll
+    for (int r = 0; r < kMaxRows; ++r) {
+      const int n = ty + 16 * r;
+      if (r < nrows && n < N) {
+        T* dst = eb + (((size_t)iz * nO + o) * N + n) * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) atomicAdd(dst + i, acc[r][i]);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ DELO
+// One thread per ray (Omega, nu): I_k = (Id + b K'_k)^-1 [(e Id - a K'_{k-1}) I_{k-1}
+//   + a S_{k-1} + b S_k], S = eps/eta1, K' = K/eta1 - Id.  Optional: out = x - I.
+template <typename T>
+__device__ __forceinline__ void kprime(const T* t, T K[4][4]) {
+  K[0][0] = 0; K[1][1] = 0; K[2][2] = 0; K[3][3] = 0;
+  K[0][1] = K[1][0] = t[0];
+  K[0][2] = K[2][0] = t[1];
+  K[0][3] = K[3][0] = t[2];
+  K[1][2] = t[3]; K[2][1] = -t[3];
+  K[1][3] = t[4]; K[3][1] = -t[4];
+  K[2][3] = t[5]; K[3][2] = -t[5];
+}
+
+template <typename T>
+__global__ void delo_kernel(const T* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
+                            const T* __restrict__ x_sub, T* __restrict__ out, int nz, int nO, int N, int boundary,
+                            double WT0) {
+  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ray >= nO * N) return;
+  const int o = ray / N, n = ray - o * N;
+  const bool up = mu[o] > 0.0;
+  T I[4] = {0, 0, 0, 0};
+  T Sp[4] = {0, 0, 0, 0};
+  T Kp[4][4];
+  for (int p = 0; p < nz; ++p) {
+    const int k = up ? p : nz - 1 - p;
+    const size_t pt = ((size_t)k * nO + o) * N + n;
+    const T* t = kt + pt * 10;
+    T Kk[4][4];
+    kprime(t, Kk);
+    const T ie = t[6];
+    T S[4];
+    for (int s = 0; s < 4; ++s) S[s] = eps[pt * 4 + s] * ie;
+    if (p == 0) {
+      I[0] = (boundary && up) ? (T)WT0 : (T)0;
+      I[1] = I[2] = I[3] = (T)0;
+    } else {
+      const T e = t[7], al = t[8], be = t[9];
+      T rhs[4];
+      for (int i = 0; i < 4; ++i) {
+        T v = e * I[i] + al * Sp[i] + be * S[i];
+        for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j];
+        rhs[i] = v;
+      }
+      T A[4][4];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) A[i][j] = (i == j ? (T)1 : (T)0) + be * Kk[i][j];
+      // Gaussian elimination without pivoting (symmetric part positive definite)
+      for (int c0 = 0; c0 < 4; ++c0) {
+        const T inv = (T)1 / A[c0][c0];
+        for (int r = c0 + 1; r < 4; ++r) {
+          const T f = A[r][c0] * inv;
+          for (int cc = c0; cc < 4; ++cc) A[r][cc] -= f * A[c0][cc];
+          rhs[r] -= f * rhs[c0];
+        }
+      }
+      for (int r = 3; r >= 0; --r) {
+        T v = rhs[r];
+        for (int cc = r + 1; cc < 4; ++cc) v -= A[r][cc] * I[cc];
+        I[r] = v / A[r][r];
+      }
+    }
+    for (int s = 0; s < 4; ++s) {
+      out[pt * 4 + s] = x_sub ? x_sub[pt * 4 + s] - I[s] : I[s];
+    }
+    for (int i = 0; i < 4; ++i) {
+      Sp[i] = S[i];
+      for (int j = 0; j < 4; ++j) Kp[i][j] = Kk[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void normalise_kernel(const T* __restrict__ num, const T* __restrict__ kt, const double* __restrict__ fac,
+                                 T* __restrict__ f, int nz, int nO, int N) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= (long long)nz * nO * N) return;
+  const int iz = (int)(pt / ((long long)nO * N));
+  const double eta1 = 1.0 / (double)kt[pt * 10 + 6];
+  f[pt] = (T)(fac[iz] * eta1 / (double)num[pt * 4]);
+}
+
+template <typename T>
+__global__ void fill_planck_kernel(T* __restrict__ x, const double* __restrict__ WT, int nz, int nO, int N) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= (long long)nz * nO * N) return;
+  const int iz = (int)(pt / ((long long)nO * N));
+  x[pt * 4] = (T)WT[iz];
+  x[pt * 4 + 1] = x[pt * 4 + 2] = x[pt * 4 + 3] = (T)0;
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+static int sigma_T(Ctx* c, const T* x, T* eps, bool normalised) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const long long npt = (long long)nz * nO * N;
+  T* M = (T*)c->scratch1.p;
+  T* Ic = (T*)c->scratch2.p;
+  T* eb = (T*)c->scratch3.p;
+  const double* sp = (const double*)c->sp.p;
+  // S1
+  spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, M, sp, nz, nO, N);
+  spline_eval_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, M, (const int*)c->iin.p, (const double*)c->tin.p,
+                                                                  sp, nullptr, Ic, nz, nO, N);
+  // S5 (initialises eps_bar)
+  const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
+  PRD_CUDA_TRY(c, cudaMemsetAsync(c->r3J.p, 0, c->r3J.bytes, c->stream));
+  r3_J_kernel<T><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
+                                                        (double*)c->r3J.p, nO, N, nq, c->nl_st);
+  r3_out_kernel<T><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)c->r3J.p, (const T*)c->r3ab.p,
+                                                               (const T*)c->r3out.p, (const T*)c->r3prof.p, eb, nz,
+                                                               nO, N, nuv, c->nl_st);
+  // S3 + S4
+  const int nchunk = (c->max_cout + kCW - 1) / kCW;
+  const size_t smem = sizeof(T) * ((size_t)kMB * 2 * kCW * 4 + (size_t)2 * N * (kMB + 1));
+  cudaFuncSetAttribute(r2_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  r2_simt_kernel<T><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
+      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntrip, nO, N, c->npairs);
+  // S6
+  spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, M, sp, nz, nO, N);
+  spline_eval_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, M, (const int*)c->ibk.p, (const double*)c->tbk.p,
+                                                                  sp, normalised ? (const T*)c->f.p : nullptr, eps, nz,
+                                                                  nO, N);
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
+
+int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised) {
+  if (c->prec == PRD_FP64) return sigma_T<double>(c, (const double*)x, (double*)eps, normalised);
+  return sigma_T<float>(c, (const float*)x, (float*)eps, normalised);
+}
+
+int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool boundary) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const double* dmu = (const double*)c->dmu.p;
+  if (c->prec == PRD_FP64)
+    delo_kernel<double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p, dmu,
+                                                                       (const double*)sub_from, (double*)out, nz, nO,
+                                                                       N, boundary ? 1 : 0, c->WT[0]);
+  else
+    delo_kernel<float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p, dmu,
+                                                                      (const float*)sub_from, (float*)out, nz, nO, N,
+                                                                      boundary ? 1 : 0, c->WT[0]);
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
+
+int compute_normalisation(Ctx* c) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const long long npt = (long long)nz * nO * N;
+  DBuf wt, fac, xin, num;
+  std::vector<double> f(nz);
+  for (int iz = 0; iz < nz; ++iz) f[iz] = (1.0 - c->eps[iz]) * c->WT[iz];
+  int rc;
+  if ((rc = upload(c, wt, c->WT.data(), nz * 8)) || (rc = upload(c, fac, f.data(), nz * 8)) ||
+      (rc = dalloc(c, xin, nvec(c) * c->esz)) || (rc = dalloc(c, num, nvec(c) * c->esz))) {
+    dfree(wt); dfree(fac); dfree(xin); dfree(num);
+    return rc;
+  }
+  if (c->prec == PRD_FP64) {
+    fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
+    rc = apply_sigma(c, xin.p, num.p, false);
+    if (!rc)
+      normalise_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const double*)num.p, (const double*)c->kt.p,
+                                                                           (const double*)fac.p, (double*)c->f.p, nz, nO, N);
+  } else {
+    fill_planck_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((float*)xin.p, (const double*)wt.p, nz, nO, N);
+    rc = apply_sigma(c, xin.p, num.p, false);
+    if (!rc)
+      normalise_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const float*)num.p, (const float*)c->kt.p,
+                                                                          (const double*)fac.p, (float*)c->f.p, nz, nO, N);
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  dfree(wt); dfree(fac); dfree(xin); dfree(num);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("normalisation: ") + cudaGetErrorString(e));
+  return PRD_OK;
+}
+
+int apply_operator(Ctx* c, const void* x, void* y) {
+  int rc = apply_sigma(c, x, c->gm_t.p, true);
+  if (rc) return rc;
+  return apply_lambda(c, c->gm_t.p, y, x, false);
+}
+
+int rhs(Ctx* c, void* b) { return apply_lambda(c, c->epsth.p, b, nullptr, true); }
+
+}  // namespace prd

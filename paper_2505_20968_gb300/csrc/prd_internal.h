@@ -1,0 +1,150 @@
+// Internal declarations shared by the library's translation units (host C++
+// and CUDA).  Nothing here is part of the C ABI (include/prd.h).
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "../../include/prd.h"
+
+namespace prd {
+
+using cplx = std::complex<double>;
+
+// physical constants (CODATA 2018), library copy
+constexpr double kC = 2.99792458e8;            // m/s
+constexpr double kKB = 1.380649e-23;           // J/K
+constexpr double kAMU = 1.66053906660e-27;     // kg
+constexpr double kMuBoverH = 1.39962449361e10; // Hz/T
+constexpr double kGauss = 1e-4;                // T/G
+constexpr double kCmToHz = 2.99792458e10;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+constexpr int kWeidemanN64 = 36;   // Faddeeva expansion terms, FP64 paths
+constexpr int kWeidemanN32 = 20;   // Faddeeva expansion terms, FP32 paths
+
+// device buffer with byte size
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  int prec = PRD_FP32;
+  size_t esz = 4;               // element size of vectors (4 or 8)
+  cudaStream_t stream = nullptr;
+  std::string err = "ok";
+
+  // ---- inputs
+  bool have_atom = false, have_atm = false, have_quad = false, ready = false;
+  prd_atom atom{};
+  int nz = 0;
+  std::vector<double> z, T, xi, a, eps, rE, k, WT, B, thB, chB, v;
+  int nnu = 0;
+  std::vector<double> grid;
+  int grid_kind = 0, n_mu_half = 0, n_chi = 0, mu_rule = 0, mode = 0;
+  int m_in = 2;
+
+  // ---- derived on host
+  int nO = 0;
+  std::vector<double> mu, chi, wang;
+  int ncls = 0;                       // scattering-angle classes (class 0: Theta = 0)
+  std::vector<double> theta;          // per class
+  std::vector<int> cls;               // [o][o'] class index
+  // per class: output directions (CSR) and, per output direction, input dirs
+  std::vector<int> cout_ptr, cout_dir;    // cout_ptr[c]..cout_ptr[c+1]
+  std::vector<int> pair_ptr, pair_in;     // per (class, out-entry): pairs
+  int npairs = 0, max_cout = 0;
+  int nu_st = 0, nl_st = 0;             // upper / lower states
+  int ntrip = 0;                         // R_II triples (k, kl, kl')
+  std::vector<int> trip_k, trip_l, trip_lp;
+  int nq3 = 0;                           // R_III incident combos (ku, kv, kl)
+  double nu0 = 0;
+  std::vector<double> dnuD, vD;          // per z (Hz, km/s)
+  std::vector<double> u;                 // [z][n]
+  std::vector<double> ub;                // [z][o]
+  std::vector<double> shift;             // [z][ku][kl]
+  std::vector<cplx> alpha, beta;         // [z][ku][kv]
+  std::vector<cplx> amp;                 // [z][o][2][ku][kl]
+  std::vector<double> Q;                 // [z][n][n] natural-spline 2nd-derivative map
+  std::vector<int> theta_node_cls;       // AA: unused
+  int n_aa_theta = 0;
+  std::vector<double> aa_theta, aa_w;     // AA Theta rule
+
+  // ---- device
+  DBuf tiles;        // [z][c][t][n][2N]    (T)
+  DBuf Y;            // [z][pair][t][16]    complex (T2)
+  DBuf r3w;          // [z][q3][N] complex  (T2)  R_III incident weights
+  DBuf r3in;         // [z][o'][q3][4] complex: w_o' * I_j(o'; ku, kv, kl)
+  DBuf r3out;        // [z][o][uv][kl'][4] complex: O_i(o; ku, kv, kl') * c
+  DBuf r3prof;       // [z][uv][kl'][N] complex: outgoing profile
+  DBuf r3J;          // [z][uv] complex scratch
+  DBuf r3ab;         // [z][uv] complex (beta-alpha) * k * c3
+  DBuf kt;           // [z][o][n][10] K'/eta1 (6), 1/eta1, exp(-d), alpha, beta
+  DBuf epsth;        // [z][o][n][4]
+  DBuf f;            // [z][o][n]
+  DBuf sp;           // spline tables: per z  h[N-1], cp[N], den[N]  (T) -> [z][3][N]
+  DBuf ugrid;        // [z][N] (T)
+  DBuf iin, ibk;     // interpolation [z][o][n]: int k | flag, and t (T)  -> int2/ T pairs
+  DBuf tin, tbk;
+  DBuf cls_dev;      // cout_ptr, cout_dir, pair_ptr, pair_in  (int)
+  DBuf dmu;          // [nO] mu of each direction (double)
+  DBuf scratch1, scratch2, scratch3;  // N-vector scratch (T)
+  // preconditioner
+  DBuf pc_phi;       // [z][N][N] Phi_bar (T)
+  DBuf pc_M;         // [z][N][N] Phi_bar (Id - A)^-1 (T)
+  DBuf pc_lii;       // [z][o][n] Lambda_ii (T)
+  DBuf pc_eta;       // [z][o][n]: eta1 (T)  (scalar Lambda*)
+  DBuf pc_delo;      // [z][o][n][3] (T)
+  DBuf pc_s1, pc_s2, pc_s3;   // scalar N/4 scratch
+  std::vector<double> pc_lii_host;
+  // GMRES
+  std::vector<DBuf> krylov;
+  DBuf gm_w, gm_r, gm_t, gm_dots;
+  std::vector<void*> owned;
+
+  ~Ctx();
+};
+
+// ---- errors
+int fail(Ctx* c, int code, const std::string& msg);
+#define PRD_CUDA_TRY(ctx, expr)                                                     \
+  do {                                                                              \
+    cudaError_t _e = (expr);                                                        \
+    if (_e != cudaSuccess)                                                          \
+      return ::prd::fail((ctx), PRD_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+int dalloc(Ctx* c, DBuf& b, size_t bytes);
+void dfree(DBuf& b);
+int upload(Ctx* c, DBuf& b, const void* host, size_t bytes);
+
+// ---- host math (host_math.cpp)
+cplx faddeeva_host(cplx z);
+void weideman_coeffs(int n, double* a_out, double* L_out);
+void natural_spline_Q(const double* u, int n, double* Q);
+
+// ---- setup pieces (host_setup.cpp)
+int build_host_tables(Ctx* c);
+int build_device_tables(Ctx* c);
+
+// ---- device launchers (kernels_*.cu)
+int launch_tiles(Ctx* c);
+int launch_setup_tables(Ctx* c);   // normalisation etc. (needs apply)
+int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised);
+int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool boundary);
+int apply_operator(Ctx* c, const void* x, void* y);
+int apply_precond(Ctx* c, const void* y, void* x);
+int compute_normalisation(Ctx* c);
+int rhs(Ctx* c, void* b);
+int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x, int* iters,
+          double* true_res, double* hist);
+int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, void* out);
+int upload_faddeeva_coeffs(Ctx* c);
+
+size_t nvec(const Ctx* c);   // 4*nz*nO*nnu
+
+}  // namespace prd
