@@ -61,7 +61,7 @@ static int setup(Ctx* c) {
   int rc = build_host_tables(c);
   if (rc) return rc;
   // memory check for the tiles
-  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntrip * c->nnu * 2 * c->nnu * c->esz;
+  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * 2 * c->nnu * c->esz;
   size_t fr = 0, tot = 0;
   PRD_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
   if (tile_bytes > fr * 0.9)

@@ -53,6 +53,36 @@ cplx faddeeva_host(cplx z) {
   return 2.0 * p / (d * d) + 1.0 / (kSqrtPi * d);
 }
 
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1], Newton on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double dp = n * (t * p1 - p0) / (t * t - 1.0);
+      const double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    const double dp = n * (t * p1 - p0) / (t * t - 1.0);
+    x[n - 1 - i] = t;   // ascending
+    w[n - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
 // Natural cubic spline (zero end second derivatives): Q maps node values to
 // second derivatives M = Q y.  Rows 0 and n-1 are zero.  Row-major n x n.
 void natural_spline_Q(const double* u, int n, double* Q) {

@@ -13,35 +13,6 @@ namespace prd {
 
 namespace {
 
-void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double t = std::cos(kPi * (i + 0.75) / (n + 0.5));
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = t;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      const double dp = n * (t * p1 - p0) / (t * t - 1.0);
-      const double dt = p1 / dp;
-      t -= dt;
-      if (std::fabs(dt) < 1e-16) break;
-    }
-    double p0 = 1.0, p1 = t;
-    for (int k = 2; k <= n; ++k) {
-      const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
-      p0 = p1;
-      p1 = p2;
-    }
-    const double dp = n * (t * p1 - p0) / (t * t - 1.0);
-    x[n - 1 - i] = t;   // ascending
-    w[n - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
-  }
-}
-
 // Stokes "Pauli" matrices: I = Tr(rho), Q = Tr(s_z rho), U = Tr(s_x rho),
 // V = Tr(s_y rho), rho the coherency matrix of (E_a, E_b).
 const cplx kSig[4][2][2] = {
@@ -309,6 +280,19 @@ int build_host_tables(Ctx* c) {
           c->trip_lp.push_back(lp);
         }
   c->ntrip = (int)c->trip_k.size();
+  // group of each upper state: the J level whose B = 0 energy is closest
+  {
+    std::vector<int> grp_of(nu_, 0);
+    c->ngrp = 1;
+    if (at.twoS == 1) {
+      c->ngrp = 2;
+      const double E12 = at.E_u_cm[0] * kCmToHz - c->nu0, E32 = at.E_u_cm[1] * kCmToHz - c->nu0;
+      States sb = pb_states(at, c->nu0, 0.0);
+      for (int k = 0; k < nu_; ++k) grp_of[k] = std::fabs(sb.E[k] - E12) <= std::fabs(sb.E[k] - E32) ? 0 : 1;
+    }
+    c->trip_grp.resize(c->ntrip);
+    for (int t = 0; t < c->ntrip; ++t) c->trip_grp[t] = grp_of[c->trip_k[t]];
+  }
   c->shift.assign((size_t)nz * nu_ * nl, 0.0);
   c->alpha.assign((size_t)nz * nu_ * nu_, 0.0);
   c->beta.assign((size_t)nz * nu_ * nu_, 0.0);

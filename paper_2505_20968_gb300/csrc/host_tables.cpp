@@ -165,8 +165,8 @@ int build_device_tables(Ctx* c) {
   // ---- R_II contraction coefficients Y[z][pair][t][i][j] (complex)
   {
     const double c2 = 3.0 / (4.0 * kPi * S2);
-    const int nt = c->ntrip;
-    std::vector<double> Y((size_t)nz * c->npairs * nt * 32);
+    const int nt = c->ntrip, nti = c->ntile(), ng = c->ngrp;
+    std::vector<double> Y((size_t)nz * c->npairs * nti * 32, 0.0);
 #pragma omp parallel for schedule(dynamic)
     for (int iz = 0; iz < nz; ++iz) {
       std::vector<std::vector<cplx>> O(nO), I(nO);
@@ -188,9 +188,13 @@ int build_device_tables(Ctx* c) {
                     y += O[o][(((size_t)ku * nu_ + k) * nl + lp) * 4 + i] *
                          I[op][(((size_t)ku * nu_ + k) * nl + l) * 4 + j] * al[(size_t)ku * nu_ + k];
                   y *= fac;
-                  const size_t idx = ((((size_t)iz * c->npairs + pidx) * nt + t) * 16 + i * 4 + j) * 2;
+                  // deviation tile of triple t, and the group-mean tile of its J level
+                  const size_t idx = ((((size_t)iz * c->npairs + pidx) * nti + ng + t) * 16 + i * 4 + j) * 2;
                   Y[idx] = y.real();
                   Y[idx + 1] = y.imag();
+                  const size_t ig = ((((size_t)iz * c->npairs + pidx) * nti + c->trip_grp[t]) * 16 + i * 4 + j) * 2;
+                  Y[ig] += y.real();
+                  Y[ig + 1] += y.imag();
                 }
             }
           }

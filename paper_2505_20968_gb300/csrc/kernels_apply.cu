@@ -386,12 +386,33 @@ static int sigma_T(Ctx* c, const T* x, T* eps, bool normalised) {
   const size_t smem = sizeof(T) * ((size_t)kMB * 2 * kCW * 4 + (size_t)2 * N * (kMB + 1));
   cudaFuncSetAttribute(r2_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   r2_simt_kernel<T><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
-      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntrip, nO, N, c->npairs);
+      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
   // S6
   spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, M, sp, nz, nO, N);
   spline_eval_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, M, (const int*)c->ibk.p, (const double*)c->tbk.p,
                                                                   sp, normalised ? (const T*)c->f.p : nullptr, eps, nz,
                                                                   nO, N);
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
+
+// Spline frame change of a whole vector: to the comoving frame (I(u_n - u_b))
+// or back (eps(u_n + u_b)); uses scratch1 for the second derivatives.
+int spline_frame_change(Ctx* c, const void* in, void* out, bool to_comoving) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const long long npt = (long long)nz * nO * N;
+  const double* sp = (const double*)c->sp.p;
+  const int* kk = (const int*)(to_comoving ? c->iin.p : c->ibk.p);
+  const double* tt = (const double*)(to_comoving ? c->tin.p : c->tbk.p);
+  if (c->prec == PRD_FP64) {
+    spline_M_kernel<double><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>((const double*)in, (double*)c->scratch1.p, sp, nz, nO, N);
+    spline_eval_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const double*)in, (const double*)c->scratch1.p, kk, tt,
+                                                                         sp, nullptr, (double*)out, nz, nO, N);
+  } else {
+    spline_M_kernel<float><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>((const float*)in, (float*)c->scratch1.p, sp, nz, nO, N);
+    spline_eval_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const float*)in, (const float*)c->scratch1.p, kk, tt,
+                                                                        sp, nullptr, (float*)out, nz, nO, N);
+  }
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

@@ -307,6 +307,34 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) r3_kernel(R3Params p, T* o
   fold_row<T>(PyR, PyI, PmR, PmI, p.Q + (size_t)iz * N * N, N, o, o + N);
 }
 
+// Group-mean / deviation split of the FP64 tiles of one height:
+//   tiles[c][g][.]        = mean over the triples t of group g of G_t
+//   tiles[c][ngrp + t][.] = G_t - mean of its group
+// so that the large dispersion parts that cancel between Zeeman components
+// of one J level are summed once, in FP64, before rounding to the storage type.
+template <typename T>
+__global__ void group_split_kernel(const double* __restrict__ src, T* __restrict__ dst, const int* __restrict__ grp,
+                                   int ncls, int ntrip, int ngrp, int rowlen) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (c, n*2N + col)
+  if (idx >= (long long)ncls * rowlen) return;
+  const int c = (int)(idx / rowlen);
+  const int e = (int)(idx - (long long)c * rowlen);
+  double mean[2] = {0.0, 0.0};
+  int cnt[2] = {0, 0};
+  for (int t = 0; t < ntrip; ++t) {
+    const int g = grp[t];
+    mean[g] += src[((size_t)c * ntrip + t) * rowlen + e];
+    cnt[g] += 1;
+  }
+  for (int g = 0; g < ngrp; ++g) {
+    mean[g] = cnt[g] ? mean[g] / cnt[g] : 0.0;
+    dst[((size_t)c * (ngrp + ntrip) + g) * rowlen + e] = (T)mean[g];
+  }
+  for (int t = 0; t < ntrip; ++t)
+    dst[((size_t)c * (ngrp + ntrip) + ngrp + t) * rowlen + e] =
+        (T)(src[((size_t)c * ntrip + t) * rowlen + e] - mean[grp[t]]);
+}
+
 // -------------------------------------------------------------- launchers
 static int upload_consts(Ctx* c) {
   WeidemanConst wc;
@@ -357,26 +385,36 @@ int launch_tiles(Ctx* c) {
   const size_t smem = (size_t)kRowsPerBlock * 4 * N * sizeof(double);
   const long long rows_per_z = (long long)c->ncls * c->ntrip * N;
   int err = 0;
-  if (c->prec == PRD_FP64) {
-    cudaFuncSetAttribute(tile_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(r3_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  } else {
-    cudaFuncSetAttribute(tile_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(r3_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(tile_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(r3_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(r3_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  DBuf scr, dgrp;
+  if ((rc = dalloc(c, scr, (size_t)rows_per_z * 2 * N * sizeof(double))) ||
+      (rc = upload(c, dgrp, c->trip_grp.data(), c->trip_grp.size() * 4))) {
+    dfree(du); dfree(dQ); dfree(da); dfree(dsh); dfree(dtr); dfree(dth); dfree(dath); dfree(daw); dfree(scr);
+    return rc;
   }
+  const int rowlen = 2 * N * N;     // one tile (n rows of 2N)
+  const size_t ztile = (size_t)c->ncls * c->ntile() * rowlen;
   for (int iz = 0; iz < nz && !err; ++iz) {
     p.z0 = iz;
     const long long nrows = rows_per_z;
     const int blocks = (int)((nrows + kRowsPerBlock - 1) / kRowsPerBlock);
-    if (c->prec == PRD_FP64) {
-      double* base = (double*)c->tiles.p + (size_t)iz * rows_per_z * 2 * N;
-      tile_kernel<double, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(p, base, (int)nrows);
-    } else {
-      float* base = (float*)c->tiles.p + (size_t)iz * rows_per_z * 2 * N;
-      tile_kernel<float, float><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(p, base, (int)nrows);
-    }
+    // W in FP64 in both modes: the per-triple tiles are differenced against
+    // their group mean, so their errors must be far below the storage epsilon
+    tile_kernel<double, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(p, (double*)scr.p, (int)nrows);
+    const int sb = ceil_div((long long)c->ncls * rowlen, 256);
+    if (c->prec == PRD_FP64)
+      group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)c->tiles.p + iz * ztile,
+                                                            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, rowlen);
+    else
+      group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)c->tiles.p + iz * ztile,
+                                                           (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, rowlen);
     if (cudaPeekAtLastError() != cudaSuccess) err = 1;
   }
+  cudaStreamSynchronize(c->stream);
+  dfree(scr);
+  dfree(dgrp);
   if (!err) {
     R3Params q{(const double*)du.p, (const double*)dQ.p, (const double*)da.p, (const double*)dsh.p, N,
                c->nu_st, c->nl_st};
@@ -385,12 +423,71 @@ int launch_tiles(Ctx* c) {
     if (c->prec == PRD_FP64)
       r3_kernel<double, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(q, (double*)c->r3w.p, nz);
     else
-      r3_kernel<float, float><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(q, (float*)c->r3w.p, nz);
+      r3_kernel<float, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(q, (float*)c->r3w.p, nz);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   dfree(du); dfree(dQ); dfree(da); dfree(dsh); dfree(dtr); dfree(dth); dfree(dath); dfree(daw);
   if (err || e != cudaSuccess)
     return fail(c, PRD_E_CUDA, std::string("tile generation: ") + cudaGetErrorString(e != cudaSuccess ? e : cudaGetLastError()));
+  return PRD_OK;
+}
+
+// Angle-averaged tiles and R_III incident weights of the unmagnetised J-level
+// components (shifts shift_g[z][g]) for the preconditioner, returned in FP64.
+int launch_pc_tiles(Ctx* c, const std::vector<double>& shift_g, std::vector<double>& aa_tiles,
+                    std::vector<double>& r3g) {
+  int rc = upload_consts(c);
+  if (rc) return rc;
+  const int nz = c->nz, N = c->nnu, ng = c->ngrp;
+  std::vector<double> x, w, th, tw;
+  gauss_legendre(32, x, w);
+  for (int h = 0; h < 2; ++h) {
+    const double lo = h * 0.5 * kPi, hi = lo + 0.5 * kPi;
+    for (int i = 0; i < 32; ++i) {
+      const double t = 0.5 * (hi - lo) * x[i] + 0.5 * (hi + lo);
+      th.push_back(t);
+      tw.push_back(0.5 * 0.5 * (hi - lo) * w[i] * std::sin(t));
+    }
+  }
+  std::vector<int> trip;
+  for (int g = 0; g < ng; ++g) { trip.push_back(g); trip.push_back(0); trip.push_back(0); }
+  const double th0 = 0.0;
+  DBuf du, dQ, da, dsh, dtr, dth, dath, daw, out, out3;
+  auto cleanup = [&]() { dfree(du); dfree(dQ); dfree(da); dfree(dsh); dfree(dtr); dfree(dth); dfree(dath);
+                         dfree(daw); dfree(out); dfree(out3); };
+  const long long rows_per_z = (long long)ng * N;
+  if ((rc = upload(c, du, c->u.data(), c->u.size() * 8)) || (rc = upload(c, dQ, c->Q.data(), c->Q.size() * 8)) ||
+      (rc = upload(c, da, c->a.data(), nz * 8)) || (rc = upload(c, dsh, shift_g.data(), shift_g.size() * 8)) ||
+      (rc = upload(c, dtr, trip.data(), trip.size() * 4)) || (rc = upload(c, dth, &th0, 8)) ||
+      (rc = upload(c, dath, th.data(), th.size() * 8)) || (rc = upload(c, daw, tw.data(), tw.size() * 8)) ||
+      (rc = dalloc(c, out, (size_t)nz * rows_per_z * 2 * N * 8)) ||
+      (rc = dalloc(c, out3, (size_t)nz * ng * ng * 2 * N * 8))) {
+    cleanup();
+    return rc;
+  }
+  TileParams p{(const double*)du.p, (const double*)dQ.p, (const double*)da.p, (const double*)dsh.p,
+               (const int*)dtr.p, (const double*)dth.p, (const double*)dath.p, (const double*)daw.p,
+               (int)th.size(), N, ng, 1, ng, 1, 0, 1};
+  const size_t smem = (size_t)kRowsPerBlock * 4 * N * sizeof(double);
+  cudaFuncSetAttribute(tile_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(r3_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  for (int iz = 0; iz < nz; ++iz) {
+    p.z0 = iz;
+    tile_kernel<double, double><<<ceil_div(rows_per_z, kRowsPerBlock), 32 * kRowsPerBlock, smem, c->stream>>>(
+        p, (double*)out.p + (size_t)iz * rows_per_z * 2 * N, (int)rows_per_z);
+  }
+  R3Params q{(const double*)du.p, (const double*)dQ.p, (const double*)da.p, (const double*)dsh.p, N, ng, 1};
+  r3_kernel<double, double><<<ceil_div((long long)nz * ng * ng, kRowsPerBlock), 32 * kRowsPerBlock, smem,
+                              c->stream>>>(q, (double*)out3.p, nz);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) {
+    aa_tiles.resize((size_t)nz * rows_per_z * 2 * N);
+    r3g.resize((size_t)nz * ng * ng * 2 * N);
+    e = cudaMemcpy(aa_tiles.data(), out.p, aa_tiles.size() * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(r3g.data(), out3.p, r3g.size() * 8, cudaMemcpyDeviceToHost);
+  }
+  cleanup();
+  if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("preconditioner tiles: ") + cudaGetErrorString(e));
   return PRD_OK;
 }
 

@@ -61,6 +61,12 @@ struct Ctx {
   int nu_st = 0, nl_st = 0;             // upper / lower states
   int ntrip = 0;                         // R_II triples (k, kl, kl')
   std::vector<int> trip_k, trip_l, trip_lp;
+  // Tiles are stored as one mean tile per group of triples whose upper state
+  // belongs to the same J level, followed by each triple's deviation from it
+  // (tile index ti < ngrp: group mean; ti = ngrp + t: deviation of triple t).
+  int ngrp = 1;
+  std::vector<int> trip_grp;
+  int ntile() const { return ngrp + ntrip; }
   int nq3 = 0;                           // R_III incident combos (ku, kv, kl)
   double nu0 = 0;
   std::vector<double> dnuD, vD;          // per z (Hz, km/s)
@@ -101,6 +107,7 @@ struct Ctx {
   DBuf pc_delo;      // [z][o][n][3] (T)
   DBuf pc_s1, pc_s2, pc_s3;   // scalar N/4 scratch
   std::vector<double> pc_lii_host;
+  void* pc_w = nullptr;   // device angular weights (double), owned via `owned`
   // GMRES
   std::vector<DBuf> krylov;
   DBuf gm_w, gm_r, gm_t, gm_dots;
@@ -126,6 +133,7 @@ int upload(Ctx* c, DBuf& b, const void* host, size_t bytes);
 cplx faddeeva_host(cplx z);
 void weideman_coeffs(int n, double* a_out, double* L_out);
 void natural_spline_Q(const double* u, int n, double* Q);
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 
 // ---- setup pieces (host_setup.cpp)
 int build_host_tables(Ctx* c);

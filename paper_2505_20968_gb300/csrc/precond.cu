@@ -1,14 +1,254 @@
-// Physics-based preconditioner P = Id - Lambda* Sigma* (Sect. 5.2, App. F).
+// Physics-based preconditioner P = Id - Lambda* Sigma* (Sect. 5.2) with the
+// block-diagonal inner preconditioner of App. F.
+//
+//  Sigma*: unpolarised, unmagnetised PRD-AA on Stokes I only (K = Q = 0):
+//     eps_bar*(z,u) = k [alpha0 sum_g c_g r_AA(u'+s_g, u+s_g) + (beta0-alpha0) phi*(u) phi*(u')] J_bar(u')
+//     with J_bar the angle average of the comoving I, r_AA = (1/pi) 1/2 int sin(Theta) Re F dTheta
+//     (Eq. R_AA), c_g the J-level weights (2J+1)/(2(2L+1)) and phi* = sum_g c_g H(a,u+s_g)/sqrt(pi);
+//     eps* = eps_bar* back in the observer frame.  Lambda*: scalar DELO-linear with eta_I.
+//  P^-1 y: m_in Richardson sweeps x <- x + P_hat^-1 (y - P x) from x = 0, with
+//     P_hat_i^-1 = Id + Lambda_ii Phi_bar_i (Id - A_i)^-1 Phi^Omega,  A_i = Phi^Omega Lambda_ii Phi_bar_i
+//     (App. F, without the frame-change interpolations inside P_hat).
+//  Q, U, V pass through unchanged (P is the identity there).
+#include <cmath>
+#include <vector>
 #include "prd_internal.h"
 #include "device_common.cuh"
 
 namespace prd {
 
-int launch_precond_setup(Ctx* c) { return PRD_OK; }
+int launch_pc_tiles(Ctx* c, const std::vector<double>& shift_g, std::vector<double>& aa_tiles,
+                    std::vector<double>& r3g);
+
+// J[z][m] = sum_o w_o X[z][o][m][0]
+template <typename T>
+__global__ void pc_angle_avg_kernel(const T* __restrict__ X, const double* __restrict__ w, T* __restrict__ J, int nz,
+                                    int nO, int N) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nz * N) return;
+  const int iz = idx / N, m = idx - iz * N;
+  double s = 0.0;
+  for (int o = 0; o < nO; ++o) s += w[o] * (double)X[(((size_t)iz * nO + o) * N + m) * 4];
+  J[idx] = (T)s;
+}
+
+// V[z][o][n][0] = sum_m A[z][n][m] J[z][m]  (broadcast over o; Q,U,V zero)
+template <typename T>
+__global__ void pc_matvec_bcast_kernel(const T* __restrict__ A, const T* __restrict__ J, T* __restrict__ V, int nz,
+                                       int nO, int N) {
+  const int iz = blockIdx.y;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const T* a = A + ((size_t)iz * N + n) * N;
+  const T* j = J + (size_t)iz * N;
+  double s = 0.0;
+  for (int m = 0; m < N; ++m) s += (double)a[m] * (double)j[m];
+  for (int o = 0; o < nO; ++o) {
+    T* v = V + (((size_t)iz * nO + o) * N + n) * 4;
+    v[0] = (T)s;
+    v[1] = v[2] = v[3] = (T)0;
+  }
+}
+
+// Scalar DELO-linear sweep of Stokes I: out = Lambda* eps (zero boundary).
+template <typename T>
+__global__ void pc_delo_kernel(const T* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
+                               T* __restrict__ out, int nz, int nO, int N) {
+  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ray >= nO * N) return;
+  const int o = ray / N, n = ray - o * N;
+  const bool up = mu[o] > 0.0;
+  T I = 0, Sp = 0;
+  for (int p = 0; p < nz; ++p) {
+    const int k = up ? p : nz - 1 - p;
+    const size_t pt = ((size_t)k * nO + o) * N + n;
+    const T* t = kt + pt * 10;
+    const T S = eps[pt * 4] * t[6];
+    if (p == 0) I = 0;
+    else I = t[7] * I + t[8] * Sp + t[9] * S;
+    out[pt * 4] = I;
+    Sp = S;
+  }
+}
+
+// x[.][0] += r[.][0] + lii * v[.][0]  (Richardson update with P_hat^-1)
+template <typename T>
+__global__ void pc_update_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict__ lii,
+                                 const T* __restrict__ v, long long npt) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npt) return;
+  x[pt * 4] += r[pt * 4] + lii[pt] * v[pt * 4];
+}
+
+// r[.][0] = y[.][0] - x[.][0] + LS[.][0]   (residual of P x = y on Stokes I)
+template <typename T>
+__global__ void pc_resid_kernel(const T* __restrict__ y, const T* __restrict__ x, const T* __restrict__ ls,
+                                T* __restrict__ r, long long npt) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npt) return;
+  r[pt * 4] = y[pt * 4] - x[pt * 4] + ls[pt * 4];
+}
+
+template <typename T>
+__global__ void pc_init_kernel(const T* __restrict__ y, T* __restrict__ x, long long npt) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npt) return;
+  x[pt * 4] = 0;
+  x[pt * 4 + 1] = y[pt * 4 + 1];
+  x[pt * 4 + 2] = y[pt * 4 + 2];
+  x[pt * 4 + 3] = y[pt * 4 + 3];
+}
+
+// spline kernels from kernels_apply.cu
+int spline_frame_change(Ctx* c, const void* in, void* out, bool to_comoving);
+
+static int lu_inverse(std::vector<double>& A, int n) {
+  std::vector<int> piv(n);
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * n + k]) > std::fabs(A[(size_t)p * n + k])) p = i;
+    piv[k] = p;
+    if (A[(size_t)p * n + k] == 0.0) return -1;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+    for (int i = k + 1; i < n; ++i) {
+      const double f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      A[(size_t)i * n + k] = f;
+      for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+    }
+  }
+  for (int col = 0; col < n; ++col) {
+    std::vector<double> b(n, 0.0);
+    b[col] = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) b[i] -= A[(size_t)i * n + j] * b[j];
+    for (int i = n - 1; i >= 0; --i) {
+      for (int j = i + 1; j < n; ++j) b[i] -= A[(size_t)i * n + j] * b[j];
+      b[i] /= A[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + col] = b[i];
+  }
+  A.swap(inv);
+  return 0;
+}
+
+int launch_precond_setup(Ctx* c) {
+  const int nz = c->nz, N = c->nnu, nO = c->nO, ng = c->ngrp;
+  // J-level shifts at B = 0 and weights
+  std::vector<double> sg((size_t)nz * ng), cg(ng);
+  const prd_atom& at = c->atom;
+  for (int g = 0; g < ng; ++g) {
+    const double E = (at.twoS == 0 ? at.E_u_cm[0] : at.E_u_cm[g]) * kCmToHz - c->nu0;
+    cg[g] = (at.twoS == 0) ? 1.0 : (g == 0 ? 1.0 / 3.0 : 2.0 / 3.0);
+    for (int iz = 0; iz < nz; ++iz) sg[(size_t)iz * ng + g] = E / c->dnuD[iz];
+  }
+  std::vector<double> aa, r3;   // aa: [z][g][N][2N]; r3: [z][g*g][2N]
+  int rc = launch_pc_tiles(c, sg, aa, r3);
+  if (rc) return rc;
+  std::vector<double> phi((size_t)nz * N * N), Mm((size_t)nz * N * N);
+  std::vector<int> bad(nz, 0);
+#pragma omp parallel for schedule(dynamic)
+  for (int iz = 0; iz < nz; ++iz) {
+    const double a0 = (1.0 - c->eps[iz]) * (1.0 - c->rE[iz]);
+    const double b0 = 1.0 - c->eps[iz];
+    std::vector<double> ph(N), rs(N, 0.0);
+    for (int n = 0; n < N; ++n) {
+      double s = 0.0;
+      for (int g = 0; g < ng; ++g)
+        s += cg[g] * faddeeva_host(cplx(c->u[(size_t)iz * N + n] + sg[(size_t)iz * ng + g], c->a[iz])).real() / kSqrtPi;
+      ph[n] = s;
+    }
+    for (int g = 0; g < ng; ++g) {
+      const double* rr = &r3[((size_t)iz * ng * ng + g * ng + g) * 2 * N];
+      for (int m = 0; m < N; ++m) rs[m] += cg[g] * rr[m] / (2.0 * kSqrtPi);
+    }
+    double* P = &phi[(size_t)iz * N * N];
+    for (int n = 0; n < N; ++n)
+      for (int m = 0; m < N; ++m) {
+        double v = 0.0;
+        for (int g = 0; g < ng; ++g) v += cg[g] * aa[(((size_t)iz * ng + g) * N + n) * 2 * N + m] / kPi;
+        P[(size_t)n * N + m] = c->k[iz] * (a0 * v + (b0 - a0) * ph[n] * rs[m]);
+      }
+    // lambda_bar(n) = sum_o w_o Lambda_ii(z, o, n)
+    std::vector<double> lb(N, 0.0);
+    for (int o = 0; o < nO; ++o)
+      for (int n = 0; n < N; ++n) lb[n] += c->wang[o] * c->pc_lii_host[((size_t)iz * nO + o) * N + n];
+    std::vector<double> A((size_t)N * N);
+    for (int n = 0; n < N; ++n)
+      for (int m = 0; m < N; ++m) A[(size_t)n * N + m] = (n == m ? 1.0 : 0.0) - lb[n] * P[(size_t)n * N + m];
+    if (lu_inverse(A, N)) { bad[iz] = 1; continue; }
+    double* Mz = &Mm[(size_t)iz * N * N];
+    for (int n = 0; n < N; ++n)
+      for (int m = 0; m < N; ++m) {
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) s += P[(size_t)n * N + k] * A[(size_t)k * N + m];
+        Mz[(size_t)n * N + m] = s;
+      }
+  }
+  for (int iz = 0; iz < nz; ++iz)
+    if (bad[iz]) return fail(c, PRD_E_ARG, "block-Jacobi matrix (Id - A_i) is singular at height " + std::to_string(iz));
+  auto up = [&](DBuf& b, const std::vector<double>& v) {
+    if (c->prec == PRD_FP64) return upload(c, b, v.data(), v.size() * 8);
+    std::vector<float> f(v.begin(), v.end());
+    return upload(c, b, f.data(), f.size() * 4);
+  };
+  if ((rc = up(c->pc_phi, phi)) || (rc = up(c->pc_M, Mm))) return rc;
+  DBuf w;
+  if ((rc = upload(c, w, c->wang.data(), nO * 8))) return rc;
+  c->owned.push_back(w.p);   // angular weights (double), freed with the ctx
+  c->pc_w = w.p;
+  const size_t vb = nvec(c) * c->esz;
+  if ((rc = dalloc(c, c->pc_s1, vb)) || (rc = dalloc(c, c->pc_s2, vb)) || (rc = dalloc(c, c->pc_s3, vb)) ||
+      (rc = dalloc(c, c->gm_w, (size_t)nz * N * c->esz)))
+    return rc;
+  return PRD_OK;
+}
+
+template <typename T>
+static int precond_T(Ctx* c, const T* y, T* x) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const long long npt = (long long)nz * nO * N;
+  T* r = (T*)c->pc_s1.p;
+  T* t1 = (T*)c->pc_s2.p;
+  T* t2 = (T*)c->pc_s3.p;
+  T* J = (T*)c->gm_w.p;
+  const double* w = (const double*)c->pc_w;
+  const int g1 = ceil_div(npt, 256);
+  pc_init_kernel<T><<<g1, 256, 0, c->stream>>>(y, x, npt);
+  for (int sweep = 0; sweep < c->m_in; ++sweep) {
+    // r = y - P x on Stokes I (P x = x - Lambda* Sigma* x)
+    if (sweep == 0) {
+      PRD_CUDA_TRY(c, cudaMemcpyAsync(r, y, nvec(c) * c->esz, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      int rc = spline_frame_change(c, x, t1, true);                       // comoving I~
+      if (rc) return rc;
+      pc_angle_avg_kernel<T><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>(t1, w, J, nz, nO, N);
+      pc_matvec_bcast_kernel<T><<<dim3(ceil_div(N, 128), nz), 128, 0, c->stream>>>((const T*)c->pc_phi.p, J, t2, nz, nO, N);
+      if ((rc = spline_frame_change(c, t2, t1, false))) return rc;       // eps* (observer)
+      pc_delo_kernel<T><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>(t1, (const T*)c->kt.p, (const double*)c->dmu.p, t2,
+                                                                      nz, nO, N);
+      pc_resid_kernel<T><<<g1, 256, 0, c->stream>>>(y, x, t2, r, npt);
+    }
+    // x += P_hat^-1 r
+    pc_angle_avg_kernel<T><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>(r, w, J, nz, nO, N);
+    pc_matvec_bcast_kernel<T><<<dim3(ceil_div(N, 128), nz), 128, 0, c->stream>>>((const T*)c->pc_M.p, J, t2, nz, nO, N);
+    pc_update_kernel<T><<<g1, 256, 0, c->stream>>>(x, r, (const T*)c->pc_lii.p, t2, npt);
+  }
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
 
 int apply_precond(Ctx* c, const void* y, void* x) {
-  PRD_CUDA_TRY(c, cudaMemcpyAsync(x, y, nvec(c) * c->esz, cudaMemcpyDeviceToDevice, c->stream));
-  return PRD_OK;
+  if (c->m_in <= 0) {
+    PRD_CUDA_TRY(c, cudaMemcpyAsync(x, y, nvec(c) * c->esz, cudaMemcpyDeviceToDevice, c->stream));
+    return PRD_OK;
+  }
+  if (c->prec == PRD_FP64) return precond_T<double>(c, (const double*)y, (double*)x);
+  return precond_T<float>(c, (const float*)y, (float*)x);
 }
 
 int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, void* out) {
