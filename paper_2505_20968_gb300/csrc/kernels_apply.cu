@@ -127,9 +127,9 @@ __global__ void r3_J_kernel(const T* __restrict__ Ic, const T* __restrict__ r3w,
 }
 
 // eps_bar[z][o][n][i] = Re sum_uv ab[uv] J[uv] sum_kl' O_i(o; uv, kl') prof[uv][kl'][n]
-template <typename T>
+template <typename T, typename A>
 __global__ void r3_out_kernel(const double* __restrict__ J, const T* __restrict__ ab, const T* __restrict__ rout,
-                              const T* __restrict__ prof, T* __restrict__ eb, int nz, int nO, int N, int nuv,
+                              const T* __restrict__ prof, A* __restrict__ eb, int nz, int nO, int N, int nuv,
                               int nl) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= (long long)nz * nO * N) return;
@@ -149,8 +149,8 @@ __global__ void r3_out_kernel(const double* __restrict__ J, const T* __restrict_
       for (int i = 0; i < 4; ++i) acc[i] += (double)ro[2 * i] * dr - (double)ro[2 * i + 1] * di;
     }
   }
-  T* o = eb + pt * 4;
-  for (int i = 0; i < 4; ++i) o[i] = (T)acc[i];
+  A* o = eb + pt * 4;
+  for (int i = 0; i < 4; ++i) o[i] = (A)acc[i];
 }
 
 // ------------------------------------------------------------------ R_II (SIMT)
@@ -163,10 +163,10 @@ constexpr int kCW = 16;      // output directions per CTA
 constexpr int kMB = 16;      // incident-frequency block
 constexpr int kMaxRows = 16; // rows per thread (N <= 256)
 
-template <typename T>
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tiles, const T* __restrict__ Y,
                                                       const T* __restrict__ Ic, const int* __restrict__ cls,
-                                                      T* __restrict__ eb, int ncls, int ntrip, int nO, int N,
+                                                      A* __restrict__ eb, int ncls, int ntrip, int nO, int N,
                                                       int npairs) {
   const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
   const int* cout_ptr = cls;
@@ -178,17 +178,17 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
   const int e_end = cout_ptr[c + 1];
   if (e0 >= e_end) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T (*Zs)[2][kCW * 4] = reinterpret_cast<T (*)[2][kCW * 4]>(smraw);
-  T* Asb = reinterpret_cast<T*>(smraw + sizeof(T) * kMB * 2 * kCW * 4);
+  A (*Zs)[2][kCW * 4] = reinterpret_cast<A (*)[2][kCW * 4]>(smraw);
+  T* Asb = reinterpret_cast<T*>(smraw + sizeof(A) * kMB * 2 * kCW * 4);
   // As[h][n][mm] -> Asb[(h * N + n) * (kMB + 1) + mm]
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int e_mine = e0 + tx;
-  T acc[kMaxRows][4];
+  A acc[kMaxRows][4];
 #pragma unroll
   for (int r = 0; r < kMaxRows; ++r)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[r][i] = (T)0;
+    for (int i = 0; i < 4; ++i) acc[r][i] = (A)0;
   const int nrows = (N + 15) / 16;
   const size_t tile_sz = (size_t)N * 2 * N;
   const T* tbase = tiles + ((size_t)iz * ncls + c) * ntrip * tile_sz;
@@ -201,18 +201,18 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
       // ---- Z block
       {
         const int m = m0 + zm;
-        T zr[4] = {0, 0, 0, 0}, zi[4] = {0, 0, 0, 0};
+        A zr[4] = {0, 0, 0, 0}, zi[4] = {0, 0, 0, 0};
         if (e_z < e_end && m < N) {
           for (int p = pair_ptr[e_z]; p < pair_ptr[e_z + 1]; ++p) {
             const int op = pair_in[p];
             const T* iv = Ic + (((size_t)iz * nO + op) * N + m) * 4;
             const T* y = Y + (((size_t)iz * npairs + p) * ntrip + t) * 32;
-            const T i0 = iv[0], i1 = iv[1], i2 = iv[2], i3 = iv[3];
+            const A i0 = iv[0], i1 = iv[1], i2 = iv[2], i3 = iv[3];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
               const T* yi = y + i * 8;
-              zr[i] += yi[0] * i0 + yi[2] * i1 + yi[4] * i2 + yi[6] * i3;
-              zi[i] += yi[1] * i0 + yi[3] * i1 + yi[5] * i2 + yi[7] * i3;
+              zr[i] += (A)yi[0] * i0 + (A)yi[2] * i1 + (A)yi[4] * i2 + (A)yi[6] * i3;
+              zi[i] += (A)yi[1] * i0 + (A)yi[3] * i1 + (A)yi[5] * i2 + (A)yi[7] * i3;
             }
           }
         }
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
       __syncthreads();
 #pragma unroll 4
       for (int mm = 0; mm < kMB; ++mm) {
-        T zr[4], zi[4];
+        A zr[4], zi[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           zr[i] = Zs[mm][0][tx * 4 + i];
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
           if (r < nrows) {
             const int n = ty + 16 * r;
             if (n < N) {
-              const T ar = Asb[n * (kMB + 1) + mm], ai = Asb[(N + n) * (kMB + 1) + mm];
+              const A ar = Asb[n * (kMB + 1) + mm], ai = Asb[(N + n) * (kMB + 1) + mm];
 #pragma unroll
               for (int i = 0; i < 4; ++i) acc[r][i] += ar * zr[i] - ai * zi[i];
             }
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
     for (int r = 0; r < kMaxRows; ++r) {
       const int n = ty + 16 * r;
       if (r < nrows && n < N) {
-        T* dst = eb + (((size_t)iz * nO + o) * N + n) * 4;
+        A* dst = eb + (((size_t)iz * nO + o) * N + n) * 4;
 #pragma unroll
         for (int i = 0; i < 4; ++i) atomicAdd(dst + i, acc[r][i]);
       }
@@ -341,8 +341,8 @@ __global__ void delo_kernel(const T* __restrict__ eps, const T* __restrict__ kt,
   }
 }
 
-template <typename T>
-__global__ void normalise_kernel(const T* __restrict__ num, const T* __restrict__ kt, const double* __restrict__ fac,
+template <typename A, typename T>
+__global__ void normalise_kernel(const A* __restrict__ num, const T* __restrict__ kt, const double* __restrict__ fac,
                                  T* __restrict__ f, int nz, int nO, int N) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= (long long)nz * nO * N) return;
@@ -361,13 +361,14 @@ __global__ void fill_planck_kernel(T* __restrict__ x, const double* __restrict__
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T>
-static int sigma_T(Ctx* c, const T* x, T* eps, bool normalised) {
+template <typename T, typename A>
+static int sigma_T(Ctx* c, const T* x, A* eps, bool normalised, A* eb_ext = nullptr, A* M_ext = nullptr) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
   T* M = (T*)c->scratch1.p;
   T* Ic = (T*)c->scratch2.p;
-  T* eb = (T*)c->scratch3.p;
+  A* eb = eb_ext ? eb_ext : (A*)c->scratch3.p;
+  A* Mb = M_ext ? M_ext : (A*)c->scratch1.p;
   const double* sp = (const double*)c->sp.p;
   // S1
   spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, M, sp, nz, nO, N);
@@ -378,19 +379,19 @@ static int sigma_T(Ctx* c, const T* x, T* eps, bool normalised) {
   PRD_CUDA_TRY(c, cudaMemsetAsync(c->r3J.p, 0, c->r3J.bytes, c->stream));
   r3_J_kernel<T><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
                                                         (double*)c->r3J.p, nO, N, nq, c->nl_st);
-  r3_out_kernel<T><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)c->r3J.p, (const T*)c->r3ab.p,
+  r3_out_kernel<T, A><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)c->r3J.p, (const T*)c->r3ab.p,
                                                                (const T*)c->r3out.p, (const T*)c->r3prof.p, eb, nz,
                                                                nO, N, nuv, c->nl_st);
   // S3 + S4
   const int nchunk = (c->max_cout + kCW - 1) / kCW;
-  const size_t smem = sizeof(T) * ((size_t)kMB * 2 * kCW * 4 + (size_t)2 * N * (kMB + 1));
-  cudaFuncSetAttribute(r2_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  r2_simt_kernel<T><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
+  const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
+  cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
       (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
   // S6
-  spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, M, sp, nz, nO, N);
-  spline_eval_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, M, (const int*)c->ibk.p, (const double*)c->tbk.p,
-                                                                  sp, normalised ? (const T*)c->f.p : nullptr, eps, nz,
+  spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, Mb, sp, nz, nO, N);
+  spline_eval_kernel<A><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, Mb, (const int*)c->ibk.p, (const double*)c->tbk.p,
+                                                                  sp, normalised ? (const A*)c->f.p : nullptr, eps, nz,
                                                                   nO, N);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
@@ -418,8 +419,8 @@ int spline_frame_change(Ctx* c, const void* in, void* out, bool to_comoving) {
 }
 
 int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised) {
-  if (c->prec == PRD_FP64) return sigma_T<double>(c, (const double*)x, (double*)eps, normalised);
-  return sigma_T<float>(c, (const float*)x, (float*)eps, normalised);
+  if (c->prec == PRD_FP64) return sigma_T<double, double>(c, (const double*)x, (double*)eps, normalised);
+  return sigma_T<float, float>(c, (const float*)x, (float*)eps, normalised);
 }
 
 int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool boundary) {
@@ -437,33 +438,40 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
   return PRD_OK;
 }
 
+// Kirchhoff factor f = (1-eps) W_T eta_I / [Sigma (W_T,0,0,0)]_I (App. E).  In
+// FP32 mode the unnormalised Sigma is applied to the Planck field with FP64
+// accumulation over the operator's own FP32-stored tables, so that f corrects
+// the photon budget of exactly the matrix used at apply time.
 int compute_normalisation(Ctx* c) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
-  DBuf wt, fac, xin, num;
+  DBuf wt, fac, xin, num, eb, Mb;
   std::vector<double> f(nz);
   for (int iz = 0; iz < nz; ++iz) f[iz] = (1.0 - c->eps[iz]) * c->WT[iz];
   int rc;
+  const size_t vb64 = nvec(c) * 8;
+  auto cleanup = [&]() { dfree(wt); dfree(fac); dfree(xin); dfree(num); dfree(eb); dfree(Mb); };
   if ((rc = upload(c, wt, c->WT.data(), nz * 8)) || (rc = upload(c, fac, f.data(), nz * 8)) ||
-      (rc = dalloc(c, xin, nvec(c) * c->esz)) || (rc = dalloc(c, num, nvec(c) * c->esz))) {
-    dfree(wt); dfree(fac); dfree(xin); dfree(num);
+      (rc = dalloc(c, xin, nvec(c) * c->esz)) || (rc = dalloc(c, num, vb64)) || (rc = dalloc(c, eb, vb64)) ||
+      (rc = dalloc(c, Mb, vb64))) {
+    cleanup();
     return rc;
   }
   if (c->prec == PRD_FP64) {
     fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
-    rc = apply_sigma(c, xin.p, num.p, false);
+    rc = sigma_T<double, double>(c, (const double*)xin.p, (double*)num.p, false);
     if (!rc)
-      normalise_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const double*)num.p, (const double*)c->kt.p,
-                                                                           (const double*)fac.p, (double*)c->f.p, nz, nO, N);
+      normalise_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const double*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
   } else {
     fill_planck_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((float*)xin.p, (const double*)wt.p, nz, nO, N);
-    rc = apply_sigma(c, xin.p, num.p, false);
+    rc = sigma_T<float, double>(c, (const float*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p);
     if (!rc)
-      normalise_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const float*)num.p, (const float*)c->kt.p,
-                                                                          (const double*)fac.p, (float*)c->f.p, nz, nO, N);
+      normalise_kernel<double, float><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const float*)c->kt.p, (const double*)fac.p, (float*)c->f.p, nz, nO, N);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  dfree(wt); dfree(fac); dfree(xin); dfree(num);
+  cleanup();
   if (rc) return rc;
   if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("normalisation: ") + cudaGetErrorString(e));
   return PRD_OK;
