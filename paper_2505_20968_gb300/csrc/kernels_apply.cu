@@ -57,10 +57,10 @@ template <> struct V4<double> { using type = double4; };
 
 // Evaluate the spline of every (z, Omega) row at the tabulated points; the
 // intensity component is multiplied by fI (nullable).
-template <typename T>
+template <typename T, typename F = T>
 __global__ void spline_eval_kernel(const T* __restrict__ y, const T* __restrict__ M, const int* __restrict__ kidx,
                                    const double* __restrict__ tt, const double* __restrict__ sp,
-                                   const T* __restrict__ fI, T* __restrict__ out, int nz, int nO, int N) {
+                                   const F* __restrict__ fI, T* __restrict__ out, int nz, int nO, int N) {
   using V = typename V4<T>::type;
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (z, o, n)
   if (pt >= (long long)nz * nO * N) return;
@@ -82,21 +82,21 @@ __global__ void spline_eval_kernel(const T* __restrict__ y, const T* __restrict_
     r.z = c0 * a.z + c1 * b.z + c2 * ma.z + c3 * mb.z;
     r.w = c0 * a.w + c1 * b.w + c2 * ma.w + c3 * mb.w;
   }
-  if (fI) r.x *= fI[pt];
+  if (fI) r.x *= (T)fI[pt];
   reinterpret_cast<V*>(out)[pt] = r;
 }
 
 // ------------------------------------------------------------------ R_III
 // J[z][ku kv] += sum_{o', j} rin[z][o'][q][j] * sum_m r3w[z][q][m] I~[z][o'][m][j]
-template <typename T>
-__global__ void r3_J_kernel(const T* __restrict__ Ic, const T* __restrict__ r3w, const T* __restrict__ rin,
+template <typename T, typename A>
+__global__ void r3_J_kernel(const A* __restrict__ Ic, const T* __restrict__ r3w, const T* __restrict__ rin,
                             double* __restrict__ J, int nO, int N, int nq, int nl) {
   const int q = blockIdx.x, iz = blockIdx.y;
   const T* w = r3w + ((size_t)iz * nq + q) * 2 * N;
   double accr = 0.0, acci = 0.0;
   for (int idx = threadIdx.x; idx < nO * N; idx += blockDim.x) {
     const int o = idx / N, m = idx - o * N;
-    const T* iv = Ic + (((size_t)iz * nO + o) * N + m) * 4;
+    const A* iv = Ic + (((size_t)iz * nO + o) * N + m) * 4;
     const T* ri = rin + (((size_t)iz * nO + o) * nq + q) * 8;
     const double wr = (double)w[m], wi = (double)w[N + m];
     double sr = 0.0, si = 0.0;
@@ -165,7 +165,7 @@ constexpr int kMaxRows = 16; // rows per thread (N <= 256)
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tiles, const T* __restrict__ Y,
-                                                      const T* __restrict__ Ic, const int* __restrict__ cls,
+                                                      const A* __restrict__ Ic, const int* __restrict__ cls,
                                                       A* __restrict__ eb, int ncls, int ntrip, int nO, int N,
                                                       int npairs) {
   const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
         if (e_z < e_end && m < N) {
           for (int p = pair_ptr[e_z]; p < pair_ptr[e_z + 1]; ++p) {
             const int op = pair_in[p];
-            const T* iv = Ic + (((size_t)iz * nO + op) * N + m) * 4;
+            const A* iv = Ic + (((size_t)iz * nO + op) * N + m) * 4;
             const T* y = Y + (((size_t)iz * npairs + p) * ntrip + t) * 32;
             const A i0 = iv[0], i1 = iv[1], i2 = iv[2], i3 = iv[3];
 #pragma unroll
@@ -271,8 +271,8 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
 // ------------------------------------------------------------------ DELO
 // One thread per ray (Omega, nu): I_k = (Id + b K'_k)^-1 [(e Id - a K'_{k-1}) I_{k-1}
 //   + a S_{k-1} + b S_k], S = eps/eta1, K' = K/eta1 - Id.  Optional: out = x - I.
-template <typename T>
-__device__ __forceinline__ void kprime(const T* t, T K[4][4]) {
+template <typename T, typename A>
+__device__ __forceinline__ void kprime(const T* t, A K[4][4]) {
   K[0][0] = 0; K[1][1] = 0; K[2][2] = 0; K[3][3] = 0;
   K[0][1] = K[1][0] = t[0];
   K[0][2] = K[2][0] = t[1];
@@ -282,53 +282,53 @@ __device__ __forceinline__ void kprime(const T* t, T K[4][4]) {
   K[2][3] = t[5]; K[3][2] = -t[5];
 }
 
-template <typename T>
-__global__ void delo_kernel(const T* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
-                            const T* __restrict__ x_sub, T* __restrict__ out, int nz, int nO, int N, int boundary,
+template <typename T, typename A>
+__global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
+                            const A* __restrict__ x_sub, A* __restrict__ out, int nz, int nO, int N, int boundary,
                             double WT0) {
   const int ray = blockIdx.x * blockDim.x + threadIdx.x;
   if (ray >= nO * N) return;
   const int o = ray / N, n = ray - o * N;
   const bool up = mu[o] > 0.0;
-  T I[4] = {0, 0, 0, 0};
-  T Sp[4] = {0, 0, 0, 0};
-  T Kp[4][4];
+  A I[4] = {0, 0, 0, 0};
+  A Sp[4] = {0, 0, 0, 0};
+  A Kp[4][4];
   for (int p = 0; p < nz; ++p) {
     const int k = up ? p : nz - 1 - p;
     const size_t pt = ((size_t)k * nO + o) * N + n;
     const T* t = kt + pt * 10;
-    T Kk[4][4];
+    A Kk[4][4];
     kprime(t, Kk);
-    const T ie = t[6];
-    T S[4];
+    const A ie = t[6];
+    A S[4];
     for (int s = 0; s < 4; ++s) S[s] = eps[pt * 4 + s] * ie;
     if (p == 0) {
-      I[0] = (boundary && up) ? (T)WT0 : (T)0;
-      I[1] = I[2] = I[3] = (T)0;
+      I[0] = (boundary && up) ? (A)WT0 : (A)0;
+      I[1] = I[2] = I[3] = (A)0;
     } else {
-      const T e = t[7], al = t[8], be = t[9];
-      T rhs[4];
+      const A e = t[7], al = t[8], be = t[9];
+      A rhs[4];
       for (int i = 0; i < 4; ++i) {
-        T v = e * I[i] + al * Sp[i] + be * S[i];
+        A v = e * I[i] + al * Sp[i] + be * S[i];
         for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j];
         rhs[i] = v;
       }
-      T A[4][4];
+      A M4[4][4];
       for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) A[i][j] = (i == j ? (T)1 : (T)0) + be * Kk[i][j];
+        for (int j = 0; j < 4; ++j) M4[i][j] = (i == j ? (A)1 : (A)0) + be * Kk[i][j];
       // Gaussian elimination without pivoting (symmetric part positive definite)
       for (int c0 = 0; c0 < 4; ++c0) {
-        const T inv = (T)1 / A[c0][c0];
+        const A inv = (A)1 / M4[c0][c0];
         for (int r = c0 + 1; r < 4; ++r) {
-          const T f = A[r][c0] * inv;
-          for (int cc = c0; cc < 4; ++cc) A[r][cc] -= f * A[c0][cc];
+          const A f = M4[r][c0] * inv;
+          for (int cc = c0; cc < 4; ++cc) M4[r][cc] -= f * M4[c0][cc];
           rhs[r] -= f * rhs[c0];
         }
       }
       for (int r = 3; r >= 0; --r) {
-        T v = rhs[r];
-        for (int cc = r + 1; cc < 4; ++cc) v -= A[r][cc] * I[cc];
-        I[r] = v / A[r][r];
+        A v = rhs[r];
+        for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * I[cc];
+        I[r] = v / M4[r][r];
       }
     }
     for (int s = 0; s < 4; ++s) {
@@ -362,22 +362,23 @@ __global__ void fill_planck_kernel(T* __restrict__ x, const double* __restrict__
 
 // ------------------------------------------------------------------ launchers
 template <typename T, typename A>
-static int sigma_T(Ctx* c, const T* x, A* eps, bool normalised, A* eb_ext = nullptr, A* M_ext = nullptr) {
+static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = nullptr, A* M_ext = nullptr,
+                   A* Ic_ext = nullptr) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
-  T* M = (T*)c->scratch1.p;
-  T* Ic = (T*)c->scratch2.p;
-  A* eb = eb_ext ? eb_ext : (A*)c->scratch3.p;
   A* Mb = M_ext ? M_ext : (A*)c->scratch1.p;
+  A* M = Mb;
+  A* Ic = Ic_ext ? Ic_ext : (A*)c->scratch2.p;
+  A* eb = eb_ext ? eb_ext : (A*)c->scratch3.p;
   const double* sp = (const double*)c->sp.p;
   // S1
-  spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, M, sp, nz, nO, N);
-  spline_eval_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, M, (const int*)c->iin.p, (const double*)c->tin.p,
+  spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, M, sp, nz, nO, N);
+  spline_eval_kernel<A, A><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, M, (const int*)c->iin.p, (const double*)c->tin.p,
                                                                   sp, nullptr, Ic, nz, nO, N);
   // S5 (initialises eps_bar)
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
   PRD_CUDA_TRY(c, cudaMemsetAsync(c->r3J.p, 0, c->r3J.bytes, c->stream));
-  r3_J_kernel<T><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
+  r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
                                                         (double*)c->r3J.p, nO, N, nq, c->nl_st);
   r3_out_kernel<T, A><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)c->r3J.p, (const T*)c->r3ab.p,
                                                                (const T*)c->r3out.p, (const T*)c->r3prof.p, eb, nz,
@@ -390,9 +391,10 @@ static int sigma_T(Ctx* c, const T* x, A* eps, bool normalised, A* eb_ext = null
       (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
   // S6
   spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, Mb, sp, nz, nO, N);
-  spline_eval_kernel<A><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, Mb, (const int*)c->ibk.p, (const double*)c->tbk.p,
-                                                                  sp, normalised ? (const A*)c->f.p : nullptr, eps, nz,
-                                                                  nO, N);
+  spline_eval_kernel<A, T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, Mb, (const int*)c->ibk.p,
+                                                                     (const double*)c->tbk.p, sp,
+                                                                     normalised ? (const T*)c->f.p : nullptr, eps, nz,
+                                                                     nO, N);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
@@ -407,11 +409,11 @@ int spline_frame_change(Ctx* c, const void* in, void* out, bool to_comoving) {
   const double* tt = (const double*)(to_comoving ? c->tin.p : c->tbk.p);
   if (c->prec == PRD_FP64) {
     spline_M_kernel<double><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>((const double*)in, (double*)c->scratch1.p, sp, nz, nO, N);
-    spline_eval_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const double*)in, (const double*)c->scratch1.p, kk, tt,
+    spline_eval_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const double*)in, (const double*)c->scratch1.p, kk, tt,
                                                                          sp, nullptr, (double*)out, nz, nO, N);
   } else {
     spline_M_kernel<float><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>((const float*)in, (float*)c->scratch1.p, sp, nz, nO, N);
-    spline_eval_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const float*)in, (const float*)c->scratch1.p, kk, tt,
+    spline_eval_kernel<float, float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const float*)in, (const float*)c->scratch1.p, kk, tt,
                                                                         sp, nullptr, (float*)out, nz, nO, N);
   }
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
@@ -427,11 +429,11 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const double* dmu = (const double*)c->dmu.p;
   if (c->prec == PRD_FP64)
-    delo_kernel<double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p, dmu,
+    delo_kernel<double, double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p, dmu,
                                                                        (const double*)sub_from, (double*)out, nz, nO,
                                                                        N, boundary ? 1 : 0, c->WT[0]);
   else
-    delo_kernel<float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p, dmu,
+    delo_kernel<float, float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p, dmu,
                                                                       (const float*)sub_from, (float*)out, nz, nO, N,
                                                                       boundary ? 1 : 0, c->WT[0]);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
@@ -445,15 +447,15 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
 int compute_normalisation(Ctx* c) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
-  DBuf wt, fac, xin, num, eb, Mb;
+  DBuf wt, fac, xin, num, eb, Mb, Ic;
   std::vector<double> f(nz);
   for (int iz = 0; iz < nz; ++iz) f[iz] = (1.0 - c->eps[iz]) * c->WT[iz];
   int rc;
   const size_t vb64 = nvec(c) * 8;
-  auto cleanup = [&]() { dfree(wt); dfree(fac); dfree(xin); dfree(num); dfree(eb); dfree(Mb); };
+  auto cleanup = [&]() { dfree(wt); dfree(fac); dfree(xin); dfree(num); dfree(eb); dfree(Mb); dfree(Ic); };
   if ((rc = upload(c, wt, c->WT.data(), nz * 8)) || (rc = upload(c, fac, f.data(), nz * 8)) ||
-      (rc = dalloc(c, xin, nvec(c) * c->esz)) || (rc = dalloc(c, num, vb64)) || (rc = dalloc(c, eb, vb64)) ||
-      (rc = dalloc(c, Mb, vb64))) {
+      (rc = dalloc(c, xin, vb64)) || (rc = dalloc(c, num, vb64)) || (rc = dalloc(c, eb, vb64)) ||
+      (rc = dalloc(c, Mb, vb64)) || (rc = dalloc(c, Ic, vb64))) {
     cleanup();
     return rc;
   }
@@ -464,8 +466,9 @@ int compute_normalisation(Ctx* c) {
       normalise_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
           (const double*)num.p, (const double*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
   } else {
-    fill_planck_kernel<float><<<ceil_div(npt, 256), 256, 0, c->stream>>>((float*)xin.p, (const double*)wt.p, nz, nO, N);
-    rc = sigma_T<float, double>(c, (const float*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p);
+    fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
+    rc = sigma_T<float, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p,
+                                (double*)Ic.p);
     if (!rc)
       normalise_kernel<double, float><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
           (const double*)num.p, (const float*)c->kt.p, (const double*)fac.p, (float*)c->f.p, nz, nO, N);
@@ -484,5 +487,36 @@ int apply_operator(Ctx* c, const void* x, void* y) {
 }
 
 int rhs(Ctx* c, void* b) { return apply_lambda(c, c->epsth.p, b, nullptr, true); }
+
+// FP32 mode only: y = (Id - Lambda Sigma) x with FP64 vectors and FP64
+// accumulation over the FP32-stored operator (residuals of the refinement).
+int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws /* 4 x nvec doubles */) {
+  const size_t nv = nvec(c);
+  double* eps = ws;
+  int rc = sigma_T<float, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv);
+  if (rc) return rc;
+  delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
+      eps, (const float*)c->kt.p, (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu, 0, c->WT[0]);
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
+
+int rhs_acc(Ctx* c, double* b) {
+  const size_t nv = nvec(c);
+  DBuf e64;
+  int rc = dalloc(c, e64, nv * 8);
+  if (rc) return rc;
+  std::vector<float> h(nv);
+  cudaMemcpy(h.data(), c->epsth.p, nv * 4, cudaMemcpyDeviceToHost);
+  std::vector<double> hd(h.begin(), h.end());
+  cudaMemcpy(e64.p, hd.data(), nv * 8, cudaMemcpyHostToDevice);
+  delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
+      (const double*)e64.p, (const float*)c->kt.p, (const double*)c->dmu.p, nullptr, b, c->nz, c->nO, c->nnu, 1,
+      c->WT[0]);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  dfree(e64);
+  if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("rhs_acc: ") + cudaGetErrorString(e));
+  return PRD_OK;
+}
 
 }  // namespace prd

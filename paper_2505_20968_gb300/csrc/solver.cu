@@ -126,29 +126,27 @@ struct Vops {
 
 }  // namespace
 
-int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x, int* iters, double* true_res,
-          double* hist) {
+// GMRES on A x = b in the ctx precision; x holds the initial guess on entry.
+static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_iter, int restart, int* iters,
+                      double* true_res, double* hist, double hist_scale, int* nh_io) {
   const size_t n = nvec(c);
   const size_t vb = n * c->esz;
   Vops ops{c, n};
   int rc = ops.init();
   if (rc) return rc;
   const int m = std::max(1, std::min(restart, 200));
-  DBuf V, b, r, w;
-  auto cleanup = [&]() { dfree(V); dfree(b); dfree(r); dfree(w); dfree(ops.dots); };
-  if ((rc = dalloc(c, V, vb * (m + 1))) || (rc = dalloc(c, b, vb)) || (rc = dalloc(c, r, vb)) || (rc = dalloc(c, w, vb))) {
+  DBuf V, r, w;
+  struct { void* p; } b{const_cast<void*>(bvec)};
+  auto cleanup = [&]() { dfree(V); dfree(r); dfree(w); dfree(ops.dots); };
+  if ((rc = dalloc(c, V, vb * (m + 1))) || (rc = dalloc(c, r, vb)) || (rc = dalloc(c, w, vb))) {
     cleanup();
     return rc;
   }
   auto vec = [&](int k) { return (void*)((char*)V.p + (size_t)k * vb); };
-  // b = Lambda eps_th + t
-  if ((rc = rhs(c, b.p))) { cleanup(); return rc; }
-  if (x0) PRD_CUDA_TRY(c, cudaMemcpyAsync(x, x0, vb, cudaMemcpyDeviceToDevice, c->stream));
-  else PRD_CUDA_TRY(c, cudaMemsetAsync(x, 0, vb, c->stream));
   double bnorm;
   if ((rc = ops.norm(b.p, &bnorm))) { cleanup(); return rc; }
   if (!(bnorm > 0) || !std::isfinite(bnorm)) { cleanup(); return fail(c, PRD_E_NAN, "right-hand side norm is zero or not finite"); }
-  int it = 0, nh = 0;
+  int it = 0, nh = nh_io ? *nh_io : 0;
   double tol_in = tol;
   double tr = 1.0;
   int status = PRD_E_NOCONV;
@@ -197,7 +195,7 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
       const double est = tr * std::fabs(g[j + 1]) / beta0;   // estimate of the true relative residual
-      if (hist && nh <= max_iter) hist[nh++] = est;
+      if (hist && nh <= max_iter) hist[nh++] = est * hist_scale;
       if (hn <= 1e-300 * std::max(1.0, beta0)) { breakdown = true; ++j; break; }
       if ((rc = ops.scale(r.p, 1.0 / hn, vec(j + 1)))) break;
       if (est < 0.5 * tol_in) { ++j; break; }
@@ -232,10 +230,121 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
   }
   if (iters) *iters = it;
   if (true_res) *true_res = tr;
+  if (nh_io) *nh_io = nh;
   cleanup();
   if (rc) return rc;
   if (status == PRD_E_NOCONV) return fail(c, PRD_E_NOCONV, "GMRES reached max_iter before tol");
   if (status == PRD_E_BREAKDOWN) return fail(c, PRD_E_BREAKDOWN, "GMRES breakdown before tol");
+  return PRD_OK;
+}
+
+__global__ void d2f_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f2d_add_kernel(const float* __restrict__ a, double* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] += (double)a[i];
+}
+__global__ void f2d_kernel(const float* __restrict__ a, double* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void sub_kernel(const double* __restrict__ b, double* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = b[i] - y[i];
+}
+__global__ void dnorm2_kernel(const double* __restrict__ a, size_t n, double* out) {
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s += a[i] * a[i];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws);
+int rhs_acc(Ctx* c, double* b);
+
+static int dnorm(Ctx* c, const double* a, size_t n, double* dsum, double* out) {
+  PRD_CUDA_TRY(c, cudaMemsetAsync(dsum, 0, 8, c->stream));
+  dnorm2_kernel<<<608, 256, 0, c->stream>>>(a, n, dsum);
+  double h;
+  PRD_CUDA_TRY(c, cudaMemcpyAsync(&h, dsum, 8, cudaMemcpyDeviceToHost, c->stream));
+  PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *out = std::sqrt(h);
+  return PRD_OK;
+}
+
+int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x, int* iters, double* true_res,
+          double* hist) {
+  const size_t n = nvec(c);
+  const size_t vb = n * c->esz;
+  int rc;
+  if (c->prec == PRD_FP64) {
+    DBuf b;
+    if ((rc = dalloc(c, b, vb))) return rc;
+    if ((rc = rhs(c, b.p))) { dfree(b); return rc; }
+    if (x0) PRD_CUDA_TRY(c, cudaMemcpyAsync(x, x0, vb, cudaMemcpyDeviceToDevice, c->stream));
+    else PRD_CUDA_TRY(c, cudaMemsetAsync(x, 0, vb, c->stream));
+    rc = gmres_core(c, b.p, x, tol, max_iter, restart, iters, true_res, hist, 1.0, nullptr);
+    dfree(b);
+    return rc;
+  }
+  // FP32 mode: mixed-precision iterative refinement.  Residuals b - A x are
+  // formed with FP64 vectors and FP64 accumulation over the FP32-stored
+  // operator (the FP64 residual check); corrections come from FP32 GMRES.
+  DBuf b64, x64, r64, ws, d32, r32, dsum;
+  auto cleanup = [&]() { dfree(b64); dfree(x64); dfree(r64); dfree(ws); dfree(d32); dfree(r32); dfree(dsum); };
+  if ((rc = dalloc(c, b64, n * 8)) || (rc = dalloc(c, x64, n * 8)) || (rc = dalloc(c, r64, n * 8)) ||
+      (rc = dalloc(c, ws, 4 * n * 8)) || (rc = dalloc(c, d32, vb)) || (rc = dalloc(c, r32, vb)) ||
+      (rc = dalloc(c, dsum, 8))) {
+    cleanup();
+    return rc;
+  }
+  const int G = 608;
+  if ((rc = rhs_acc(c, (double*)b64.p))) { cleanup(); return rc; }
+  if (x0) f2d_kernel<<<G, 256, 0, c->stream>>>((const float*)x0, (double*)x64.p, n);
+  else PRD_CUDA_TRY(c, cudaMemsetAsync(x64.p, 0, n * 8, c->stream));
+  double bn;
+  if ((rc = dnorm(c, (const double*)b64.p, n, (double*)dsum.p, &bn))) { cleanup(); return rc; }
+  if (!(bn > 0) || !std::isfinite(bn)) { cleanup(); return fail(c, PRD_E_NAN, "right-hand side norm is zero or not finite"); }
+  int it_total = 0, nh = 0, status = PRD_E_NOCONV;
+  double res = 1.0;
+  for (int outer = 0; outer < 12 && it_total < max_iter; ++outer) {
+    if ((rc = apply_operator_acc(c, (const double*)x64.p, (double*)r64.p, (double*)ws.p))) break;
+    sub_kernel<<<G, 256, 0, c->stream>>>((const double*)b64.p, (double*)r64.p, n);
+    double rn;
+    if ((rc = dnorm(c, (const double*)r64.p, n, (double*)dsum.p, &rn))) break;
+    res = rn / bn;
+    if (!std::isfinite(res)) { rc = fail(c, PRD_E_NAN, "residual is not finite"); break; }
+    if (res < tol) { status = PRD_OK; break; }
+    d2f_kernel<<<G, 256, 0, c->stream>>>((const double*)r64.p, (float*)r32.p, n);
+    PRD_CUDA_TRY(c, cudaMemsetAsync(d32.p, 0, vb, c->stream));
+    const double tin = std::max(0.3 * tol / res, 3e-6);
+    int its = 0;
+    double tr_in = 0;
+    int rci = gmres_core(c, r32.p, d32.p, tin, max_iter - it_total, restart, &its, &tr_in, hist, res, &nh);
+    it_total += its;
+    if (rci && rci != PRD_E_NOCONV) { rc = rci; break; }
+    f2d_add_kernel<<<G, 256, 0, c->stream>>>((const float*)d32.p, (double*)x64.p, n);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  }
+  if (!rc) {
+    d2f_kernel<<<G, 256, 0, c->stream>>>((const double*)x64.p, (float*)x, n);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = fail(c, PRD_E_CUDA, cudaGetErrorString(e));
+  }
+  if (iters) *iters = it_total;
+  if (true_res) *true_res = res;
+  cleanup();
+  if (rc) return rc;
+  if (status != PRD_OK) return fail(c, PRD_E_NOCONV, "refined GMRES reached max_iter before tol");
   return PRD_OK;
 }
 
