@@ -146,7 +146,7 @@ int build_device_tables(Ctx* c) {
   if ((rc = upload_T(c, c->kt, kt)) || (rc = upload_T(c, c->epsth, epsth))) return rc;
   {
     std::vector<double> ones(npt, 1.0);
-    if ((rc = upload_T(c, c->f, ones))) return rc;
+    if ((rc = upload(c, c->f, ones.data(), npt * 8))) return rc;   // FP64 in both modes
   }
   // ---- preconditioner scalar formal-solver tables: eta1 and DELO weights
   {

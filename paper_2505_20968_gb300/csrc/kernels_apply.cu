@@ -75,12 +75,13 @@ __global__ void spline_eval_kernel(const T* __restrict__ y, const T* __restrict_
     const double t = tt[pt], omt = 1.0 - t;
     const double h = sp[(size_t)iz * 3 * N + k];
     const double k6 = h * h / 6.0;
-    const T c0 = (T)omt, c1 = (T)t, c2 = (T)(k6 * (omt * omt * omt - omt)), c3 = (T)(k6 * (t * t * t - t));
+    // y_k + t (y_{k+1} - y_k) + ...: reproduces a constant exactly in any precision
+    const T c1 = (T)t, c2 = (T)(k6 * (omt * omt * omt - omt)), c3 = (T)(k6 * (t * t * t - t));
     const V a = yr[k], b = yr[k + 1], ma = Mr[k], mb = Mr[k + 1];
-    r.x = c0 * a.x + c1 * b.x + c2 * ma.x + c3 * mb.x;
-    r.y = c0 * a.y + c1 * b.y + c2 * ma.y + c3 * mb.y;
-    r.z = c0 * a.z + c1 * b.z + c2 * ma.z + c3 * mb.z;
-    r.w = c0 * a.w + c1 * b.w + c2 * ma.w + c3 * mb.w;
+    r.x = a.x + c1 * (b.x - a.x) + c2 * ma.x + c3 * mb.x;
+    r.y = a.y + c1 * (b.y - a.y) + c2 * ma.y + c3 * mb.y;
+    r.z = a.z + c1 * (b.z - a.z) + c2 * ma.z + c3 * mb.z;
+    r.w = a.w + c1 * (b.w - a.w) + c2 * ma.w + c3 * mb.w;
   }
   if (fI) r.x *= (T)fI[pt];
   reinterpret_cast<V*>(out)[pt] = r;
@@ -306,17 +307,20 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
       I[0] = (boundary && up) ? (A)WT0 : (A)0;
       I[1] = I[2] = I[3] = (A)0;
     } else {
+      // D = I_k - S_k solves (Id + b K'_k) D = e (I_{k-1} - S_k) + a (S_{k-1} - S_k)
+      //      - a K'_{k-1} I_{k-1} - b K'_k S_k,  with b = 1 - e - a used only
+      // in the dichroic terms: a constant unpolarised source is reproduced
+      // exactly whatever the rounding of the stored weights.
       const A e = t[7], al = t[8], be = t[9];
       A rhs[4];
       for (int i = 0; i < 4; ++i) {
-        A v = e * I[i] + al * Sp[i] + be * S[i];
-        for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j];
+        A v = e * (I[i] - S[i]) + al * (Sp[i] - S[i]);
+        for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + be * Kk[i][j] * S[j];
         rhs[i] = v;
       }
       A M4[4][4];
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) M4[i][j] = (i == j ? (A)1 : (A)0) + be * Kk[i][j];
-      // Gaussian elimination without pivoting (symmetric part positive definite)
       for (int c0 = 0; c0 < 4; ++c0) {
         const A inv = (A)1 / M4[c0][c0];
         for (int r = c0 + 1; r < 4; ++r) {
@@ -325,11 +329,13 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
           rhs[r] -= f * rhs[c0];
         }
       }
+      A D[4];
       for (int r = 3; r >= 0; --r) {
         A v = rhs[r];
-        for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * I[cc];
-        I[r] = v / M4[r][r];
+        for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * D[cc];
+        D[r] = v / M4[r][r];
       }
+      for (int i = 0; i < 4; ++i) I[i] = S[i] + D[i];
     }
     for (int s = 0; s < 4; ++s) {
       out[pt * 4 + s] = x_sub ? x_sub[pt * 4 + s] - I[s] : I[s];
@@ -343,12 +349,12 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
 
 template <typename A, typename T>
 __global__ void normalise_kernel(const A* __restrict__ num, const T* __restrict__ kt, const double* __restrict__ fac,
-                                 T* __restrict__ f, int nz, int nO, int N) {
+                                 double* __restrict__ f, int nz, int nO, int N) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= (long long)nz * nO * N) return;
   const int iz = (int)(pt / ((long long)nO * N));
   const double eta1 = 1.0 / (double)kt[pt * 10 + 6];
-  f[pt] = (T)(fac[iz] * eta1 / (double)num[pt * 4]);
+  f[pt] = fac[iz] * eta1 / (double)num[pt * 4];
 }
 
 template <typename T>
@@ -391,9 +397,9 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
       (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
   // S6
   spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, Mb, sp, nz, nO, N);
-  spline_eval_kernel<A, T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, Mb, (const int*)c->ibk.p,
+  spline_eval_kernel<A, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, Mb, (const int*)c->ibk.p,
                                                                      (const double*)c->tbk.p, sp,
-                                                                     normalised ? (const T*)c->f.p : nullptr, eps, nz,
+                                                                     normalised ? (const double*)c->f.p : nullptr, eps, nz,
                                                                      nO, N);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
@@ -471,7 +477,7 @@ int compute_normalisation(Ctx* c) {
                                 (double*)Ic.p);
     if (!rc)
       normalise_kernel<double, float><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
-          (const double*)num.p, (const float*)c->kt.p, (const double*)fac.p, (float*)c->f.p, nz, nO, N);
+          (const double*)num.p, (const float*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cleanup();

@@ -87,7 +87,7 @@ def test_fp32_sigma_and_operator(name):
 @pytest.mark.parametrize("name", ["mgii", "hi", "hi_aa"])
 def test_fp32_emergent_stokes_after_solve(name):
     cfg, P, O = pair(name)
-    xg, info = P.solve(tol=1e-6, max_iter=300, restart=100, check=False)
+    xg, info = P.solve(tol=1e-9, max_iter=300, restart=100, check=False)
     xo, _ = O.solve(tol=1e-12)
     top = P.mu > 0
     Ig = xg.cpu().numpy()[-1, top].astype(np.float64)
