@@ -70,11 +70,14 @@ struct Vops {
   size_t n;
   int grid;
   DBuf dots;
-  int init() {
+  int cap = 0;   // capacity of `dots` in doubles
+  int init(int capacity) {
     grid = 152 * 4;
-    return dalloc(c, dots, 64 * sizeof(double));
+    cap = capacity;
+    return dalloc(c, dots, (size_t)capacity * sizeof(double));
   }
   int dot_many(const void* V, size_t ld, int nv, const void* w, double* out) {
+    if (nv > cap) return fail(c, PRD_E_ARG, "internal: dot buffer too small");
     PRD_CUDA_TRY(c, cudaMemsetAsync(dots.p, 0, nv * sizeof(double), c->stream));
     if (c->prec == PRD_FP64)
       multidot_kernel<double><<<dim3(grid, nv), 256, 0, c->stream>>>((const double*)V, ld, (const double*)w, n, (double*)dots.p);
@@ -85,6 +88,7 @@ struct Vops {
     return PRD_OK;
   }
   int axpy_many(const void* V, size_t ld, const double* h, int nv, void* w) {
+    if (nv > cap) return fail(c, PRD_E_ARG, "internal: dot buffer too small");
     PRD_CUDA_TRY(c, cudaMemcpyAsync(dots.p, h, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->prec == PRD_FP64)
       multiaxpy_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, (const double*)dots.p, nv, (double*)w, n);
@@ -94,6 +98,7 @@ struct Vops {
     return PRD_OK;
   }
   int update(const void* V, size_t ld, const double* y, int nv, void* x) {
+    if (nv > cap) return fail(c, PRD_E_ARG, "internal: dot buffer too small");
     PRD_CUDA_TRY(c, cudaMemcpyAsync(dots.p, y, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->prec == PRD_FP64)
       update_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, (const double*)dots.p, nv, (double*)x, n);
@@ -131,10 +136,10 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
                       double* true_res, double* hist, double hist_scale, int* nh_io) {
   const size_t n = nvec(c);
   const size_t vb = n * c->esz;
-  Vops ops{c, n};
-  int rc = ops.init();
-  if (rc) return rc;
   const int m = std::max(1, std::min(restart, 200));
+  Vops ops{c, n};
+  int rc = ops.init(m + 2);
+  if (rc) return rc;
   DBuf V, r, w;
   struct { void* p; } b{const_cast<void*>(bvec)};
   auto cleanup = [&]() { dfree(V); dfree(r); dfree(w); dfree(ops.dots); };
@@ -326,10 +331,11 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
     if (res < tol) { status = PRD_OK; break; }
     d2f_kernel<<<G, 256, 0, c->stream>>>((const double*)r64.p, (float*)r32.p, n);
     PRD_CUDA_TRY(c, cudaMemsetAsync(d32.p, 0, vb, c->stream));
-    const double tin = std::max(0.3 * tol / res, 3e-6);
+    const double tin = std::max(0.3 * tol / res, 3e-5);
     int its = 0;
     double tr_in = 0;
-    int rci = gmres_core(c, r32.p, d32.p, tin, max_iter - it_total, restart, &its, &tr_in, hist, res, &nh);
+    const int cap_in = std::min(max_iter - it_total, std::max(2 * restart, 40));
+    int rci = gmres_core(c, r32.p, d32.p, tin, cap_in, restart, &its, &tr_in, hist, res, &nh);
     it_total += its;
     if (rci && rci != PRD_E_NOCONV) { rc = rci; break; }
     f2d_add_kernel<<<G, 256, 0, c->stream>>>((const float*)d32.p, (double*)x64.p, n);
