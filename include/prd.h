@@ -158,6 +158,15 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
 int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu,
                         const double* chi, void* out_dev);
 
+/* Stage timing (tracing).  When on, CUDA events recorded on the ctx stream
+ * bracket each stage of every apply; prd_stage_times returns the accumulated
+ * milliseconds and call counts per stage (index 0: S1 comoving interpolation,
+ * 1: S5 R_III, 2: S3+S4 R_II contraction, 3: S6 back-interpolation and f,
+ * 4: S7+S8 formal solution) and synchronises the stream.  Turning it on or
+ * off resets the counters. */
+int prd_set_profiling(prd_ctx* ctx, int on);
+int prd_stage_times(prd_ctx* ctx, double* ms, int64_t* count, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,7 +68,7 @@ def delo_coeffs(d):
 
 
 class Problem:
-    def __init__(self, cfg, mode=None):
+    def __init__(self, cfg, mode=None, normalise=True):
         self.cfg = cfg
         atom, atm, quad = cfg["atom"], cfg["atm"], cfg["quad"]
         self.atom = atom
@@ -127,7 +127,8 @@ class Problem:
         self._build_K()
         self._build_delo()
         self.f = np.ones((nz, self.nO, self.nN))
-        self.f = self._normalisation()
+        if normalise:
+            self.f = self._normalisation()
 
     def amplitudes(self, iz, mu, chi):
         """a[alpha, ku, kl] = <k_u| e_alpha . d |k_l> for direction (mu, chi)."""
@@ -239,6 +240,8 @@ class Problem:
         ampO = amp[o] if amp_o is None else amp_o
         ampI = amp[op]
         th = self.thetas[self.cls[o, op]] if theta is None else theta
+        if self.mode == 1:
+            th = -1.0
         s = self.shift[iz]
         nu_, nl = self.nu_states, self.nl_states
         N = self.nN
@@ -295,6 +298,70 @@ class Problem:
         if normalised:
             S[:, :, 0] *= self.f[iz][:, :, None, None, None]
         return S.reshape(nO * N * 4, nO * N * 4)
+
+    def sigma_sample(self, x, iz, o):
+        """eps(z, Omega, :) = Sigma x at one height and direction (normalised
+        with f computed at the same point); for spot checks at full size."""
+        N = self.nN
+        sb = np.zeros((N, 4))
+        sw = np.zeros((N, 4))
+        Il = np.zeros((N, 4))
+        Il[:, 0] = self.WT[iz]
+        for op in range(self.nO):
+            blk = self.block(iz, o, op).reshape(N * 4, N * 4)
+            It = self.interp_in(iz, op) @ x[iz, op]
+            sb += (blk @ It.ravel()).reshape(N, 4)
+            sw += (blk @ (self.interp_in(iz, op) @ Il).ravel()).reshape(N, 4)
+        Ub = self.interp_back(iz, o)
+        eps = Ub @ sb
+        num = (Ub @ sw)[:, 0]
+        f = (1.0 - self.eps[iz]) * self.WT[iz] * self.eta1[iz, o] / num
+        eps[:, 0] *= f
+        return eps, f
+
+    def lambda_ray(self, eps, o, n):
+        """Lambda eps along one ray (Omega, nu) for every height."""
+        sub = eps[:, o:o + 1, n:n + 1]
+        out = self.formal_solution(sub, K=self.K[:, o:o + 1, n:n + 1], eta1=self.eta1[:, o:o + 1, n:n + 1],
+                                   dtau=self.dtau[:, o:o + 1, n:n + 1], mu=self.mu[o:o + 1])
+        return out[:, 0, 0]
+
+    def emergent(self, x, mu, chi):
+        """Emergent Stokes vector at z_max along a line of sight (mu > 0, chi)
+        off the grid (Sect. 6.2): scattering emissivity rows for the new
+        direction, Kirchhoff factor from the same rows, thermal part, and one
+        DELO-linear formal solution from the lower boundary."""
+        nz, N = self.nz, self.nN
+        n_l = unit_vector(np.array([mu]), np.array([chi]))[0]
+        v = np.asarray(self.cfg["atm"]["v_kms"], float)
+        eps = np.zeros((nz, 1, N, 4))
+        K = np.zeros((nz, 1, N, 4, 4))
+        for iz in range(nz):
+            amp = self.amplitudes(iz, mu, chi)
+            ub = (v[iz] @ n_l) / self.vD_kms[iz]
+            K[iz, 0] = self.K_from_kappa(self.kappa(iz, amp, ub, self.u[iz]))
+            sb = np.zeros((N, 4))
+            sw = np.zeros((N, 4))
+            Il = np.zeros((N, 4))
+            Il[:, 0] = self.WT[iz]
+            for op in range(self.nO):
+                th = scattering_angle(n_l, self.nvec[op])
+                th = 0.0 if th < 1e-10 else (np.pi if abs(th - np.pi) < 1e-10 else th)
+                blk = self.block(iz, None, op, amp_o=amp, theta=th).reshape(N * 4, N * 4)
+                Uin = self.interp_in(iz, op)
+                sb += (blk @ (Uin @ x[iz, op]).ravel()).reshape(N, 4)
+                sw += (blk @ (Uin @ Il).ravel()).reshape(N, 4)
+            Ub = self.spl[iz].basis(self.u[iz] + ub)
+            e = Ub @ sb
+            f = (1.0 - self.eps[iz]) * self.WT[iz] * K[iz, 0, :, 0, 0] / (Ub @ sw)[:, 0]
+            e[:, 0] *= f
+            eps[iz, 0] = e + (self.eps[iz] * self.WT[iz]) * K[iz, 0, :, :, 0]
+        eta1 = K[..., 0, 0]
+        dtau = np.zeros((nz, 1, N))
+        for k in range(1, nz):
+            dtau[k, 0] = 0.5 * (eta1[k - 1, 0] + eta1[k, 0]) * (self.z[k] - self.z[k - 1]) / mu
+        out = self.formal_solution(eps, boundary=True, K=K, eta1=eta1, dtau=dtau, mu=np.array([mu]))
+        return out[-1, 0]
 
     def _normalisation(self):
         f = np.ones((self.nz, self.nO, self.nN))

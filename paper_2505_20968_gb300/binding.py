@@ -34,7 +34,8 @@ _lib = None
 EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd_set_atom",
            "prd_set_atmosphere", "prd_set_quadrature", "prd_setup", "prd_sizes", "prd_directions",
            "prd_workspace_bytes", "prd_rhs", "prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator",
-           "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes"]
+           "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
+           "prd_set_profiling", "prd_stage_times"]
 
 
 def lib():
@@ -66,6 +67,8 @@ def lib():
         L.prd_set_precond_sweeps.argtypes = [P, I]
         L.prd_solve.argtypes = [P, D, I, I, P, P, ctypes.POINTER(I), DP, DP]
         L.prd_emergent_stokes.argtypes = [P, P, I, DP, DP, P]
+        L.prd_set_profiling.argtypes = [P, I]
+        L.prd_stage_times.argtypes = [P, DP, ctypes.POINTER(ctypes.c_int64), I]
         _lib = L
     return _lib
 
@@ -191,6 +194,18 @@ class PRD:
         out = torch.empty((len(mu), self.nN, 4), dtype=self.dtype, device=self.device) if out is None else out
         self._check(lib().prd_emergent_stokes(self.h, self._vec(x), len(mu), mup, chip, ctypes.c_void_p(out.data_ptr())))
         return out
+
+    STAGES = ("S1_interp_in", "S5_R3", "S3_R2_contraction", "S6_interp_back", "S7_delo")
+
+    def set_profiling(self, on=True):
+        self._check(lib().prd_set_profiling(self.h, 1 if on else 0))
+
+    def stage_times(self):
+        ms = np.zeros(8)
+        cnt = np.zeros(8, dtype=np.int64)
+        self._check(lib().prd_stage_times(self.h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 8))
+        return {k: (ms[i], int(cnt[i])) for i, k in enumerate(self.STAGES)}
 
     def close(self):
         if getattr(self, "h", None):

@@ -51,7 +51,41 @@ static void free_all(Ctx* c) {
   c->owned.clear();
 }
 
-Ctx::~Ctx() { free_all(this); }
+void stage_begin(Ctx* c, int stage, cudaEvent_t* out) {
+  *out = nullptr;
+  if (!c->prof) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, c->stream);
+  *out = e;
+}
+
+void stage_end(Ctx* c, int stage, cudaEvent_t start) {
+  if (!c->prof || !start) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, c->stream);
+  c->ev_pending.push_back({stage, {start, e}});
+}
+
+void stage_collect(Ctx* c) {
+  for (auto& p : c->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.second.second) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+      c->stage_ms[p.first] += ms;
+      c->stage_n[p.first] += 1;
+    }
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  c->ev_pending.clear();
+}
+
+Ctx::~Ctx() {
+  stage_collect(this);
+  free_all(this);
+}
 
 int launch_precond_setup(Ctx* c);
 
@@ -319,6 +353,25 @@ int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double*
   } catch (const std::exception& e) {
     return fail(c, PRD_E_NOMEM, std::string("host exception: ") + e.what());
   }
+}
+
+int prd_set_profiling(prd_ctx* ctx, int on) {
+  CTX_OR_ARG(ctx);
+  prd::stage_collect(c);
+  c->prof = on != 0;
+  for (int i = 0; i < 8; ++i) { c->stage_ms[i] = 0; c->stage_n[i] = 0; }
+  return PRD_OK;
+}
+
+int prd_stage_times(prd_ctx* ctx, double* ms, int64_t* count, int n) {
+  CTX_OR_ARG(ctx);
+  if (!ms || n < 1) return fail(c, PRD_E_ARG, "bad stage_times arguments");
+  prd::stage_collect(c);
+  for (int i = 0; i < n && i < 8; ++i) {
+    ms[i] = c->stage_ms[i];
+    if (count) count[i] = c->stage_n[i];
+  }
+  return PRD_OK;
 }
 
 }  // extern "C"

@@ -130,6 +130,27 @@ States pb_states(const prd_atom& at, double nu0, double B_gauss) {
 
 size_t nvec(const Ctx* c) { return (size_t)4 * c->nz * c->nO * c->nnu; }
 
+void dir_amplitudes(const Ctx* c, int iz, double m, double ch, cplx* out) {
+  const int nu_ = c->nu_st, nl = c->nl_st;
+  const double isq2 = 1.0 / std::sqrt(2.0);
+  const cplx eqc[3][3] = {{isq2, cplx(0, isq2), 0.0}, {0.0, 0.0, 1.0}, {-isq2, cplx(0, isq2), 0.0}};
+  const double* R = &c->Rmag[(size_t)iz * 9];
+  const double sn = std::sqrt(std::max(0.0, 1.0 - m * m));
+  const double e[2][3] = {{-std::sin(ch), std::cos(ch), 0.0}, {m * std::cos(ch), m * std::sin(ch), -sn}};
+  for (int al = 0; al < 2; ++al) {
+    double eB[3];
+    for (int r = 0; r < 3; ++r) eB[r] = R[r * 3] * e[al][0] + R[r * 3 + 1] * e[al][1] + R[r * 3 + 2] * e[al][2];
+    cplx proj[3];
+    for (int q = 0; q < 3; ++q) proj[q] = eqc[q][0] * eB[0] + eqc[q][1] * eB[1] + eqc[q][2] * eB[2];
+    for (int ku = 0; ku < nu_; ++ku)
+      for (int l = 0; l < nl; ++l) {
+        cplx sum = 0.0;
+        for (int q = 0; q < 3; ++q) sum += proj[q] * c->Dmat[(size_t)iz * 3 * nu_ * nl + ((size_t)q * nu_ + ku) * nl + l];
+        out[((size_t)al * nu_ + ku) * nl + l] = sum;
+      }
+  }
+}
+
 int build_host_tables(Ctx* c) {
   const int nz = c->nz, N = c->nnu;
   // ---------------- angular grid (Sect. 4.2)
@@ -297,6 +318,8 @@ int build_host_tables(Ctx* c) {
   c->alpha.assign((size_t)nz * nu_ * nu_, 0.0);
   c->beta.assign((size_t)nz * nu_ * nu_, 0.0);
   c->amp.assign((size_t)nz * nO * 2 * nu_ * nl, 0.0);
+  c->Dmat.assign((size_t)nz * 3 * nu_ * nl, 0.0);
+  c->Rmag.assign((size_t)nz * 9, 0.0);
   const double isq2 = 1.0 / std::sqrt(2.0);
   // spherical unit vectors e_q (q=-1,0,1) in the magnetic frame, conjugated
   const cplx eqc[3][3] = {{isq2, cplx(0, isq2), 0.0}, {0.0, 0.0, 1.0}, {-isq2, cplx(0, isq2), 0.0}};
@@ -318,6 +341,9 @@ int build_host_tables(Ctx* c) {
     const double R[3][3] = {{std::cos(tb) * std::cos(cb), std::cos(tb) * std::sin(cb), -std::sin(tb)},
                             {-std::sin(cb), std::cos(cb), 0.0},
                             {std::sin(tb) * std::cos(cb), std::sin(tb) * std::sin(cb), std::cos(tb)}};
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) c->Rmag[(size_t)iz * 9 + r * 3 + q] = R[r][q];
+    for (size_t i = 0; i < st.D.size(); ++i) c->Dmat[(size_t)iz * 3 * nu_ * nl + i] = st.D[i];
     for (int o = 0; o < nO; ++o) {
       const double m = c->mu[o], ch = c->chi[o];
       const double sn = std::sqrt(std::max(0.0, 1.0 - m * m));

@@ -52,11 +52,10 @@ void delo(double d, double* e, double* al, double* be) {
 
 // Outgoing factor O_i(o; ku, kv, kl') = sum_ab a_b(kv,kl') sig_i[b][a] conj(a_a(ku,kl'))
 // Incoming factor I_j(o'; ku, kv, kl) = sum_gd conj(a_d(kv,kl)) sig_j[g][d] a_g(ku,kl)
-static void phase_factors(const Ctx* c, int iz, int o, std::vector<cplx>& O, std::vector<cplx>& I) {
+static void phase_factors_amp(const Ctx* c, const cplx* A, std::vector<cplx>& O, std::vector<cplx>& I) {
   const int nu_ = c->nu_st, nl = c->nl_st;
   O.assign((size_t)nu_ * nu_ * nl * 4, 0.0);
   I.assign((size_t)nu_ * nu_ * nl * 4, 0.0);
-  const cplx* A = &c->amp[(((size_t)iz * c->nO + o) * 2) * nu_ * nl];
   auto amp = [&](int al, int ku, int kl) { return A[((size_t)al * nu_ + ku) * nl + kl]; };
   for (int ku = 0; ku < nu_; ++ku)
     for (int kv = 0; kv < nu_; ++kv)
@@ -71,6 +70,136 @@ static void phase_factors(const Ctx* c, int iz, int o, std::vector<cplx>& O, std
           O[(((size_t)ku * nu_ + kv) * nl + l) * 4 + s] = so;
           I[(((size_t)ku * nu_ + kv) * nl + l) * 4 + s] = si;
         }
+}
+
+static void phase_factors(const Ctx* c, int iz, int o, std::vector<cplx>& O, std::vector<cplx>& I) {
+  phase_factors_amp(c, &c->amp[(((size_t)iz * c->nO + o) * 2) * c->nu_st * c->nl_st], O, I);
+}
+
+// propagation matrix K (4x4) for amplitudes A at shift ub and reduced frequency un
+static void kmatrix(const Ctx* c, int iz, const cplx* A, double ub, double un, double K[4][4]) {
+  const int nu_ = c->nu_st, nl = c->nl_st;
+  const double S2 = (c->atom.twoS == 1) ? 2.0 : 1.0;
+  cplx kap[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int ku = 0; ku < nu_; ++ku)
+    for (int l = 0; l < nl; ++l) {
+      const double x = un + ub + c->shift[((size_t)iz * nu_ + ku) * nl + l];
+      const cplx w = std::conj(faddeeva_host(cplx(x, c->a[iz])));
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          kap[a][b] += std::conj(A[((size_t)a * nu_ + ku) * nl + l]) * A[((size_t)b * nu_ + ku) * nl + l] * w;
+    }
+  const double norm = c->k[iz] / (2.0 * kSqrtPi * S2);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cplx tr = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          for (int d = 0; d < 2; ++d) {
+            tr += sig(i, a, b) * kap[b][d] * norm * sig(j, d, a);
+            tr += sig(i, a, b) * sig(j, b, d) * std::conj(kap[a][d] * norm);
+          }
+      K[i][j] = 0.5 * tr.real();
+    }
+}
+
+void los_tables(const Ctx* c, double mu, double chi, LosTables& L) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu, nu_ = c->nu_st, nl = c->nl_st, nt = c->ntrip, ng = c->ngrp;
+  const int nti = c->ntile(), nuv = nu_ * nu_;
+  const double S2 = (c->atom.twoS == 1) ? 2.0 : 1.0;
+  const double c2 = 3.0 / (4.0 * kPi * S2);
+  const double sn = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+  const double nl_[3] = {sn * std::cos(chi), sn * std::sin(chi), mu};
+  L.theta.assign(nO, 0.0);
+  for (int op = 0; op < nO; ++op) {
+    const double so = std::sqrt(std::max(0.0, 1.0 - c->mu[op] * c->mu[op]));
+    const double np_[3] = {so * std::cos(c->chi[op]), so * std::sin(c->chi[op]), c->mu[op]};
+    double dm = 0, ds = 0;
+    for (int d = 0; d < 3; ++d) {
+      dm += (nl_[d] - np_[d]) * (nl_[d] - np_[d]);
+      ds += (nl_[d] + np_[d]) * (nl_[d] + np_[d]);
+    }
+    double th = 2.0 * std::atan2(std::sqrt(dm), std::sqrt(ds));
+    if (th < 1e-10) th = 0.0;
+    if (std::fabs(th - kPi) < 1e-10) th = kPi;
+    L.theta[op] = c->mode == PRD_MODE_AA ? -1.0 : th;
+  }
+  L.Y.assign((size_t)nz * nO * nti * 32, 0.0);
+  L.rout.assign((size_t)nz * nuv * nl * 8, 0.0);
+  L.kt.assign((size_t)nz * N * 10, 0.0);
+  L.epsth.assign((size_t)nz * N * 4, 0.0);
+  L.kidx.assign((size_t)nz * N, 0);
+  L.tt.assign((size_t)nz * N, 0.0);
+  std::vector<double> eta((size_t)nz * N);
+  for (int iz = 0; iz < nz; ++iz) {
+    std::vector<cplx> A((size_t)2 * nu_ * nl);
+    dir_amplitudes(c, iz, mu, chi, A.data());
+    std::vector<cplx> O, Id, Oo, Io;
+    phase_factors_amp(c, A.data(), O, Id);
+    const cplx* al = &c->alpha[(size_t)iz * nu_ * nu_];
+    for (int op = 0; op < nO; ++op) {
+      phase_factors(c, iz, op, Oo, Io);
+      const double fac = c2 * c->k[iz] * c->wang[op];
+      for (int t = 0; t < nt; ++t) {
+        const int k = c->trip_k[t], l = c->trip_l[t], lp = c->trip_lp[t];
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) {
+            cplx y = 0.0;
+            for (int ku = 0; ku < nu_; ++ku)
+              y += O[(((size_t)ku * nu_ + k) * nl + lp) * 4 + i] * Io[(((size_t)ku * nu_ + k) * nl + l) * 4 + j] *
+                   al[(size_t)ku * nu_ + k];
+            y *= fac;
+            const size_t idx = ((((size_t)iz * nO + op) * nti + ng + t) * 16 + i * 4 + j) * 2;
+            L.Y[idx] = y.real();
+            L.Y[idx + 1] = y.imag();
+            const size_t ig = ((((size_t)iz * nO + op) * nti + c->trip_grp[t]) * 16 + i * 4 + j) * 2;
+            L.Y[ig] += y.real();
+            L.Y[ig + 1] += y.imag();
+          }
+      }
+    }
+    for (int q = 0; q < nuv * nl; ++q)
+      for (int s = 0; s < 4; ++s) {
+        L.rout[(((size_t)iz * nuv * nl + q) * 4 + s) * 2] = O[(size_t)q * 4 + s].real();
+        L.rout[(((size_t)iz * nuv * nl + q) * 4 + s) * 2 + 1] = O[(size_t)q * 4 + s].imag();
+      }
+    const double ub = (c->v[3 * iz] * nl_[0] + c->v[3 * iz + 1] * nl_[1] + c->v[3 * iz + 2] * nl_[2]) / c->vD[iz];
+    const double* u = &c->u[(size_t)iz * N];
+    for (int n = 0; n < N; ++n) {
+      double K[4][4];
+      kmatrix(c, iz, A.data(), ub, u[n], K);
+      const double e1 = K[0][0];
+      double* t = &L.kt[((size_t)iz * N + n) * 10];
+      t[0] = K[0][1] / e1; t[1] = K[0][2] / e1; t[2] = K[0][3] / e1;
+      t[3] = K[1][2] / e1; t[4] = K[1][3] / e1; t[5] = K[2][3] / e1;
+      t[6] = 1.0 / e1;
+      eta[(size_t)iz * N + n] = e1;
+      for (int s = 0; s < 4; ++s) L.epsth[((size_t)iz * N + n) * 4 + s] = c->eps[iz] * c->WT[iz] * K[s][0];
+      const double x = u[n] + ub;
+      int kk;
+      double tv = 0.0;
+      if (x <= u[0]) kk = -1;
+      else if (x >= u[N - 1]) kk = N - 1;
+      else {
+        int lo = 0, hi = N - 1;
+        while (hi - lo > 1) { const int md = (lo + hi) / 2; if (u[md] <= x) lo = md; else hi = md; }
+        kk = lo;
+        tv = (x - u[kk]) / (u[kk + 1] - u[kk]);
+      }
+      L.kidx[(size_t)iz * N + n] = kk;
+      L.tt[(size_t)iz * N + n] = tv;
+    }
+  }
+  // DELO weights along the line of sight (upward, mu > 0)
+  for (int n = 0; n < N; ++n)
+    for (int p = 1; p < nz; ++p) {
+      const double d = 0.5 * (eta[(size_t)(p - 1) * N + n] + eta[(size_t)p * N + n]) * std::fabs(c->z[p] - c->z[p - 1]) / mu;
+      double e, a, b;
+      delo(d, &e, &a, &b);
+      L.kt[((size_t)p * N + n) * 10 + 7] = e;
+      L.kt[((size_t)p * N + n) * 10 + 8] = a;
+      L.kt[((size_t)p * N + n) * 10 + 9] = b;
+    }
 }
 
 int build_device_tables(Ctx* c) {

@@ -377,11 +377,15 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   A* Ic = Ic_ext ? Ic_ext : (A*)c->scratch2.p;
   A* eb = eb_ext ? eb_ext : (A*)c->scratch3.p;
   const double* sp = (const double*)c->sp.p;
+  cudaEvent_t e0;
   // S1
+  stage_begin(c, ST_S1, &e0);
   spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, M, sp, nz, nO, N);
   spline_eval_kernel<A, A><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, M, (const int*)c->iin.p, (const double*)c->tin.p,
                                                                   sp, nullptr, Ic, nz, nO, N);
+  stage_end(c, ST_S1, e0);
   // S5 (initialises eps_bar)
+  stage_begin(c, ST_S5, &e0);
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
   PRD_CUDA_TRY(c, cudaMemsetAsync(c->r3J.p, 0, c->r3J.bytes, c->stream));
   r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
@@ -389,18 +393,23 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   r3_out_kernel<T, A><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)c->r3J.p, (const T*)c->r3ab.p,
                                                                (const T*)c->r3out.p, (const T*)c->r3prof.p, eb, nz,
                                                                nO, N, nuv, c->nl_st);
+  stage_end(c, ST_S5, e0);
   // S3 + S4
+  stage_begin(c, ST_S3, &e0);
   const int nchunk = (c->max_cout + kCW - 1) / kCW;
   const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
   cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
       (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
+  stage_end(c, ST_S3, e0);
   // S6
+  stage_begin(c, ST_S6, &e0);
   spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, Mb, sp, nz, nO, N);
   spline_eval_kernel<A, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(eb, Mb, (const int*)c->ibk.p,
                                                                      (const double*)c->tbk.p, sp,
                                                                      normalised ? (const double*)c->f.p : nullptr, eps, nz,
                                                                      nO, N);
+  stage_end(c, ST_S6, e0);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
@@ -434,6 +443,8 @@ int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised) {
 int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool boundary) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const double* dmu = (const double*)c->dmu.p;
+  cudaEvent_t e0;
+  stage_begin(c, ST_S7, &e0);
   if (c->prec == PRD_FP64)
     delo_kernel<double, double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p, dmu,
                                                                        (const double*)sub_from, (double*)out, nz, nO,
@@ -442,6 +453,7 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
     delo_kernel<float, float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p, dmu,
                                                                       (const float*)sub_from, (float*)out, nz, nO, N,
                                                                       boundary ? 1 : 0, c->WT[0]);
+  stage_end(c, ST_S7, e0);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
@@ -523,6 +535,141 @@ int rhs_acc(Ctx* c, double* b) {
   dfree(e64);
   if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("rhs_acc: ") + cudaGetErrorString(e));
   return PRD_OK;
+}
+
+// ------------------------------------------------------------------ S11
+// Emergent Stokes vectors along extra lines of sight (Sect. 6.2): for each
+// LOS the comoving emissivity eps_bar(z, LOS, .) is built from the solution's
+// comoving field with new tiles for the angles Theta(LOS, Omega'), normalised
+// with f computed from the same rows on the Planck field, moved to the
+// observer frame, and one DELO sweep from the bottom boundary gives I at z_max.
+template <typename T>
+__global__ void planck_comoving_kernel(T* __restrict__ Ic, const double* __restrict__ WT, int nz, int nO, int N) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= (long long)nz * nO * N) return;
+  const int iz = (int)(pt / ((long long)nO * N));
+  Ic[pt * 4] = (T)WT[iz];
+  Ic[pt * 4 + 1] = Ic[pt * 4 + 2] = Ic[pt * 4 + 3] = (T)0;
+}
+
+// eps(z, n) = (eps_sc with f) + eps_th;  f = (1-eps) W_T eta_I / num_I
+template <typename T>
+__global__ void los_combine_kernel(const T* __restrict__ es, const T* __restrict__ ew, const T* __restrict__ kt,
+                                   const T* __restrict__ eth, const double* __restrict__ fac, T* __restrict__ out,
+                                   int nz, int N) {
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= nz * N) return;
+  const int iz = pt / N;
+  const double f = fac[iz] / ((double)kt[pt * 10 + 6] * (double)ew[pt * 4]);
+  out[pt * 4] = (T)((double)es[pt * 4] * f + (double)eth[pt * 4]);
+  for (int s = 1; s < 4; ++s) out[pt * 4 + s] = es[pt * 4 + s] + eth[pt * 4 + s];
+}
+
+template <typename T>
+static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const double* chis, T* out) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu, nti = c->ntile(), nuv = c->nu_st * c->nu_st, nl = c->nl_st;
+  const int nq = nuv * nl;
+  const long long npt = (long long)nz * nO * N;
+  const size_t tz = (size_t)nO * nti * N * 2 * N * sizeof(T);   // tiles of one height, all LOS classes
+  DBuf Icx, Icw, Jx, Jw, tiles, Yd, rout, ktd, ethd, kidx, ttd, es_bar, ew_bar, es, ew, M, eps, lam, fac, dmu, clsd;
+  auto cleanup = [&]() {
+    DBuf* bs[] = {&Icx, &Icw, &Jx, &Jw, &tiles, &Yd, &rout, &ktd, &ethd, &kidx, &ttd, &es_bar, &ew_bar, &es, &ew,
+                  &M, &eps, &lam, &fac, &dmu, &clsd};
+    for (DBuf* b : bs) dfree(*b);
+  };
+  const size_t vb = nvec(c) * sizeof(T), lb = (size_t)nz * N * 4 * sizeof(T);
+  int rc;
+  std::vector<double> facv(nz), wt(c->WT);
+  for (int iz = 0; iz < nz; ++iz) facv[iz] = (1.0 - c->eps[iz]) * c->WT[iz];
+  // class structure of one LOS: class o' has the single output entry 0 and the single pair (LOS, o')
+  std::vector<int> cls;
+  for (int i = 0; i <= nO; ++i) cls.push_back(i);
+  for (int i = 0; i < nO; ++i) cls.push_back(0);
+  for (int i = 0; i <= nO; ++i) cls.push_back(i);
+  for (int i = 0; i < nO; ++i) cls.push_back(i);
+  if ((rc = dalloc(c, Icx, vb)) || (rc = dalloc(c, Icw, vb)) || (rc = dalloc(c, Jx, (size_t)nz * nuv * 16)) ||
+      (rc = dalloc(c, Jw, (size_t)nz * nuv * 16)) || (rc = dalloc(c, tiles, tz)) || (rc = dalloc(c, es_bar, lb)) ||
+      (rc = dalloc(c, ew_bar, lb)) || (rc = dalloc(c, es, lb)) || (rc = dalloc(c, ew, lb)) || (rc = dalloc(c, M, lb)) ||
+      (rc = dalloc(c, eps, lb)) || (rc = dalloc(c, lam, lb)) || (rc = upload(c, fac, facv.data(), nz * 8)) ||
+      (rc = upload(c, clsd, cls.data(), cls.size() * 4))) {
+    cleanup();
+    return rc;
+  }
+  DBuf wtd;
+  if ((rc = upload(c, wtd, wt.data(), nz * 8))) { cleanup(); return rc; }
+  // comoving fields of the solution and of the Planck function, and their R_III moments
+  spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, (T*)c->scratch1.p, (const double*)c->sp.p, nz, nO, N);
+  spline_eval_kernel<T, T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, (T*)c->scratch1.p, (const int*)c->iin.p,
+                                                                     (const double*)c->tin.p, (const double*)c->sp.p,
+                                                                     nullptr, (T*)Icx.p, nz, nO, N);
+  planck_comoving_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>((T*)Icw.p, (const double*)wtd.p, nz, nO, N);
+  PRD_CUDA_TRY(c, cudaMemsetAsync(Jx.p, 0, Jx.bytes, c->stream));
+  PRD_CUDA_TRY(c, cudaMemsetAsync(Jw.p, 0, Jw.bytes, c->stream));
+  r3_J_kernel<T, T><<<dim3(nq, nz), 256, 0, c->stream>>>((const T*)Icx.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
+                                                        (double*)Jx.p, nO, N, nq, nl);
+  r3_J_kernel<T, T><<<dim3(nq, nz), 256, 0, c->stream>>>((const T*)Icw.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
+                                                        (double*)Jw.p, nO, N, nq, nl);
+  PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const double mu1 = 1.0;
+  for (int l = 0; l < nlos && !rc; ++l) {
+    LosTables L;
+    los_tables(c, mus[l], chis[l], L);
+    auto up = [&](DBuf& b, const std::vector<double>& v) {
+      std::vector<T> h(v.begin(), v.end());
+      return upload(c, b, h.data(), h.size() * sizeof(T));
+    };
+    if ((rc = up(Yd, L.Y)) || (rc = up(rout, L.rout)) || (rc = up(ktd, L.kt)) || (rc = up(ethd, L.epsth)) ||
+        (rc = upload(c, kidx, L.kidx.data(), L.kidx.size() * 4)) || (rc = upload(c, ttd, L.tt.data(), L.tt.size() * 8)) ||
+        (rc = upload(c, dmu, &mus[l], 8)))
+      break;
+    (void)mu1;
+    // R_III parts initialise the comoving rows
+    r3_out_kernel<T, T><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
+        (const double*)Jx.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (T*)es_bar.p, nz, 1, N, nuv, nl);
+    r3_out_kernel<T, T><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
+        (const double*)Jw.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (T*)ew_bar.p, nz, 1, N, nuv, nl);
+    // R_II: tiles of every height for the LOS classes, then the contraction
+    for (int iz = 0; iz < nz && !rc; ++iz) {
+      std::vector<double> th(L.theta);
+      if ((rc = gen_tiles_z(c, iz, th, tiles.p))) break;
+      const size_t smem = sizeof(T) * ((size_t)kMB * 2 * kCW * 4 + (size_t)2 * N * (kMB + 1));
+      cudaFuncSetAttribute(r2_simt_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      const T* Yz = (const T*)Yd.p + (size_t)iz * nO * nti * 32;
+      r2_simt_kernel<T, T><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
+          (const T*)tiles.p, Yz, (const T*)Icx.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
+          (T*)es_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO);
+      r2_simt_kernel<T, T><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
+          (const T*)tiles.p, Yz, (const T*)Icw.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
+          (T*)ew_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO);
+      PRD_CUDA_TRY(c, cudaPeekAtLastError());
+    }
+    if (rc) break;
+    // observer frame, normalisation, thermal part, formal solution along the LOS
+    spline_M_kernel<T><<<ceil_div(nz * 4, 128), 128, 0, c->stream>>>((const T*)es_bar.p, (T*)M.p, (const double*)c->sp.p, nz, 1, N);
+    spline_eval_kernel<T, T><<<ceil_div((long long)nz * N, 256), 256, 0, c->stream>>>(
+        (const T*)es_bar.p, (const T*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
+        (T*)es.p, nz, 1, N);
+    spline_M_kernel<T><<<ceil_div(nz * 4, 128), 128, 0, c->stream>>>((const T*)ew_bar.p, (T*)M.p, (const double*)c->sp.p, nz, 1, N);
+    spline_eval_kernel<T, T><<<ceil_div((long long)nz * N, 256), 256, 0, c->stream>>>(
+        (const T*)ew_bar.p, (const T*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
+        (T*)ew.p, nz, 1, N);
+    los_combine_kernel<T><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const T*)es.p, (const T*)ew.p,
+                                                                       (const T*)ktd.p, (const T*)ethd.p,
+                                                                       (const double*)fac.p, (T*)eps.p, nz, N);
+    delo_kernel<T, T><<<ceil_div(N, 128), 128, 0, c->stream>>>((const T*)eps.p, (const T*)ktd.p, (const double*)dmu.p,
+                                                             nullptr, (T*)lam.p, nz, 1, N, 1, c->WT[0]);
+    PRD_CUDA_TRY(c, cudaMemcpyAsync(out + (size_t)l * N * 4, (const T*)lam.p + (size_t)(nz - 1) * N * 4,
+                                    (size_t)N * 4 * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  dfree(wtd);
+  cleanup();
+  return rc;
+}
+
+int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, void* out) {
+  if (c->prec == PRD_FP64) return emergent_T<double>(c, (const double*)x, nlos, mu, chi, (double*)out);
+  return emergent_T<float>(c, (const float*)x, nlos, mu, chi, (float*)out);
 }
 
 }  // namespace prd

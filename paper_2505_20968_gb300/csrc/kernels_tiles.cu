@@ -432,6 +432,50 @@ int launch_tiles(Ctx* c) {
   return PRD_OK;
 }
 
+// Tiles of one height for an arbitrary list of scattering angles (one class
+// per entry), stored like the main tiles: [class][group means, deviations][n][2N].
+int gen_tiles_z(Ctx* c, int iz, const std::vector<double>& thetas, void* outT) {
+  int rc = upload_consts(c);
+  if (rc) return rc;
+  const int N = c->nnu, ncl = (int)thetas.size();
+  std::vector<int> trip;
+  for (int t = 0; t < c->ntrip; ++t) { trip.push_back(c->trip_k[t]); trip.push_back(c->trip_l[t]); trip.push_back(c->trip_lp[t]); }
+  std::vector<double> aath = c->aa_theta, aaw = c->aa_w;
+  if (aath.empty()) { aath.push_back(0); aaw.push_back(0); }
+  DBuf du, dQ, da, dsh, dtr, dth, dath, daw, scr, dgrp;
+  auto cleanup = [&]() { dfree(du); dfree(dQ); dfree(da); dfree(dsh); dfree(dtr); dfree(dth); dfree(dath);
+                         dfree(daw); dfree(scr); dfree(dgrp); };
+  const long long nrows = (long long)ncl * c->ntrip * N;
+  if ((rc = upload(c, du, c->u.data(), c->u.size() * 8)) || (rc = upload(c, dQ, c->Q.data(), c->Q.size() * 8)) ||
+      (rc = upload(c, da, c->a.data(), c->nz * 8)) || (rc = upload(c, dsh, c->shift.data(), c->shift.size() * 8)) ||
+      (rc = upload(c, dtr, trip.data(), trip.size() * 4)) || (rc = upload(c, dth, thetas.data(), thetas.size() * 8)) ||
+      (rc = upload(c, dath, aath.data(), aath.size() * 8)) || (rc = upload(c, daw, aaw.data(), aaw.size() * 8)) ||
+      (rc = dalloc(c, scr, (size_t)nrows * 2 * N * 8)) ||
+      (rc = upload(c, dgrp, c->trip_grp.data(), c->trip_grp.size() * 4))) {
+    cleanup();
+    return rc;
+  }
+  TileParams p{(const double*)du.p, (const double*)dQ.p, (const double*)da.p, (const double*)dsh.p,
+               (const int*)dtr.p, (const double*)dth.p, (const double*)dath.p, (const double*)daw.p,
+               (int)c->aa_theta.size(), N, c->nu_st, c->nl_st, c->ntrip, ncl, iz, c->mode == PRD_MODE_AA ? 1 : 0};
+  const size_t smem = (size_t)kRowsPerBlock * 4 * N * sizeof(double);
+  cudaFuncSetAttribute(tile_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  tile_kernel<double, double><<<ceil_div(nrows, kRowsPerBlock), 32 * kRowsPerBlock, smem, c->stream>>>(
+      p, (double*)scr.p, (int)nrows);
+  const int rowlen = 2 * N * N;
+  const int sb = ceil_div((long long)ncl * rowlen, 256);
+  if (c->prec == PRD_FP64)
+    group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)outT, (const int*)dgrp.p, ncl,
+                                                          c->ntrip, c->ngrp, rowlen);
+  else
+    group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)outT, (const int*)dgrp.p, ncl,
+                                                         c->ntrip, c->ngrp, rowlen);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cleanup();
+  if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("line-of-sight tiles: ") + cudaGetErrorString(e));
+  return PRD_OK;
+}
+
 // Angle-averaged tiles and R_III incident weights of the unmagnetised J-level
 // components (shifts shift_g[z][g]) for the preconditioner, returned in FP64.
 int launch_pc_tiles(Ctx* c, const std::vector<double>& shift_g, std::vector<double>& aa_tiles,

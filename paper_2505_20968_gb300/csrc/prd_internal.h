@@ -75,6 +75,8 @@ struct Ctx {
   std::vector<double> shift;             // [z][ku][kl]
   std::vector<cplx> alpha, beta;         // [z][ku][kv]
   std::vector<cplx> amp;                 // [z][o][2][ku][kl]
+  std::vector<double> Dmat;              // [z][3][ku][kl] dipole elements <ku|d_q|kl>
+  std::vector<double> Rmag;              // [z][3][3] rows of the magnetic frame
   std::vector<double> Q;                 // [z][n][n] natural-spline 2nd-derivative map
   std::vector<int> theta_node_cls;       // AA: unused
   int n_aa_theta = 0;
@@ -112,6 +114,12 @@ struct Ctx {
   std::vector<DBuf> krylov;
   DBuf gm_w, gm_r, gm_t, gm_dots;
   std::vector<void*> owned;
+  // stage timing (prd_set_profiling): events on the ctx stream around each stage
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long stage_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   ~Ctx();
 };
@@ -138,6 +146,20 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // ---- setup pieces (host_setup.cpp)
 int build_host_tables(Ctx* c);
 int build_device_tables(Ctx* c);
+// polarisation amplitudes a[alpha][ku][kl] = <ku| e_alpha . d |kl> of any direction
+void dir_amplitudes(const Ctx* c, int iz, double mu, double chi, cplx* out);
+// tables of one extra line of sight (emergent_stokes)
+struct LosTables {
+  std::vector<double> Y;       // [z][nO][ntile][32]  pairs (LOS, o')
+  std::vector<double> theta;   // [z? no: nO]  scattering angle LOS-o'
+  std::vector<double> rout;    // [z][nuv][nl][4][2]
+  std::vector<double> kt;      // [z][N][10]
+  std::vector<double> epsth;   // [z][N][4]
+  std::vector<int> kidx;       // [z][N]   back-interpolation intervals
+  std::vector<double> tt;      // [z][N]
+};
+void los_tables(const Ctx* c, double mu, double chi, LosTables& L);
+int gen_tiles_z(Ctx* c, int iz, const std::vector<double>& thetas, void* outT);
 
 // ---- device launchers (kernels_*.cu)
 int launch_tiles(Ctx* c);
@@ -154,5 +176,12 @@ int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* ch
 int upload_faddeeva_coeffs(Ctx* c);
 
 size_t nvec(const Ctx* c);   // 4*nz*nO*nnu
+
+// Stage ids for prd_stage_times.
+enum Stage { ST_S1 = 0, ST_S5 = 1, ST_S3 = 2, ST_S6 = 3, ST_S7 = 4, ST_PRE = 5 };
+// Begin / end a timed stage (no-ops unless profiling is on).
+void stage_begin(Ctx* c, int stage, cudaEvent_t* out);
+void stage_end(Ctx* c, int stage, cudaEvent_t start);
+void stage_collect(Ctx* c);
 
 }  // namespace prd

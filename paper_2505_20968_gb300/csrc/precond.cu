@@ -251,8 +251,4 @@ int apply_precond(Ctx* c, const void* y, void* x) {
   return precond_T<float>(c, (const float*)y, (float*)x);
 }
 
-int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, void* out) {
-  return fail(c, PRD_E_STATE, "emergent_stokes not available in this build");
-}
-
 }  // namespace prd

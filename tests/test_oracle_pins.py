@@ -322,3 +322,15 @@ def test_sqrt_eps_law():
     S = (P.apply_sigma(x) + P.eps_th)[..., 0] / P.eta1
     assert abs(S[-1, 0, P.nN // 2] / np.sqrt(eps) - 1.0) < 0.08
     assert abs(S[0, 0, P.nN // 2] - 1.0) < 0.01          # thermalised at depth
+
+
+def test_emergent_along_grid_direction_is_the_solution():
+    """The extra formal solution of Sect. 6.2, taken along a direction of the
+    grid, must return the solution's own emergent Stokes vector."""
+    cfg = inputs.twolevel_slab(n_z=6, n_x=9, n_mu_half=2, n_chi=4, eps=1e-2)
+    cfg["atm"]["B_G"][:] = 30.0
+    P = Problem(cfg)
+    x, _ = P.solve(tol=1e-13)
+    for o in [i for i in range(P.nO) if P.mu[i] > 0][:3]:
+        e = P.emergent(x, P.mu[o], P.chi[o])
+        assert np.max(np.abs(e - x[-1, o])) < 1e-10 * np.max(np.abs(x[-1, o]))
