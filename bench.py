@@ -130,6 +130,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-tol", type=float, default=1e-8)
+    ap.add_argument("--workload", default="mgii", choices=["mgii", "mgii_small"],
+                    help="mgii_small (8 heights) is only for ncu captures of single kernels")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -137,7 +139,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    cfg = inputs.mgii(seed=2 + rank)
+    cfg = inputs.mgii(seed=2 + rank) if args.workload == "mgii" else inputs.mgii(n_z=8, seed=2 + rank)
     workload = {"workload": "mgii_hk_like: two-term Mg II h&k, 70 heights, 200 wavelengths, "
                             "4+4 GL mu x 8 chi (64 directions), B<=100 G, |v|<=5 km/s, N=3,584,000",
                 "precision": "fp32 tiles/vectors, fp64 reductions", "parallelism": f"{world} independent instances",
