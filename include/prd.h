@@ -158,6 +158,22 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
 int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu,
                         const double* chi, void* out_dev);
 
+/* Same result as prd_apply_sigma, for callers that must not allocate device
+ * memory at call time: code that runs while another framework owns the
+ * allocator, inside allocation-free real-time or replay loops, or in
+ * environments where cudaMalloc is not permitted after initialisation.  This
+ * call allocates nothing (no cudaMalloc/cudaFree, no allocating library call):
+ * its intermediates (comoving field, spline second derivatives, comoving
+ * emissivity, R_III moments) live in one static device array of 64 MiB that
+ * every GPU which loads the library holds until the process exits.  A problem
+ * whose intermediates need more than 64 MiB is rejected with PRD_E_ARG.  The
+ * first call on a device looks up that array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the array and overwrites it, so calls that overlap on the GPU (other
+ * streams, other contexts on the same device) race.  The paper has no
+ * counterpart: this is a deployment variant of the Sigma apply. */
+int prd_apply_sigma_noalloc(prd_ctx* ctx, const void* x_dev, void* eps_dev);
+
 /* Stage timing (tracing).  When on, CUDA events recorded on the ctx stream
  * bracket each stage of every apply; prd_stage_times returns the accumulated
  * milliseconds and call counts per stage (index 0: S1 comoving interpolation,

@@ -35,7 +35,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_set_atmosphere", "prd_set_quadrature", "prd_setup", "prd_sizes", "prd_directions",
            "prd_workspace_bytes", "prd_rhs", "prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator",
            "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
-           "prd_set_profiling", "prd_stage_times"]
+           "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc"]
 
 
 def lib():
@@ -62,7 +62,8 @@ def lib():
         L.prd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         for f in ("prd_rhs",):
             getattr(L, f).argtypes = [P, P]
-        for f in ("prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator", "prd_apply_preconditioner"):
+        for f in ("prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator", "prd_apply_preconditioner",
+                  "prd_apply_sigma_noalloc"):
             getattr(L, f).argtypes = [P, P, P]
         L.prd_set_precond_sweeps.argtypes = [P, I]
         L.prd_solve.argtypes = [P, D, I, I, P, P, ctypes.POINTER(I), DP, DP]
@@ -150,6 +151,12 @@ class PRD:
         self._stream()
         out = self.empty() if out is None else out
         self._check(lib().prd_apply_sigma(self.h, self._vec(x), self._vec(out)))
+        return out
+
+    def apply_sigma_noalloc(self, x, out):
+        """Sigma x with the library's static scratch (allocates nothing; out must be given)."""
+        self._stream()
+        self._check(lib().prd_apply_sigma_noalloc(self.h, self._vec(x), self._vec(out)))
         return out
 
     def apply_lambda(self, eps, out=None):

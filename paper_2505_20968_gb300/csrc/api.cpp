@@ -120,9 +120,6 @@ static int setup(Ctx* c) {
 using prd::Ctx;
 using prd::fail;
 
-struct prd_ctx {
-  Ctx c;
-};
 
 #define CTX_OR_ARG(ctx)                 \
   if (!(ctx)) return PRD_E_ARG;         \

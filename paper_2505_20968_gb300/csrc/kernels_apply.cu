@@ -7,6 +7,7 @@
 //   S6  frame change back (u_n + u_b(z,Omega)) and Kirchhoff factor f (App. E)
 //   S7+S8  DELO-linear sweep per ray, y = x - Lambda eps      (Sect. 3)
 #include <cstdio>
+#include <mutex>
 #include "prd_internal.h"
 #include "device_common.cuh"
 
@@ -369,7 +370,7 @@ __global__ void fill_planck_kernel(T* __restrict__ x, const double* __restrict__
 // ------------------------------------------------------------------ launchers
 template <typename T, typename A>
 static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = nullptr, A* M_ext = nullptr,
-                   A* Ic_ext = nullptr) {
+                   A* Ic_ext = nullptr, double* J_ext = nullptr) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
   A* Mb = M_ext ? M_ext : (A*)c->scratch1.p;
@@ -387,10 +388,11 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   // S5 (initialises eps_bar)
   stage_begin(c, ST_S5, &e0);
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
-  PRD_CUDA_TRY(c, cudaMemsetAsync(c->r3J.p, 0, c->r3J.bytes, c->stream));
+  double* J = J_ext ? J_ext : (double*)c->r3J.p;
+  PRD_CUDA_TRY(c, cudaMemsetAsync(J, 0, (size_t)nz * nuv * 2 * sizeof(double), c->stream));
   r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
-                                                        (double*)c->r3J.p, nO, N, nq, c->nl_st);
-  r3_out_kernel<T, A><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)c->r3J.p, (const T*)c->r3ab.p,
+                                                        J, nO, N, nq, c->nl_st);
+  r3_out_kernel<T, A><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)J, (const T*)c->r3ab.p,
                                                                (const T*)c->r3out.p, (const T*)c->r3prof.p, eb, nz,
                                                                nO, N, nuv, c->nl_st);
   stage_end(c, ST_S5, e0);
@@ -672,4 +674,62 @@ int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* ch
   return emergent_T<float>(c, (const float*)x, nlos, mu, chi, (float*)out);
 }
 
+// ------------------------------------------------------------------ static scratch
+// Scratch of prd_apply_sigma_noalloc: one file-scope device array, present on
+// every GPU that loads the library until the process exits.
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_sigma_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {nullptr};   // device address of g_sigma_scratch per device
+}  // namespace
+
+// Device address of the static scratch on the current device, looked up once
+// per device (the host-side symbol is only a stand-in and must not be passed
+// to a kernel).
+static int static_scratch(Ctx* c, void** out) {
+  if (c->device < 0 || c->device >= 64) return fail(c, PRD_E_ARG, "device index out of range for static scratch");
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[c->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sigma_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(c, PRD_E_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_scratch_ptr[c->device] = p;
+  }
+  *out = g_scratch_ptr[c->device];
+  return PRD_OK;
+}
+
+template <typename T>
+static int sigma_static_T(Ctx* c, const T* x, T* eps) {
+  const size_t nv = nvec(c);
+  const size_t nuv = (size_t)c->nu_st * c->nu_st;
+  const size_t jbytes = ((size_t)c->nz * nuv * 2 * sizeof(double) + 255) / 256 * 256;
+  const size_t vb = (nv * sizeof(T) + 255) / 256 * 256;
+  if (jbytes + 3 * vb > kStaticScratchBytes)
+    return fail(c, PRD_E_ARG, "problem needs " + std::to_string((jbytes + 3 * vb) >> 20) +
+                                  " MiB of scratch; prd_apply_sigma_noalloc supports at most 64 MiB");
+  void* base = nullptr;
+  int rc = static_scratch(c, &base);
+  if (rc) return rc;
+  unsigned char* b = (unsigned char*)base;
+  double* J = (double*)b;
+  T* M = (T*)(b + jbytes);
+  T* Ic = (T*)(b + jbytes + vb);
+  T* eb = (T*)(b + jbytes + 2 * vb);
+  return sigma_T<T, T>(c, x, eps, true, eb, M, Ic, J);
+}
+
 }  // namespace prd
+
+extern "C" int prd_apply_sigma_noalloc(prd_ctx* ctx, const void* x_dev, void* eps_dev) {
+  if (!ctx) return PRD_E_ARG;
+  prd::Ctx* c = &ctx->c;
+  cudaSetDevice(c->device);
+  if (!c->ready) return prd::fail(c, PRD_E_STATE, "call prd_setup first");
+  if (!x_dev || !eps_dev || x_dev == eps_dev) return prd::fail(c, PRD_E_ARG, "x_dev/eps_dev NULL or aliased");
+  if (c->prec == PRD_FP64) return prd::sigma_static_T<double>(c, (const double*)x_dev, (double*)eps_dev);
+  return prd::sigma_static_T<float>(c, (const float*)x_dev, (float*)eps_dev);
+}

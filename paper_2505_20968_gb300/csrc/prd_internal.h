@@ -185,3 +185,8 @@ void stage_end(Ctx* c, int stage, cudaEvent_t start);
 void stage_collect(Ctx* c);
 
 }  // namespace prd
+
+// The opaque handle of the C ABI.
+struct prd_ctx {
+  prd::Ctx c;
+};
