@@ -141,6 +141,16 @@ int prd_apply_preconditioner(prd_ctx* ctx, const void* y_dev, void* x_dev);
 /* Set the number of inner sweeps m_in (>= 1, default 2) of the preconditioner. */
 int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
 
+/* Options.  PRD_OPT_TENSOR_CORES (FP32 only): 1 runs the R_II contraction on
+ * the tcgen05 tensor cores (TMA-fed tiles, TMEM accumulators, 3xTF32 split
+ * products), 0 on the CUDA cores.  PRD_OPT_PRECOND_SWEEPS: m_in as above. */
+enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2 };
+int prd_set_option(prd_ctx* ctx, int option, int value);
+/* Synchronise the ctx stream and report device-side failures: a CUDA error,
+ * or PRD_E_TIMEOUT if a bounded wait inside a kernel expired since the last
+ * call (the kernel then returned early and its output is invalid). */
+int prd_device_status(prd_ctx* ctx);
+
 /* Left-preconditioned restarted GMRES(restart) (Sect. 5.1-5.2) from x0_dev
  * (NULL = zero) into x_dev; stops when the unpreconditioned relative residual
  * ||b - A x||/||b|| < tol (checked in FP64).  *iters receives the number of

@@ -35,7 +35,8 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_set_atmosphere", "prd_set_quadrature", "prd_setup", "prd_sizes", "prd_directions",
            "prd_workspace_bytes", "prd_rhs", "prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator",
            "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
-           "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc"]
+           "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
+           "prd_device_status"]
 
 
 def lib():
@@ -69,6 +70,8 @@ def lib():
         L.prd_solve.argtypes = [P, D, I, I, P, P, ctypes.POINTER(I), DP, DP]
         L.prd_emergent_stokes.argtypes = [P, P, I, DP, DP, P]
         L.prd_set_profiling.argtypes = [P, I]
+        L.prd_set_option.argtypes = [P, I, I]
+        L.prd_device_status.argtypes = [P]
         L.prd_stage_times.argtypes = [P, DP, ctypes.POINTER(ctypes.c_int64), I]
         _lib = L
     return _lib
@@ -176,6 +179,12 @@ class PRD:
         out = self.empty() if out is None else out
         self._check(lib().prd_apply_preconditioner(self.h, self._vec(y), self._vec(out)))
         return out
+
+    def set_tensor_cores(self, on=True):
+        self._check(lib().prd_set_option(self.h, 1, 1 if on else 0))
+
+    def device_status(self):
+        self._check(lib().prd_device_status(self.h))
 
     def set_precond_sweeps(self, m):
         self._check(lib().prd_set_precond_sweeps(self.h, m))

@@ -43,7 +43,9 @@ static void free_all(Ctx* c) {
   DBuf* bufs[] = {&c->tiles, &c->Y, &c->r3w, &c->r3in, &c->r3out, &c->r3prof, &c->r3J, &c->r3ab, &c->kt,
                   &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk, &c->cls_dev, &c->dmu,
                   &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
-                  &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots};
+                  &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
+                  &c->tc_err};
+  c->tc_ready = false;
   for (DBuf* b : bufs) dfree(*b);
   for (auto& b : c->krylov) dfree(b);
   c->krylov.clear();
@@ -108,6 +110,7 @@ static int setup(Ctx* c) {
   if ((rc = build_device_tables(c))) return rc;
   if ((rc = dalloc(c, c->gm_t, nvec(c) * c->esz))) return rc;
   if ((rc = launch_tiles(c))) return rc;
+  if ((rc = r2_tc_prepare(c))) return rc;
   if ((rc = compute_normalisation(c))) return rc;
   if ((rc = launch_precond_setup(c))) return rc;
   PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -332,7 +335,12 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
   NEED_READY();
   if (!x_dev || !(tol > 0) || max_iter < 1 || restart < 1) return fail(c, PRD_E_ARG, "bad solve arguments");
   try {
-    return prd::solve(c, tol, max_iter, restart, x0_dev, x_dev, iters, true_rel_res, res_history);
+    int rc = prd::solve(c, tol, max_iter, restart, x0_dev, x_dev, iters, true_rel_res, res_history);
+    if (c->tc_err.p) {
+      const int rt = prd::r2_tc_check_error(c);
+      if (rt) return rt;
+    }
+    return rc;
   } catch (const std::exception& e) {
     return fail(c, PRD_E_NOMEM, std::string("host exception in solve: ") + e.what());
   }
@@ -350,6 +358,29 @@ int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double*
   } catch (const std::exception& e) {
     return fail(c, PRD_E_NOMEM, std::string("host exception: ") + e.what());
   }
+}
+
+int prd_set_option(prd_ctx* ctx, int option, int value) {
+  CTX_OR_ARG(ctx);
+  if (option == PRD_OPT_TENSOR_CORES) {
+    if (value && c->prec != PRD_FP32) return fail(c, PRD_E_ARG, "tensor-core contraction needs PRD_FP32");
+    c->use_tc = value ? 1 : 0;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_PRECOND_SWEEPS) {
+    if (value < 0 || value > 64) return fail(c, PRD_E_ARG, "m_in must be in [0, 64]");
+    c->m_in = value;
+    return PRD_OK;
+  }
+  return fail(c, PRD_E_ARG, "unknown option");
+}
+
+int prd_device_status(prd_ctx* ctx) {
+  CTX_OR_ARG(ctx);
+  PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  PRD_CUDA_TRY(c, cudaGetLastError());
+  if (c->tc_err.p) return prd::r2_tc_check_error(c);
+  return PRD_OK;
 }
 
 int prd_set_profiling(prd_ctx* ctx, int on) {

@@ -8,6 +8,7 @@
 //   S7+S8  DELO-linear sweep per ray, y = x - Lambda eps      (Sect. 3)
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include "prd_internal.h"
 #include "device_common.cuh"
 
@@ -308,15 +309,18 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
       I[0] = (boundary && up) ? (A)WT0 : (A)0;
       I[1] = I[2] = I[3] = (A)0;
     } else {
-      // D = I_k - S_k solves (Id + b K'_k) D = e (I_{k-1} - S_k) + a (S_{k-1} - S_k)
-      //      - a K'_{k-1} I_{k-1} - b K'_k S_k,  with b = 1 - e - a used only
-      // in the dichroic terms: a constant unpolarised source is reproduced
-      // exactly whatever the rounding of the stored weights.
+      // Optically thick step (e = exp(-dtau) <= 1/2): solve for D = I_k - S_k,
+      //   (Id + b K'_k) D = e (I_{k-1} - S_k) + a (S_{k-1} - S_k) - a K'_{k-1} I_{k-1} - b K'_k S_k,
+      // which reproduces a constant unpolarised source exactly whatever the
+      // rounding of the stored weights (b = 1 - e - a enters only the dichroic
+      // terms).  Thin step: the standard form for I_k, free of the
+      // cancellation I_{k-1} - S_k when I << S.
       const A e = t[7], al = t[8], be = t[9];
+      const bool thick = e <= (A)0.5;
       A rhs[4];
       for (int i = 0; i < 4; ++i) {
-        A v = e * (I[i] - S[i]) + al * (Sp[i] - S[i]);
-        for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + be * Kk[i][j] * S[j];
+        A v = thick ? e * (I[i] - S[i]) + al * (Sp[i] - S[i]) : e * I[i] + al * Sp[i] + be * S[i];
+        for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + (thick ? be * Kk[i][j] * S[j] : (A)0);
         rhs[i] = v;
       }
       A M4[4][4];
@@ -336,7 +340,7 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
         for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * D[cc];
         D[r] = v / M4[r][r];
       }
-      for (int i = 0; i < 4; ++i) I[i] = S[i] + D[i];
+      for (int i = 0; i < 4; ++i) I[i] = thick ? S[i] + D[i] : D[i];
     }
     for (int s = 0; s < 4; ++s) {
       out[pt * 4 + s] = x_sub ? x_sub[pt * 4 + s] - I[s] : I[s];
@@ -399,11 +403,22 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   // S3 + S4
   stage_begin(c, ST_S3, &e0);
   const int nchunk = (c->max_cout + kCW - 1) / kCW;
+  if constexpr (std::is_same<T, float>::value && std::is_same<A, float>::value) {
+    if (c->use_tc && c->tc_ready) {
+      int rc = r2_tc_launch(c, Ic, eb);
+      if (rc) return rc;
+      stage_end(c, ST_S3, e0);
+      goto s6;
+    }
+  }
+  {
   const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
   cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
       (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
   stage_end(c, ST_S3, e0);
+  }
+s6:
   // S6
   stage_begin(c, ST_S6, &e0);
   spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, Mb, sp, nz, nO, N);

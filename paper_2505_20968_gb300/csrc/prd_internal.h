@@ -114,6 +114,11 @@ struct Ctx {
   std::vector<DBuf> krylov;
   DBuf gm_w, gm_r, gm_t, gm_dots;
   std::vector<void*> owned;
+  // tensor-core contraction (r2_tc.cu)
+  alignas(64) unsigned char tmap[128] = {};
+  DBuf tc_err;
+  bool tc_ready = false;
+  int use_tc = 0;
   // stage timing (prd_set_profiling): events on the ctx stream around each stage
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -176,6 +181,9 @@ int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* ch
 int upload_faddeeva_coeffs(Ctx* c);
 
 size_t nvec(const Ctx* c);   // 4*nz*nO*nnu
+int r2_tc_prepare(Ctx* c);
+int r2_tc_launch(Ctx* c, const float* Ic, float* eb);
+int r2_tc_check_error(Ctx* c);
 
 // Stage ids for prd_stage_times.
 enum Stage { ST_S1 = 0, ST_S5 = 1, ST_S3 = 2, ST_S6 = 3, ST_S7 = 4, ST_PRE = 5 };

@@ -65,7 +65,8 @@ __global__ void pc_delo_kernel(const T* __restrict__ eps, const T* __restrict__ 
     const T* t = kt + pt * 10;
     const T S = eps[pt * 4] * t[6];
     if (p == 0) I = 0;
-    else I = S + t[7] * (I - S) + t[8] * (Sp - S);
+    else if (t[7] <= (T)0.5) I = S + t[7] * (I - S) + t[8] * (Sp - S);   // thick: photon-exact form
+    else I = t[7] * I + t[8] * Sp + t[9] * S;                              // thin: standard form
     out[pt * 4] = I;
     Sp = S;
   }

@@ -147,3 +147,22 @@ def test_emergent_stokes_off_grid(name):
     assert np.max(np.abs(out[..., 0] - ref[..., 0]) / ref[..., 0]) < tol
     for s in (1, 2, 3):
         assert np.max(np.abs(out[..., s] / out[..., 0] - ref[..., s] / ref[..., 0])) < (1e-9 if P.prec == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("name", ["mgii", "hi", "hi_aa"])
+def test_tensor_core_contraction(name):
+    """tcgen05 R_II contraction (3xTF32) against the CUDA-core contraction and
+    the oracle; no bounded wait may expire."""
+    cfg, P, G = get(name)
+    x = _t(G["x"], P)
+    P.set_tensor_cores(False)
+    e_simt = P.apply_sigma(x).cpu().numpy().astype(np.float64)
+    P.set_tensor_cores(True)
+    e_tc = P.apply_sigma(x).cpu().numpy().astype(np.float64)
+    P.device_status()
+    P.set_tensor_cores(False)
+    eo = G["sigma"]
+    for iz in range(P.nz):
+        scale = np.max(np.abs(eo[iz, ..., 0]))
+        assert np.max(np.abs(e_tc[iz] - e_simt[iz])) < 2e-6 * scale, f"height {iz}"
+        assert np.max(np.abs(e_tc[iz] - eo[iz])) < 2e-5 * scale, f"height {iz}"
