@@ -229,11 +229,12 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("kernel") == "r2_simt_kernel" and tr.get("workload") == "mgii":
+        if tr.get("kernel") == "r2_tc_kernel" and tr.get("workload") == "mgii":
             traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
-    roofline = {"bound": "hbm", "kernel": "r2_simt_kernel (S3+S4 R_II contraction)", "achieved": achieved,
+    roofline = {"bound": "hbm", "kernel": "r2_tc_kernel (S3+S4 R_II contraction, tcgen05 3xTF32)",
+                "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": src, "traffic": traffic, "algorithmic_bytes_per_launch": tile_bytes,
                 "launch_ms": r2_ms, "stage_ms": {k: v[0] / max(v[1], 1) for k, v in st.items()}}

@@ -149,6 +149,7 @@ int prd_create(prd_ctx** out, int device, int precision) {
   h->c.device = device;
   h->c.prec = precision;
   h->c.esz = precision == PRD_FP64 ? 8 : 4;
+  h->c.use_tc = precision == PRD_FP32 ? 1 : 0;   // tcgen05 contraction by default in FP32
   *out = h;
   return PRD_OK;
 }
