@@ -97,13 +97,14 @@ static int setup(Ctx* c) {
   int rc = build_host_tables(c);
   if (rc) return rc;
   // memory check for the tiles
-  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * 2 * c->nnu * c->esz;
+  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * c->ld() * c->esz;
   size_t fr = 0, tot = 0;
   PRD_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
   if (tile_bytes > fr * 0.9)
     return fail(c, PRD_E_NOMEM, "R_II tiles need " + std::to_string(tile_bytes >> 20) + " MiB, device has " +
                                     std::to_string(fr >> 20) + " MiB free");
   if ((rc = dalloc(c, c->tiles, tile_bytes))) return rc;
+  PRD_CUDA_TRY(c, cudaMemset(c->tiles.p, 0, tile_bytes));   // row padding (ld > 2N) stays zero
   const int nq = c->nu_st * c->nu_st * c->nl_st;
   if ((rc = dalloc(c, c->r3w, (size_t)c->nz * nq * 2 * c->nnu * c->esz))) return rc;
   if ((rc = upload(c, c->dmu, c->mu.data(), c->mu.size() * 8))) return rc;

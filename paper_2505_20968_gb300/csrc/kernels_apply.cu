@@ -170,7 +170,7 @@ template <typename T, typename A>
 __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tiles, const T* __restrict__ Y,
                                                       const A* __restrict__ Ic, const int* __restrict__ cls,
                                                       A* __restrict__ eb, int ncls, int ntrip, int nO, int N,
-                                                      int npairs) {
+                                                      int npairs, int ld) {
   const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
   const int* cout_ptr = cls;
   const int* cout_dir = cls + ncls + 1;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[r][i] = (A)0;
   const int nrows = (N + 15) / 16;
-  const size_t tile_sz = (size_t)N * 2 * N;
+  const size_t tile_sz = (size_t)N * ld;
   const T* tbase = tiles + ((size_t)iz * ncls + c) * ntrip * tile_sz;
   // Z-building role: thread -> (e = tid & 15, m = tid >> 4)
   const int ze = tid & 15, zm = tid >> 4;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
         const int h = (idx / kMB) & 1;
         const int n = idx / (2 * kMB);
         const int m = m0 + mm;
-        Asb[(h * N + n) * (kMB + 1) + mm] = (m < N) ? tile[(size_t)n * 2 * N + h * N + m] : (T)0;
+        Asb[(h * N + n) * (kMB + 1) + mm] = (m < N) ? tile[(size_t)n * ld + h * N + m] : (T)0;
       }
       __syncthreads();
 #pragma unroll 4
@@ -415,7 +415,7 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
   cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
-      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs);
+      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs, c->ld());
   stage_end(c, ST_S3, e0);
   }
 s6:
@@ -570,31 +570,42 @@ __global__ void planck_comoving_kernel(T* __restrict__ Ic, const double* __restr
 }
 
 // eps(z, n) = (eps_sc with f) + eps_th;  f = (1-eps) W_T eta_I / num_I
-template <typename T>
-__global__ void los_combine_kernel(const T* __restrict__ es, const T* __restrict__ ew, const T* __restrict__ kt,
-                                   const T* __restrict__ eth, const double* __restrict__ fac, T* __restrict__ out,
+template <typename T, typename A>
+__global__ void los_combine_kernel(const A* __restrict__ es, const A* __restrict__ ew, const T* __restrict__ kt,
+                                   const T* __restrict__ eth, const double* __restrict__ fac, A* __restrict__ out,
                                    int nz, int N) {
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= nz * N) return;
   const int iz = pt / N;
   const double f = fac[iz] / ((double)kt[pt * 10 + 6] * (double)ew[pt * 4]);
-  out[pt * 4] = (T)((double)es[pt * 4] * f + (double)eth[pt * 4]);
-  for (int s = 1; s < 4; ++s) out[pt * 4 + s] = es[pt * 4 + s] + eth[pt * 4 + s];
+  out[pt * 4] = (A)((double)es[pt * 4] * f + (double)eth[pt * 4]);
+  for (int s = 1; s < 4; ++s) out[pt * 4 + s] = es[pt * 4 + s] + (A)eth[pt * 4 + s];
 }
 
-template <typename T>
+template <typename S, typename D>
+__global__ void cast_kernel(const S* __restrict__ in, D* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (D)in[i];
+}
+
+// T: precision of the stored tables and of x / out; A: precision of the fields
+// along the line of sight (double in FP32 mode, like the FP64-accumulated
+// residual path, so the emergent spectrum carries no FP32 cancellation).
+
+template <typename T, typename A>
 static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const double* chis, T* out) {
   const int nz = c->nz, nO = c->nO, N = c->nnu, nti = c->ntile(), nuv = c->nu_st * c->nu_st, nl = c->nl_st;
   const int nq = nuv * nl;
   const long long npt = (long long)nz * nO * N;
-  const size_t tz = (size_t)nO * nti * N * 2 * N * sizeof(T);   // tiles of one height, all LOS classes
-  DBuf Icx, Icw, Jx, Jw, tiles, Yd, rout, ktd, ethd, kidx, ttd, es_bar, ew_bar, es, ew, M, eps, lam, fac, dmu, clsd;
+  const size_t tz = (size_t)nO * nti * N * c->ld() * sizeof(T);   // tiles of one height, all LOS classes
+  DBuf Icx, Icw, Jx, Jw, tiles, Yd, rout, ktd, ethd, kidx, ttd, es_bar, ew_bar, es, ew, M, eps, lam, fac, dmu, clsd,
+      xa, Mx;
   auto cleanup = [&]() {
     DBuf* bs[] = {&Icx, &Icw, &Jx, &Jw, &tiles, &Yd, &rout, &ktd, &ethd, &kidx, &ttd, &es_bar, &ew_bar, &es, &ew,
-                  &M, &eps, &lam, &fac, &dmu, &clsd};
+                  &M, &eps, &lam, &fac, &dmu, &clsd, &xa, &Mx};
     for (DBuf* b : bs) dfree(*b);
   };
-  const size_t vb = nvec(c) * sizeof(T), lb = (size_t)nz * N * 4 * sizeof(T);
+  const size_t vb = nvec(c) * sizeof(A), lb = (size_t)nz * N * 4 * sizeof(A);
   int rc;
   std::vector<double> facv(nz), wt(c->WT);
   for (int iz = 0; iz < nz; ++iz) facv[iz] = (1.0 - c->eps[iz]) * c->WT[iz];
@@ -608,6 +619,7 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       (rc = dalloc(c, Jw, (size_t)nz * nuv * 16)) || (rc = dalloc(c, tiles, tz)) || (rc = dalloc(c, es_bar, lb)) ||
       (rc = dalloc(c, ew_bar, lb)) || (rc = dalloc(c, es, lb)) || (rc = dalloc(c, ew, lb)) || (rc = dalloc(c, M, lb)) ||
       (rc = dalloc(c, eps, lb)) || (rc = dalloc(c, lam, lb)) || (rc = upload(c, fac, facv.data(), nz * 8)) ||
+      (rc = dalloc(c, xa, vb)) || (rc = dalloc(c, Mx, (size_t)nz * nO * N * 4 * sizeof(A))) ||
       (rc = upload(c, clsd, cls.data(), cls.size() * 4))) {
     cleanup();
     return rc;
@@ -615,16 +627,17 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
   DBuf wtd;
   if ((rc = upload(c, wtd, wt.data(), nz * 8))) { cleanup(); return rc; }
   // comoving fields of the solution and of the Planck function, and their R_III moments
-  spline_M_kernel<T><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(x, (T*)c->scratch1.p, (const double*)c->sp.p, nz, nO, N);
-  spline_eval_kernel<T, T><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, (T*)c->scratch1.p, (const int*)c->iin.p,
+  cast_kernel<T, A><<<ceil_div(npt * 4, 256), 256, 0, c->stream>>>(x, (A*)xa.p, npt * 4);
+  spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>((const A*)xa.p, (A*)Mx.p, (const double*)c->sp.p, nz, nO, N);
+  spline_eval_kernel<A, A><<<ceil_div(npt, 256), 256, 0, c->stream>>>((const A*)xa.p, (const A*)Mx.p, (const int*)c->iin.p,
                                                                      (const double*)c->tin.p, (const double*)c->sp.p,
-                                                                     nullptr, (T*)Icx.p, nz, nO, N);
-  planck_comoving_kernel<T><<<ceil_div(npt, 256), 256, 0, c->stream>>>((T*)Icw.p, (const double*)wtd.p, nz, nO, N);
+                                                                     nullptr, (A*)Icx.p, nz, nO, N);
+  planck_comoving_kernel<A><<<ceil_div(npt, 256), 256, 0, c->stream>>>((A*)Icw.p, (const double*)wtd.p, nz, nO, N);
   PRD_CUDA_TRY(c, cudaMemsetAsync(Jx.p, 0, Jx.bytes, c->stream));
   PRD_CUDA_TRY(c, cudaMemsetAsync(Jw.p, 0, Jw.bytes, c->stream));
-  r3_J_kernel<T, T><<<dim3(nq, nz), 256, 0, c->stream>>>((const T*)Icx.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
+  r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>((const A*)Icx.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
                                                         (double*)Jx.p, nO, N, nq, nl);
-  r3_J_kernel<T, T><<<dim3(nq, nz), 256, 0, c->stream>>>((const T*)Icw.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
+  r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>((const A*)Icw.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
                                                         (double*)Jw.p, nO, N, nq, nl);
   PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   const double mu1 = 1.0;
@@ -641,42 +654,42 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       break;
     (void)mu1;
     // R_III parts initialise the comoving rows
-    r3_out_kernel<T, T><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
-        (const double*)Jx.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (T*)es_bar.p, nz, 1, N, nuv, nl);
-    r3_out_kernel<T, T><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
-        (const double*)Jw.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (T*)ew_bar.p, nz, 1, N, nuv, nl);
+    r3_out_kernel<T, A><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
+        (const double*)Jx.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (A*)es_bar.p, nz, 1, N, nuv, nl);
+    r3_out_kernel<T, A><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
+        (const double*)Jw.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (A*)ew_bar.p, nz, 1, N, nuv, nl);
     // R_II: tiles of every height for the LOS classes, then the contraction
     for (int iz = 0; iz < nz && !rc; ++iz) {
       std::vector<double> th(L.theta);
       if ((rc = gen_tiles_z(c, iz, th, tiles.p))) break;
-      const size_t smem = sizeof(T) * ((size_t)kMB * 2 * kCW * 4 + (size_t)2 * N * (kMB + 1));
-      cudaFuncSetAttribute(r2_simt_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
+      cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       const T* Yz = (const T*)Yd.p + (size_t)iz * nO * nti * 32;
-      r2_simt_kernel<T, T><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
-          (const T*)tiles.p, Yz, (const T*)Icx.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
-          (T*)es_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO);
-      r2_simt_kernel<T, T><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
-          (const T*)tiles.p, Yz, (const T*)Icw.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
-          (T*)ew_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO);
+      r2_simt_kernel<T, A><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
+          (const T*)tiles.p, Yz, (const A*)Icx.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
+          (A*)es_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO, c->ld());
+      r2_simt_kernel<T, A><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
+          (const T*)tiles.p, Yz, (const A*)Icw.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
+          (A*)ew_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO, c->ld());
       PRD_CUDA_TRY(c, cudaPeekAtLastError());
     }
     if (rc) break;
     // observer frame, normalisation, thermal part, formal solution along the LOS
-    spline_M_kernel<T><<<ceil_div(nz * 4, 128), 128, 0, c->stream>>>((const T*)es_bar.p, (T*)M.p, (const double*)c->sp.p, nz, 1, N);
-    spline_eval_kernel<T, T><<<ceil_div((long long)nz * N, 256), 256, 0, c->stream>>>(
-        (const T*)es_bar.p, (const T*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
-        (T*)es.p, nz, 1, N);
-    spline_M_kernel<T><<<ceil_div(nz * 4, 128), 128, 0, c->stream>>>((const T*)ew_bar.p, (T*)M.p, (const double*)c->sp.p, nz, 1, N);
-    spline_eval_kernel<T, T><<<ceil_div((long long)nz * N, 256), 256, 0, c->stream>>>(
-        (const T*)ew_bar.p, (const T*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
-        (T*)ew.p, nz, 1, N);
-    los_combine_kernel<T><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const T*)es.p, (const T*)ew.p,
-                                                                       (const T*)ktd.p, (const T*)ethd.p,
-                                                                       (const double*)fac.p, (T*)eps.p, nz, N);
-    delo_kernel<T, T><<<ceil_div(N, 128), 128, 0, c->stream>>>((const T*)eps.p, (const T*)ktd.p, (const double*)dmu.p,
-                                                             nullptr, (T*)lam.p, nz, 1, N, 1, c->WT[0]);
-    PRD_CUDA_TRY(c, cudaMemcpyAsync(out + (size_t)l * N * 4, (const T*)lam.p + (size_t)(nz - 1) * N * 4,
-                                    (size_t)N * 4 * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    spline_M_kernel<A><<<ceil_div(nz * 4, 128), 128, 0, c->stream>>>((const A*)es_bar.p, (A*)M.p, (const double*)c->sp.p, nz, 1, N);
+    spline_eval_kernel<A, A><<<ceil_div((long long)nz * N, 256), 256, 0, c->stream>>>(
+        (const A*)es_bar.p, (const A*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
+        (A*)es.p, nz, 1, N);
+    spline_M_kernel<A><<<ceil_div(nz * 4, 128), 128, 0, c->stream>>>((const A*)ew_bar.p, (A*)M.p, (const double*)c->sp.p, nz, 1, N);
+    spline_eval_kernel<A, A><<<ceil_div((long long)nz * N, 256), 256, 0, c->stream>>>(
+        (const A*)ew_bar.p, (const A*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
+        (A*)ew.p, nz, 1, N);
+    los_combine_kernel<T, A><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const A*)es.p, (const A*)ew.p,
+                                                                          (const T*)ktd.p, (const T*)ethd.p,
+                                                                          (const double*)fac.p, (A*)eps.p, nz, N);
+    delo_kernel<T, A><<<ceil_div(N, 128), 128, 0, c->stream>>>((const A*)eps.p, (const T*)ktd.p, (const double*)dmu.p,
+                                                             nullptr, (A*)lam.p, nz, 1, N, 1, c->WT[0]);
+    cast_kernel<A, T><<<ceil_div(N * 4, 128), 128, 0, c->stream>>>((const A*)lam.p + (size_t)(nz - 1) * N * 4,
+                                                                  out + (size_t)l * N * 4, (long long)N * 4);
     PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
   dfree(wtd);
@@ -685,8 +698,8 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
 }
 
 int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, void* out) {
-  if (c->prec == PRD_FP64) return emergent_T<double>(c, (const double*)x, nlos, mu, chi, (double*)out);
-  return emergent_T<float>(c, (const float*)x, nlos, mu, chi, (float*)out);
+  if (c->prec == PRD_FP64) return emergent_T<double, double>(c, (const double*)x, nlos, mu, chi, (double*)out);
+  return emergent_T<float, double>(c, (const float*)x, nlos, mu, chi, (float*)out);
 }
 
 // ------------------------------------------------------------------ static scratch

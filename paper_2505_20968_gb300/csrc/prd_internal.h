@@ -67,6 +67,8 @@ struct Ctx {
   int ngrp = 1;
   std::vector<int> trip_grp;
   int ntile() const { return ngrp + ntrip; }
+  // row stride of a stored tile: 2N rounded up to 4 elements (16-byte rows for TMA)
+  int ld() const { return (2 * nnu + 3) / 4 * 4; }
   int nq3 = 0;                           // R_III incident combos (ku, kv, kl)
   double nu0 = 0;
   std::vector<double> dnuD, vD;          // per z (Hz, km/s)

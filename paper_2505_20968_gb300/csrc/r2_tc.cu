@@ -9,10 +9,11 @@
 // with Ycomp = Re Y for k = m < N and -Im Y for k = N + m (so that the sum is
 // Re(T Z) over the complex tile T and Z = Y I~).
 //
-// Roles (192 threads): warp 0 streams A with TMA (box 16 x 128 fp32, 64-byte
-// swizzle) and owns the TMEM allocation; warp 1 issues tcgen05.mma; warps 2-5
-// build B in shared memory, split A and B into TF32 hi/lo parts (3 products:
-// hi*hi + hi*lo + lo*hi, FP32-level accuracy) and run the epilogue from TMEM.
+// Roles (320 threads): warp 0 streams A with TMA (box 16 x 128 fp32, 64-byte
+// swizzle) and owns the TMEM allocation; warp 1 issues tcgen05.mma; warps 2-9
+// build B in shared memory from Y (staged per tile) and I~ (staged per K step),
+// split A and B into TF32 hi/lo parts (3 products: hi*hi + hi*lo + lo*hi,
+// FP32-level accuracy) and run the epilogue from TMEM.
 // Accumulators: two M = 128 blocks (rows n < 256) x NCP columns of TMEM.
 // Every mbarrier wait is bounded; on expiry the CTA records an error flag,
 // drains what it issued and returns.
@@ -31,8 +32,15 @@ constexpr int kKC = 16;                       // fp32 per stage along K (64-byte
 constexpr int kABytes = 2 * 128 * kKC * 4;    // two M blocks
 constexpr int kBBytes = 256 * kKC * 4;        // up to 256 columns
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // A, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr int kMaxE = 64;                     // output directions per CTA
+constexpr int kGen = 256;                     // builder threads (warps 2-9)
+constexpr int kThreads = 64 + kGen;
+constexpr int kYPairs = 64;                   // pairs whose Y is staged in shared memory
+constexpr int kISlots = 64;                   // incident directions staged per K step
+constexpr int kYBytes = kYPairs * 32 * 4;
+constexpr int kIBytes = kISlots * kKC * 16;
+constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + 256;  // pair slots, slot directions, barriers, flags
+constexpr int kSmemBytes = kStages * kStageBytes + kYBytes + kIBytes + kAuxBytes + 1024;
 constexpr long long kSpin = 1ll << 24;        // bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -93,7 +101,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// v rounded to TF32 (nearest, ties away).  The tensor pipe drops the low 13
+// bits of a raw FP32 operand, so both parts of a split are stored rounded:
+// hi = rna(v), lo = rna(v - hi) with v - hi exact in FP32 and |v - hi| <= 2^-11 |v|;
+// then |v - hi - lo| <= 2^-22 |v|, and the dropped lo*lo term is <= 2^-22 |a b|.
+__device__ __forceinline__ float tf32_hi(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
 
 // byte offset of element (row, k) in a K-major 64-byte-swizzled operand (k < 16)
 __device__ __forceinline__ uint32_t swz64(int row, int k) {
@@ -110,10 +126,28 @@ struct Params {
   int ncls, ntile, nO, N, npairs;
 };
 
-__global__ void __launch_bounds__(192, 1) r2_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p) {
+// barrier over the builder warps only (named barrier 1)
+__device__ __forceinline__ void gen_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory"); }
+// same barrier, returning whether v holds on every builder thread (keeps the
+// builders' loop exits uniform, so none waits at the barrier for one that left)
+__device__ __forceinline__ bool gen_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\tbar.red.and.pred q, 1, %2, p;\n\tselp.b32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kGen)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + kStages * kStageBytes);
+  float* Ys = (float*)(sm + kStages * kStageBytes);              // [pair][16][2]
+  float4* Is = (float4*)((unsigned char*)Ys + kYBytes);          // [slot][q]
+  int* pslot = (int*)((unsigned char*)Is + kIBytes);             // slot of each local pair
+  int* slot_dir = pslot + kYPairs;                                 // direction held in each slot
+  uint64_t* full = (uint64_t*)(slot_dir + kISlots);
   uint64_t* ready = full + kStages;
   uint64_t* empty = ready + kStages;
   uint64_t* done = empty + kStages;
@@ -140,7 +174,7 @@ __global__ void __launch_bounds__(192, 1) r2_tc_kernel(const __grid_constant__ C
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&ready[s], 128);
+      mbar_init(&ready[s], kGen);
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
@@ -206,77 +240,109 @@ __global__ void __launch_bounds__(192, 1) r2_tc_kernel(const __grid_constant__ C
         mma_commit(&empty[s]);
         issued = it + 1;
       }
-      if (issued > 0) mma_commit(done);
-      else *abort_flag = 1;
+      if (issued > 0) {
+        mma_commit(done);
+        // on abort, let the MMAs already issued finish before TMEM is released
+        if (*abort_flag)
+          for (long long i = 0; i < kSpin && !mbar_try(done, 0); ++i) {
+          }
+      } else {
+        *abort_flag = 1;
+      }
     }
   } else {
     // ---------------- B builders / A splitters, then epilogue
-    const int gt = threadIdx.x - 64;            // 0..127
-    const int e_l = gt >> 1, half = gt & 1;     // output direction, k half (8 k each)
-    const int e = e0 + e_l;
-    const bool have = e_l < E;
-    const int p0 = have ? pair_ptr[e] : 0, p1 = have ? pair_ptr[e + 1] : 0;
+    const int gt = threadIdx.x - 64;                        // 0..255
+    const int pp0 = pair_ptr[e0], npl = pair_ptr[e0 + E] - pp0;
+    const bool y_in_smem = npl <= kYPairs;
+    // incident directions of this CTA's pairs -> staging slots (first kISlots distinct)
+    __shared__ int nslot;
+    if (gt == 0) {
+      int ns = 0;
+      for (int pl = 0; pl < npl && pl < kYPairs; ++pl) {
+        const int op = pair_in[pp0 + pl];
+        int sidx = -1;
+        for (int s2 = 0; s2 < ns; ++s2)
+          if (slot_dir[s2] == op) { sidx = s2; break; }
+        if (sidx < 0 && ns < kISlots) { slot_dir[ns] = op; sidx = ns++; }
+        pslot[pl] = sidx;
+      }
+      nslot = ns;
+    }
+    gen_sync();
+    const int ns = nslot;
     for (int it = 0; it < iters; ++it) {
       const int s = it % kStages;
-      if (!mbar_wait(&full[s], (it / kStages) & 1, abort_flag)) break;
+      // all builders have the stage (and are done with the previous step's Ys / Is)
+      if (!gen_all(mbar_wait(&full[s], (it / kStages) & 1, abort_flag))) break;
       const int ti = it / KCH, kc = it - ti * KCH;
       unsigned char* A = sm + s * kStageBytes;
       unsigned char* Alo = A + kABytes;
       unsigned char* Bhi = Alo + kABytes;
       unsigned char* Blo = Bhi + kBBytes;
-      // A_lo = A - tf32(A): same byte layout as A
-      {
-        const float4* a4 = (const float4*)A;
-        float4* l4 = (float4*)Alo;
-        for (int q = gt; q < kABytes / 16; q += 128) {
-          float4 v = a4[q];
-          v.x -= tf32_hi(v.x); v.y -= tf32_hi(v.y); v.z -= tf32_hi(v.z); v.w -= tf32_hi(v.w);
-          l4[q] = v;
+      if (y_in_smem && kc == 0) {
+        for (int q = gt; q < npl * 8; q += kGen) {
+          const int pl = q >> 3, w = q & 7;
+          ((float4*)Ys)[q] = *((const float4*)(p.Y + (((size_t)iz * p.npairs + pp0 + pl) * p.ntile + ti) * 32) + w);
         }
       }
-      // B rows (e_l*4 + i), k = kc*16 + half*8 + q
-      float z[4][8];
+      for (int q = gt; q < ns * kKC; q += kGen) {
+        const int sl = q / kKC, qq = q - sl * kKC;
+        const int k = kc * kKC + qq;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < 2 * N) {
+          const int m = k < N ? k : k - N;
+          v = *(const float4*)(p.Ic + (((size_t)iz * p.nO + slot_dir[sl]) * N + m) * 4);
+        }
+        Is[q] = v;
+      }
+      {
+        float4* a4 = (float4*)A;
+        float4* l4 = (float4*)Alo;
+        for (int q = gt; q < kABytes / 16; q += kGen) {
+          const float4 v = a4[q];
+          float4 h, l;
+          h.x = tf32_hi(v.x); l.x = tf32_hi(v.x - h.x);
+          h.y = tf32_hi(v.y); l.y = tf32_hi(v.y - h.y);
+          h.z = tf32_hi(v.z); l.z = tf32_hi(v.z - h.z);
+          h.w = tf32_hi(v.w); l.w = tf32_hi(v.w - h.w);
+          a4[q] = h;
+          l4[q] = l;
+        }
+      }
+      gen_sync();
+      // items (row, 4-k chunk): a warp covers 8 rows x 4 chunks = one 512-byte swizzle atom
+      for (int item = gt; item < NCP * 4; item += kGen) {
+        const int row = item >> 2, kq = item & 3;
+        const int el = row >> 2, i = row & 3;
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (el < E) {
+          const int e = e0 + el;
+          const int pa = pair_ptr[e] - pp0, pb = pair_ptr[e + 1] - pp0;
+          for (int pl = pa; pl < pb; ++pl) {
+            const float* y = y_in_smem ? Ys + pl * 32 : p.Y + (((size_t)iz * p.npairs + pp0 + pl) * p.ntile + ti) * 32;
+            const float4 ya = *(const float4*)(y + i * 8), yb = *(const float4*)(y + i * 8 + 4);
+            const int sl = (pl < kYPairs) ? pslot[pl] : -1;
+            const int op = pair_in[pp0 + pl];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) z[i][q] = 0.f;
-      if (have) {
-        for (int pp = p0; pp < p1; ++pp) {
-          const int op = pair_in[pp];
-          const float* y = p.Y + (((size_t)iz * p.npairs + pp) * p.ntile + ti) * 32;
-          float yr[16], yi[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) { yr[q] = y[2 * q]; yi[q] = -y[2 * q + 1]; }
-          const float* ib = p.Ic + ((size_t)iz * p.nO + op) * N * 4;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int k = kc * kKC + half * 8 + q;
-            if (k >= 2 * N) continue;
-            const bool re = k < N;
-            const int m = re ? k : k - N;
-            const float4 iv = *(const float4*)(ib + (size_t)m * 4);
-            const float* yc = re ? yr : yi;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              z[i][q] += yc[i * 4] * iv.x + yc[i * 4 + 1] * iv.y + yc[i * 4 + 2] * iv.z + yc[i * 4 + 3] * iv.w;
+            for (int q = 0; q < 4; ++q) {
+              const int kl = kq * 4 + q, k = kc * kKC + kl;
+              if (k >= 2 * N) continue;
+              float4 iv;
+              if (sl >= 0) iv = Is[sl * kKC + kl];
+              else iv = *(const float4*)(p.Ic + (((size_t)iz * p.nO + op) * N + (k < N ? k : k - N)) * 4);
+              if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
+              else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
+            }
           }
         }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = e_l * 4 + i;
-        if (row >= NCP) continue;
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const int k = half * 8 + g * 4;
-          float4 hi, lo;
-          hi.x = tf32_hi(z[i][g * 4]);     lo.x = z[i][g * 4] - hi.x;
-          hi.y = tf32_hi(z[i][g * 4 + 1]); lo.y = z[i][g * 4 + 1] - hi.y;
-          hi.z = tf32_hi(z[i][g * 4 + 2]); lo.z = z[i][g * 4 + 2] - hi.z;
-          hi.w = tf32_hi(z[i][g * 4 + 3]); lo.w = z[i][g * 4 + 3] - hi.w;
-          *(float4*)(Bhi + swz64(row, k)) = hi;
-          *(float4*)(Blo + swz64(row, k)) = lo;
-        }
+        float4 hi, lo;
+        hi.x = tf32_hi(z[0]); lo.x = tf32_hi(z[0] - hi.x);
+        hi.y = tf32_hi(z[1]); lo.y = tf32_hi(z[1] - hi.y);
+        hi.z = tf32_hi(z[2]); lo.z = tf32_hi(z[2] - hi.z);
+        hi.w = tf32_hi(z[3]); lo.w = tf32_hi(z[3] - hi.w);
+        *(float4*)(Bhi + swz64(row, kq * 4)) = hi;
+        *(float4*)(Blo + swz64(row, kq * 4)) = lo;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&ready[s]);
@@ -286,10 +352,11 @@ __global__ void __launch_bounds__(192, 1) r2_tc_kernel(const __grid_constant__ C
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       const int q = warp & 3;                    // TMEM lane quarter of this warp
+      const int par = (warp - 2) >> 2;           // two warps per quarter split the 16-column groups
       const int r = q * 32 + lane;
       for (int mb = 0; mb < 2; ++mb) {
         const int n = mb * 128 + r;
-        for (int c0 = 0; c0 < NCP; c0 += 16) {
+        for (int c0 = par * 16; c0 < NCP; c0 += 32) {
           uint32_t v[16];
           const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mb * NCP + c0);
           asm volatile(
@@ -335,7 +402,7 @@ int r2_tc_prepare(Ctx* c) {
   const int N = c->nnu;
   const cuuint64_t nslab = (cuuint64_t)c->nz * c->ncls * c->ntile();
   cuuint64_t dims[3] = {(cuuint64_t)(2 * N), (cuuint64_t)N, nslab};
-  cuuint64_t strides[2] = {(cuuint64_t)2 * N * 4, (cuuint64_t)N * 2 * N * 4};
+  cuuint64_t strides[2] = {(cuuint64_t)c->ld() * 4, (cuuint64_t)N * c->ld() * 4};
   cuuint32_t box[3] = {tc::kKC, 128, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode((CUtensorMap*)c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->tiles.p, dims, strides, box, estr,
@@ -354,13 +421,9 @@ int r2_tc_prepare(Ctx* c) {
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
   tc::Params p{(const float*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p, c->ncls, c->ntile(),
                c->nO, c->nnu, c->npairs};
-  static bool attr_set = false;
-  if (!attr_set) {
-    PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
-    attr_set = true;
-  }
+  PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
   const int nchunk = (c->max_cout + tc::kMaxE - 1) / tc::kMaxE;
-  tc::r2_tc_kernel<<<dim3(nchunk, c->ncls, c->nz), 192, tc::kSmemBytes, c->stream>>>(*(const CUtensorMap*)c->tmap, p);
+  tc::r2_tc_kernel<<<dim3(nchunk, c->ncls, c->nz), tc::kThreads, tc::kSmemBytes, c->stream>>>(*(const CUtensorMap*)c->tmap, p);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

@@ -132,8 +132,12 @@ struct Vops {
 }  // namespace
 
 // GMRES on A x = b in the ctx precision; x holds the initial guess on entry.
+// inner: correction solve of the mixed-precision refinement.  x is zero on
+// entry and the solve ends as soon as the Arnoldi estimate is below tol (the
+// refinement's FP64 residual is the true check), so no apply is spent on a
+// residual the caller recomputes anyway.
 static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_iter, int restart, int* iters,
-                      double* true_res, double* hist, double hist_scale, int* nh_io) {
+                      double* true_res, double* hist, double hist_scale, int* nh_io, bool inner = false) {
   const size_t n = nvec(c);
   const size_t vb = n * c->esz;
   const int m = std::max(1, std::min(restart, 200));
@@ -155,13 +159,20 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   double tol_in = tol;
   double tr = 1.0;
   int status = PRD_E_NOCONV;
+  bool first = true;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
   while (it < max_iter) {
     // r = P^-1 (b - A x)
-    if ((rc = apply_operator(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
-    double rn_true;
-    if ((rc = ops.norm(w.p, &rn_true))) break;
-    tr = rn_true / bnorm;
+    if (inner && first) {
+      PRD_CUDA_TRY(c, cudaMemcpyAsync(w.p, b.p, vb, cudaMemcpyDeviceToDevice, c->stream));
+      tr = 1.0;
+    } else {
+      if ((rc = apply_operator(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
+      double rn_true;
+      if ((rc = ops.norm(w.p, &rn_true))) break;
+      tr = rn_true / bnorm;
+    }
+    first = false;
     if (!std::isfinite(tr)) { rc = fail(c, PRD_E_NAN, "residual is not finite"); break; }
     if (tr < tol) { status = PRD_OK; break; }
     if ((rc = apply_precond(c, w.p, r.p))) break;
@@ -173,7 +184,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
     g[0] = beta;
     const double beta0 = beta;
     int j = 0;
-    bool breakdown = false;
+    bool breakdown = false, est_ok = false;
     for (; j < m && it < max_iter; ++j) {
       if ((rc = apply_operator(c, vec(j), w.p)) || (rc = apply_precond(c, w.p, r.p))) break;
       ++it;
@@ -203,7 +214,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
       if (hist && nh <= max_iter) hist[nh++] = est * hist_scale;
       if (hn <= 1e-300 * std::max(1.0, beta0)) { breakdown = true; ++j; break; }
       if ((rc = ops.scale(r.p, 1.0 / hn, vec(j + 1)))) break;
-      if (est < 0.5 * tol_in) { ++j; break; }
+      if (est < 0.5 * tol_in) { ++j; est_ok = true; break; }
     }
     if (rc) break;
     // back substitution H y = g, x += V y
@@ -213,6 +224,11 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
       y[i] = s / H[(size_t)i * m + i];
     }
     if ((rc = ops.update(V.p, n, y.data(), j, x))) break;
+    if (inner && (est_ok || breakdown)) {
+      status = PRD_OK;
+      tr = std::fabs(g[j]) / beta0 * tr;
+      break;
+    }
     if (breakdown) {
       if ((rc = apply_operator(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
       double rn;
@@ -223,7 +239,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
     }
     tol_in *= 0.5;
   }
-  if (!rc && status == PRD_E_NOCONV) {
+  if (!rc && status == PRD_E_NOCONV && !inner) {
     // final true residual
     if (!(rc = apply_operator(c, x, w.p)) && !(rc = ops.rsub(b.p, w.p))) {
       double rn;
@@ -335,7 +351,7 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
     int its = 0;
     double tr_in = 0;
     const int cap_in = std::min(max_iter - it_total, std::max(2 * restart, 40));
-    int rci = gmres_core(c, r32.p, d32.p, tin, cap_in, restart, &its, &tr_in, hist, res, &nh);
+    int rci = gmres_core(c, r32.p, d32.p, tin, cap_in, restart, &its, &tr_in, hist, res, &nh, true);
     it_total += its;
     if (rci && rci != PRD_E_NOCONV) { rc = rci; break; }
     f2d_add_kernel<<<G, 256, 0, c->stream>>>((const float*)d32.p, (double*)x64.p, n);
