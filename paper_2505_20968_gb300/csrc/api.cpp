@@ -44,7 +44,7 @@ static void free_all(Ctx* c) {
                   &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk, &c->cls_dev, &c->dmu,
                   &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
                   &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
-                  &c->tc_err};
+                  &c->tc_err, &c->tc_work};
   c->tc_ready = false;
   for (DBuf* b : bufs) dfree(*b);
   for (auto& b : c->krylov) dfree(b);

@@ -119,6 +119,8 @@ struct Ctx {
   // tensor-core contraction (r2_tc.cu)
   alignas(64) unsigned char tmap[128] = {};
   DBuf tc_err;
+  DBuf tc_work;      // tcgen05 contraction work items: (class, first output entry) pairs
+  int tc_nwork = 0;
   bool tc_ready = false;
   int use_tc = 0;
   // stage timing (prd_set_profiling): events on the ctx stream around each stage

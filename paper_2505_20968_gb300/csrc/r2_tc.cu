@@ -1,6 +1,6 @@
 // S3+S4 R_II contraction on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// For one (height z, scattering-angle class c, chunk of <= 64 output
+// For one (height z, scattering-angle class c, chunk of <= 32 output
 // directions) the CTA computes the real product
 //     eps_bar[n][(o,i)] += sum_{ti, k} A[ti][n][k] * B[ti][k][(o,i)],   k in [0, 2N)
 // where A[ti] is the stored tile (Re | Im halves of the tile against the spline
@@ -10,16 +10,21 @@
 // Re(T Z) over the complex tile T and Z = Y I~).
 //
 // Roles (320 threads): warp 0 streams A with TMA (box 16 x 128 fp32, 64-byte
-// swizzle) and owns the TMEM allocation; warp 1 issues tcgen05.mma; warps 2-9
-// build B in shared memory from Y (staged per tile) and I~ (staged per K step),
-// split A and B into TF32 hi/lo parts (3 products: hi*hi + hi*lo + lo*hi,
-// FP32-level accuracy) and run the epilogue from TMEM.
+// swizzle) into a 7-stage ring and owns the TMEM allocation; warp 1 issues
+// tcgen05.mma; warps 2-9 build B in shared memory from Y (staged per tile) and
+// I~ (staged per K step; both prefetched into registers one step ahead, so the
+// builders never wait on a global load), split A and B into TF32 hi/lo parts
+// (3 products: hi*hi + hi*lo + lo*hi, FP32-level accuracy) in a 2-buffer
+// ring of their own, and run the epilogue from TMEM.  The A ring is deeper
+// than the builder ring so that enough tile bytes are in flight per SM to
+// cover HBM latency at full bandwidth.
 // Accumulators: two M = 128 blocks (rows n < 256) x NCP columns of TMEM.
 // Every mbarrier wait is bounded; on expiry the CTA records an error flag,
 // drains what it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cstdio>
+#include <vector>
 #include "prd_internal.h"
 #include "device_common.cuh"
 
@@ -27,20 +32,25 @@ namespace prd {
 
 namespace tc {
 
-constexpr int kStages = 3;
+constexpr int kStages = 7;                    // A (tile) ring
+constexpr int kCBufs = 2;                     // builder ring: A_lo, B_hi, B_lo
 constexpr int kKC = 16;                       // fp32 per stage along K (64-byte rows)
+constexpr int kMaxE = 32;                     // output directions per CTA
+constexpr int kNCPMax = 4 * kMaxE;            // MMA N (Stokes columns)
 constexpr int kABytes = 2 * 128 * kKC * 4;    // two M blocks
-constexpr int kBBytes = 256 * kKC * 4;        // up to 256 columns
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // A, A_lo, B_hi, B_lo
-constexpr int kMaxE = 64;                     // output directions per CTA
+constexpr int kBBytes = kNCPMax * kKC * 4;
+constexpr int kCBytes = kABytes + 2 * kBBytes;
 constexpr int kGen = 256;                     // builder threads (warps 2-9)
 constexpr int kThreads = 64 + kGen;
 constexpr int kYPairs = 64;                   // pairs whose Y is staged in shared memory
-constexpr int kISlots = 64;                   // incident directions staged per K step
-constexpr int kYBytes = kYPairs * 32 * 4;
-constexpr int kIBytes = kISlots * kKC * 16;
-constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + 256;  // pair slots, slot directions, barriers, flags
-constexpr int kSmemBytes = kStages * kStageBytes + kYBytes + kIBytes + kAuxBytes + 1024;
+constexpr int kISlots = 32;                   // incident directions staged per K step
+constexpr int kYBytes = kYPairs * 32 * 4;     // one tile's Y (two buffers)
+constexpr int kIBytes = kISlots * kKC * 16;   // one K step's I~ (two buffers)
+constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + (kMaxE + 2) * 4 + 256;
+constexpr int kSmemBytes = kStages * kABytes + kCBufs * kCBytes + 2 * kYBytes + 2 * kIBytes + kAuxBytes + 1024;
+static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
+static_assert(kYPairs * 8 <= 2 * kGen && kISlots * kKC <= 2 * kGen, "two prefetch registers per builder thread");
+static_assert(kNCPMax * 4 <= 2 * kGen, "two B items per builder thread");
 constexpr long long kSpin = 1ll << 24;        // bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -101,14 +111,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// v rounded to TF32 (nearest, ties away).  The tensor pipe drops the low 13
-// bits of a raw FP32 operand, so both parts of a split are stored rounded:
-// hi = rna(v), lo = rna(v - hi) with v - hi exact in FP32 and |v - hi| <= 2^-11 |v|;
-// then |v - hi - lo| <= 2^-22 |v|, and the dropped lo*lo term is <= 2^-22 |a b|.
+// v rounded to TF32 (nearest, ties away from zero: half a unit of the 13
+// dropped bits is added to the magnitude bits before they are cleared).  The
+// tensor pipe drops the low 13 bits of a raw FP32 operand, so both parts of a
+// split are stored rounded: hi = rna(v), lo = rna(v - hi) with v - hi exact in
+// FP32 and |v - hi| <= 2^-11 |v|; then |v - hi - lo| <= 2^-22 |v|, and the
+// dropped lo*lo term is <= 2^-22 |a b|.
 __device__ __forceinline__ float tf32_hi(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 
 // byte offset of element (row, k) in a K-major 64-byte-swizzled operand (k < 16)
@@ -120,6 +130,7 @@ __device__ __forceinline__ uint32_t swz64(int row, int k) {
 struct Params {
   const float* Y;       // [z][pair][ntile][16][2]
   const float* Ic;      // [z][o][N][4]
+  const int2* work;     // [item] (class, first output entry of the chunk)
   const int* cls;
   float* eb;            // [z][o][N][4]
   int* err;
@@ -143,39 +154,44 @@ __device__ __forceinline__ bool gen_all(bool v) {
 __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  float* Ys = (float*)(sm + kStages * kStageBytes);              // [pair][16][2]
-  float4* Is = (float4*)((unsigned char*)Ys + kYBytes);          // [slot][q]
-  int* pslot = (int*)((unsigned char*)Is + kIBytes);             // slot of each local pair
+  unsigned char* cbuf = sm + kStages * kABytes;                   // [buffer] A_lo, B_hi, B_lo
+  float* Ys = (float*)(cbuf + kCBufs * kCBytes);                   // [buffer][pair][16][2]
+  float4* Is = (float4*)((unsigned char*)Ys + 2 * kYBytes);      // [buffer][slot][q]
+  int* pslot = (int*)((unsigned char*)Is + 2 * kIBytes);         // slot of each local pair
   int* slot_dir = pslot + kYPairs;                                 // direction held in each slot
-  uint64_t* full = (uint64_t*)(slot_dir + kISlots);
-  uint64_t* ready = full + kStages;
-  uint64_t* empty = ready + kStages;
-  uint64_t* done = empty + kStages;
+  int* eptr = slot_dir + kISlots;                                  // local pair range of each output
+  int* nslot_p = eptr + kMaxE + 1;
+  uint64_t* full = (uint64_t*)(((uintptr_t)(nslot_p + 1) + 7) & ~(uintptr_t)7);
+  uint64_t* empty = full + kStages;
+  uint64_t* ready = empty + kStages;
+  uint64_t* cfree = ready + kCBufs;
+  uint64_t* done = cfree + kCBufs;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
-  const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
+  const int2 wk = p.work[blockIdx.x];
+  const int c = wk.x, e0 = wk.y, iz = blockIdx.y;
   const int* cout_ptr = p.cls;
   const int* cout_dir = p.cls + p.ncls + 1;
   const int ne_tot = cout_ptr[p.ncls];
   const int* pair_ptr = cout_dir + ne_tot;
   const int* pair_in = pair_ptr + ne_tot + 1;
-  const int e0 = cout_ptr[c] + chunk * kMaxE;
-  const int e_end = cout_ptr[c + 1];
-  if (e0 >= e_end) return;                       // uniform for the CTA
-  const int E = min(kMaxE, e_end - e0);
-  const int NCP = ((4 * E + 15) / 16) * 16;      // MMA N (multiple of 16, <= 256)
+  const int E = min(kMaxE, cout_ptr[c + 1] - e0);
+  const int NCP = ((4 * E + 15) / 16) * 16;      // MMA N (multiple of 16, <= 128)
   const int N = p.N;
   const int KCH = (2 * N + kKC - 1) / kKC;
   const int iters = p.ntile * KCH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t tm_cols = (NCP > 128) ? 512u : 256u;
+  const uint32_t tm_cols = 256u;                 // two M blocks x <= 128 columns
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&ready[s], kGen);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < kCBufs; ++b) {
+      mbar_init(&ready[b], kGen);
+      mbar_init(&cfree[b], 1);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
         const int s = it % kStages;
         if (it >= kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1, abort_flag)) break;
         const int ti = it / KCH, kc = it - ti * KCH;
-        unsigned char* A = sm + s * kStageBytes;
+        unsigned char* A = sm + s * kABytes;
         mbar_expect_tx(&full[s], kABytes);
         tma_load_3d(A, &tmap, kc * kKC, 0, (int)(slab0 + ti), &full[s]);
         tma_load_3d(A + kABytes / 2, &tmap, kc * kKC, 128, (int)(slab0 + ti), &full[s]);
@@ -220,11 +236,11 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NCP >> 3) << 17) | ((128u >> 4) << 24);
       int issued = 0;
       for (int it = 0; it < iters; ++it) {
-        const int s = it % kStages;
-        if (!mbar_wait(&ready[s], (it / kStages) & 1, abort_flag)) break;
+        const int s = it % kStages, cb = it % kCBufs;
+        if (!mbar_wait(&ready[cb], (it / kCBufs) & 1, abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* A = sm + s * kStageBytes;
-        unsigned char* Alo = A + kABytes;
+        unsigned char* A = sm + s * kABytes;
+        unsigned char* Alo = cbuf + cb * kCBytes;
         unsigned char* Bhi = Alo + kABytes;
         unsigned char* Blo = Bhi + kBBytes;
         for (int mb = 0; mb < 2; ++mb) {
@@ -238,6 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
           }
         }
         mma_commit(&empty[s]);
+        mma_commit(&cfree[cb]);
         issued = it + 1;
       }
       if (issued > 0) {
@@ -255,8 +272,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
     const int gt = threadIdx.x - 64;                        // 0..255
     const int pp0 = pair_ptr[e0], npl = pair_ptr[e0 + E] - pp0;
     const bool y_in_smem = npl <= kYPairs;
+    if (gt <= E) eptr[gt] = pair_ptr[e0 + gt] - pp0;
     // incident directions of this CTA's pairs -> staging slots (first kISlots distinct)
-    __shared__ int nslot;
     if (gt == 0) {
       int ns = 0;
       for (int pl = 0; pl < npl && pl < kYPairs; ++pl) {
@@ -267,35 +284,64 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
         if (sidx < 0 && ns < kISlots) { slot_dir[ns] = op; sidx = ns++; }
         pslot[pl] = sidx;
       }
-      nslot = ns;
+      *nslot_p = ns;
     }
     gen_sync();
-    const int ns = nslot;
+    const int ns = *nslot_p;
+    const size_t ybase = (size_t)iz * p.npairs + pp0;
+    const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
+    // prefetch registers: Y of the next tile, I~ of the next K step
+    float4 ypre[2], ipre[2];
+    auto load_y = [&](int ti) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int q = gt + r * kGen;
+        if (y_in_smem && q < npl * 8)
+          ypre[r] = *((const float4*)(p.Y + ((ybase + (q >> 3)) * p.ntile + ti) * 32) + (q & 7));
+      }
+    };
+    auto load_i = [&](int it) {
+      const int kc = it % KCH;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int q = gt + r * kGen;
+        if (q < ns * kKC) {
+          const int sl = q / kKC, k = kc * kKC + (q - sl * kKC);
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < 2 * N) v = *(const float4*)(Icz + ((size_t)slot_dir[sl] * N + (k < N ? k : k - N)) * 4);
+          ipre[r] = v;
+        }
+      }
+    };
+    if (iters > 0) { load_y(0); load_i(0); }
     for (int it = 0; it < iters; ++it) {
-      const int s = it % kStages;
-      // all builders have the stage (and are done with the previous step's Ys / Is)
-      if (!gen_all(mbar_wait(&full[s], (it / kStages) & 1, abort_flag))) break;
+      const int s = it % kStages, cb = it % kCBufs;
+      // the tile stage has landed and the MMAs that last read builder buffer cb
+      // are done; all builders agree (and are done with the step before)
+      bool got = mbar_wait(&full[s], (it / kStages) & 1, abort_flag);
+      if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag);
+      if (!gen_all(got)) break;
       const int ti = it / KCH, kc = it - ti * KCH;
-      unsigned char* A = sm + s * kStageBytes;
-      unsigned char* Alo = A + kABytes;
+      unsigned char* A = sm + s * kABytes;
+      unsigned char* Alo = cbuf + cb * kCBytes;
       unsigned char* Bhi = Alo + kABytes;
       unsigned char* Blo = Bhi + kBBytes;
-      if (y_in_smem && kc == 0) {
-        for (int q = gt; q < npl * 8; q += kGen) {
-          const int pl = q >> 3, w = q & 7;
-          ((float4*)Ys)[q] = *((const float4*)(p.Y + (((size_t)iz * p.npairs + pp0 + pl) * p.ntile + ti) * 32) + w);
+      float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
+      float4* Isb = Is + (it & 1) * (kISlots * kKC);
+      if (kc == 0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int q = gt + r * kGen;
+          if (y_in_smem && q < npl * 8) ((float4*)Ysb)[q] = ypre[r];
         }
+        if (ti + 1 < p.ntile) load_y(ti + 1);
       }
-      for (int q = gt; q < ns * kKC; q += kGen) {
-        const int sl = q / kKC, qq = q - sl * kKC;
-        const int k = kc * kKC + qq;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < 2 * N) {
-          const int m = k < N ? k : k - N;
-          v = *(const float4*)(p.Ic + (((size_t)iz * p.nO + slot_dir[sl]) * N + m) * 4);
-        }
-        Is[q] = v;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int q = gt + r * kGen;
+        if (q < ns * kKC) Isb[q] = ipre[r];
       }
+      if (it + 1 < iters) load_i(it + 1);
       {
         float4* a4 = (float4*)A;
         float4* l4 = (float4*)Alo;
@@ -312,25 +358,26 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
       }
       gen_sync();
       // items (row, 4-k chunk): a warp covers 8 rows x 4 chunks = one 512-byte swizzle atom
-      for (int item = gt; item < NCP * 4; item += kGen) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int item = gt + r * kGen;
+        if (item >= NCP * 4) break;
         const int row = item >> 2, kq = item & 3;
         const int el = row >> 2, i = row & 3;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (el < E) {
-          const int e = e0 + el;
-          const int pa = pair_ptr[e] - pp0, pb = pair_ptr[e + 1] - pp0;
+          const int pa = eptr[el], pb = eptr[el + 1];
           for (int pl = pa; pl < pb; ++pl) {
-            const float* y = y_in_smem ? Ys + pl * 32 : p.Y + (((size_t)iz * p.npairs + pp0 + pl) * p.ntile + ti) * 32;
+            const float* y = y_in_smem ? Ysb + pl * 32 : p.Y + ((ybase + pl) * p.ntile + ti) * 32;
             const float4 ya = *(const float4*)(y + i * 8), yb = *(const float4*)(y + i * 8 + 4);
             const int sl = (pl < kYPairs) ? pslot[pl] : -1;
-            const int op = pair_in[pp0 + pl];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int kl = kq * 4 + q, k = kc * kKC + kl;
               if (k >= 2 * N) continue;
               float4 iv;
-              if (sl >= 0) iv = Is[sl * kKC + kl];
-              else iv = *(const float4*)(p.Ic + (((size_t)iz * p.nO + op) * N + (k < N ? k : k - N)) * 4);
+              if (sl >= 0) iv = Isb[sl * kKC + kl];
+              else iv = *(const float4*)(Icz + ((size_t)pair_in[pp0 + pl] * N + (k < N ? k : k - N)) * 4);
               if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
               else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
             }
@@ -345,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
         *(float4*)(Blo + swz64(row, kq * 4)) = lo;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&ready[s]);
+      mbar_arrive(&ready[cb]);
     }
     // ---------------- epilogue: TMEM -> registers -> eps_bar
     const bool ok = mbar_wait(done, 0, abort_flag);
@@ -413,17 +460,30 @@ int r2_tc_prepare(Ctx* c) {
     int rc = dalloc(c, c->tc_err, sizeof(int));
     if (rc) return rc;
   }
+  // work items: every class split into chunks of <= kMaxE output directions
+  std::vector<int> work;
+  for (int k = 0; k < c->ncls; ++k)
+    for (int e = c->cout_ptr[k]; e < c->cout_ptr[k + 1]; e += tc::kMaxE) {
+      work.push_back(k);
+      work.push_back(e);
+    }
+  c->tc_nwork = (int)work.size() / 2;
+  dfree(c->tc_work);
+  {
+    int rc = dalloc(c, c->tc_work, work.size() * sizeof(int));
+    if (rc) return rc;
+  }
+  PRD_CUDA_TRY(c, cudaMemcpy(c->tc_work.p, work.data(), work.size() * sizeof(int), cudaMemcpyHostToDevice));
   PRD_CUDA_TRY(c, cudaMemset(c->tc_err.p, 0, sizeof(int)));
   c->tc_ready = true;
   return PRD_OK;
 }
 
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
-  tc::Params p{(const float*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p, c->ncls, c->ntile(),
-               c->nO, c->nnu, c->npairs};
+  tc::Params p{(const float*)c->Y.p, Ic, (const int2*)c->tc_work.p, (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p,
+               c->ncls, c->ntile(), c->nO, c->nnu, c->npairs};
   PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
-  const int nchunk = (c->max_cout + tc::kMaxE - 1) / tc::kMaxE;
-  tc::r2_tc_kernel<<<dim3(nchunk, c->ncls, c->nz), tc::kThreads, tc::kSmemBytes, c->stream>>>(*(const CUtensorMap*)c->tmap, p);
+  tc::r2_tc_kernel<<<dim3(c->tc_nwork, c->nz), tc::kThreads, tc::kSmemBytes, c->stream>>>(*(const CUtensorMap*)c->tmap, p);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
