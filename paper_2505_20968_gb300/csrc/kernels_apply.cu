@@ -170,7 +170,7 @@ template <typename T, typename A>
 __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tiles, const T* __restrict__ Y,
                                                       const A* __restrict__ Ic, const int* __restrict__ cls,
                                                       A* __restrict__ eb, int ncls, int ntrip, int nO, int N,
-                                                      int npairs, int ld) {
+                                                      int npairs, int ld, int tiled) {
   const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
   const int* cout_ptr = cls;
   const int* cout_dir = cls + ncls + 1;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
         const int h = (idx / kMB) & 1;
         const int n = idx / (2 * kMB);
         const int m = m0 + mm;
-        Asb[(h * N + n) * (kMB + 1) + mm] = (m < N) ? tile[(size_t)n * ld + h * N + m] : (T)0;
+        Asb[(h * N + n) * (kMB + 1) + mm] = (m < N) ? tile[tile_off(n, h * N + m, N, ld, tiled != 0)] : (T)0;
       }
       __syncthreads();
 #pragma unroll 4
@@ -415,7 +415,8 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
   cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
-      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs, c->ld());
+      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs, c->ld(),
+      c->tiled());
   stage_end(c, ST_S3, e0);
   }
 s6:
@@ -667,10 +668,10 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       const T* Yz = (const T*)Yd.p + (size_t)iz * nO * nti * 32;
       r2_simt_kernel<T, A><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
           (const T*)tiles.p, Yz, (const A*)Icx.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
-          (A*)es_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO, c->ld());
+          (A*)es_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO, c->ld(), c->tiled());
       r2_simt_kernel<T, A><<<dim3(1, nO, 1), 256, smem, c->stream>>>(
           (const T*)tiles.p, Yz, (const A*)Icw.p + (size_t)iz * nO * N * 4, (const int*)clsd.p,
-          (A*)ew_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO, c->ld());
+          (A*)ew_bar.p + (size_t)iz * N * 4, nO, nti, nO, N, nO, c->ld(), c->tiled());
       PRD_CUDA_TRY(c, cudaPeekAtLastError());
     }
     if (rc) break;

@@ -314,14 +314,14 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) r3_kernel(R3Params p, T* o
 // of one J level are summed once, in FP64, before rounding to the storage type.
 template <typename T>
 __global__ void group_split_kernel(const double* __restrict__ src, T* __restrict__ dst, const int* __restrict__ grp,
-                                   int ncls, int ntrip, int ngrp, int N, int ld) {
+                                   int ncls, int ntrip, int ngrp, int N, int ld, int tiled) {
   const int rowlen = 2 * N * N;                 // one FP64 scratch tile: N rows of 2N
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (c, n*2N + k)
   if (idx >= (long long)ncls * rowlen) return;
   const int c = (int)(idx / rowlen);
   const int e = (int)(idx - (long long)c * rowlen);
   const int n = e / (2 * N), kk = e - n * 2 * N;
-  const size_t o = (size_t)n * ld + kk;         // stored row stride ld
+  const size_t o = tile_off(n, kk, N, ld, tiled != 0);
   const size_t tsz = (size_t)N * ld;
   double mean[2] = {0.0, 0.0};
   int cnt[2] = {0, 0};
@@ -410,10 +410,12 @@ int launch_tiles(Ctx* c) {
     const int sb = ceil_div((long long)c->ncls * rowlen, 256);
     if (c->prec == PRD_FP64)
       group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)c->tiles.p + iz * ztile,
-                                                            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld());
+                                                            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
+                                                            c->tiled());
     else
       group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)c->tiles.p + iz * ztile,
-                                                           (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld());
+                                                           (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
+                                                           c->tiled());
     if (cudaPeekAtLastError() != cudaSuccess) err = 1;
   }
   cudaStreamSynchronize(c->stream);
@@ -470,10 +472,10 @@ int gen_tiles_z(Ctx* c, int iz, const std::vector<double>& thetas, void* outT) {
   const int sb = ceil_div((long long)ncl * rowlen, 256);
   if (c->prec == PRD_FP64)
     group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)outT, (const int*)dgrp.p, ncl,
-                                                          c->ntrip, c->ngrp, N, c->ld());
+                                                          c->ntrip, c->ngrp, N, c->ld(), c->tiled());
   else
     group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)outT, (const int*)dgrp.p, ncl,
-                                                         c->ntrip, c->ngrp, N, c->ld());
+                                                         c->ntrip, c->ngrp, N, c->ld(), c->tiled());
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cleanup();
   if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("line-of-sight tiles: ") + cudaGetErrorString(e));

@@ -68,7 +68,11 @@ struct Ctx {
   std::vector<int> trip_grp;
   int ntile() const { return ngrp + ntrip; }
   // row stride of a stored tile: 2N rounded up to 4 elements (16-byte rows for TMA)
-  int ld() const { return (2 * nnu + 3) / 4 * 4; }
+  // Stored tile row length: FP32 tiles are kept in the tensor-core layout of
+  // tile_off (K chunks of 16, each a contiguous [n][16] block), FP64 tiles as
+  // plain rows; both padded so every row or chunk starts on 16 bytes.
+  bool tiled() const { return prec == PRD_FP32; }
+  int ld() const { return tiled() ? (2 * nnu + 15) / 16 * 16 : (2 * nnu + 3) / 4 * 4; }
   int nq3 = 0;                           // R_III incident combos (ku, kv, kl)
   double nu0 = 0;
   std::vector<double> dnuD, vD;          // per z (Hz, km/s)
@@ -117,7 +121,6 @@ struct Ctx {
   DBuf gm_w, gm_r, gm_t, gm_dots;
   std::vector<void*> owned;
   // tensor-core contraction (r2_tc.cu)
-  alignas(64) unsigned char tmap[128] = {};
   DBuf tc_err;
   DBuf tc_work;      // tcgen05 contraction work items: (class, first output entry) pairs
   int tc_nwork = 0;
@@ -195,6 +198,18 @@ enum Stage { ST_S1 = 0, ST_S5 = 1, ST_S3 = 2, ST_S6 = 3, ST_S7 = 4, ST_PRE = 5 }
 void stage_begin(Ctx* c, int stage, cudaEvent_t* out);
 void stage_end(Ctx* c, int stage, cudaEvent_t start);
 void stage_collect(Ctx* c);
+
+// Offset of tile element (row n, column k in [0, 2N): Re | Im halves) within
+// one tile of N rows.  Plain layout: n * ld + k.  Tensor-core layout (FP32):
+// the tile is cut into K chunks of 16 columns; chunk kc is a contiguous block
+// of N rows of 64 bytes, each row's four 16-byte groups permuted by the 64-byte
+// shared-memory swizzle of its row index (group g stored at g ^ ((n >> 1) & 3)),
+// so one bulk copy of N * 64 bytes lands a K step in the operand layout.
+__host__ __device__ inline size_t tile_off(int n, int k, int N, int ld, bool tiled) {
+  if (!tiled) return (size_t)n * ld + k;
+  const int kc = k >> 4, kl = k & 15;
+  return (size_t)kc * N * 16 + (size_t)n * 16 + (size_t)((((kl >> 2) ^ ((n >> 1) & 3)) << 2) | (kl & 3));
+}
 
 }  // namespace prd
 

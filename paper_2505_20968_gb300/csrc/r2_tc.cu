@@ -9,8 +9,10 @@
 // with Ycomp = Re Y for k = m < N and -Im Y for k = N + m (so that the sum is
 // Re(T Z) over the complex tile T and Z = Y I~).
 //
-// Roles (320 threads): warp 0 streams A with TMA (box 16 x 128 fp32, 64-byte
-// swizzle) into a 7-stage ring and owns the TMEM allocation; warp 1 issues
+// Roles (320 threads): warp 0 streams A into a 7-stage ring with one bulk
+// asynchronous copy per K step (the FP32 tiles are stored pre-swizzled, K
+// step by K step, so a step is one contiguous N x 64-byte block) and owns the
+// TMEM allocation; warp 1 issues
 // tcgen05.mma; warps 2-9 build B in shared memory from Y (staged per tile) and
 // I~ (staged per K step; both prefetched into registers one step ahead, so the
 // builders never wait on a global load), split A and B into TF32 hi/lo parts
@@ -21,8 +23,6 @@
 // Accumulators: two M = 128 blocks (rows n < 256) x NCP columns of TMEM.
 // Every mbarrier wait is bounded; on expiry the CTA records an error flag,
 // drains what it issued and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cstdio>
 #include <vector>
 #include "prd_internal.h"
@@ -46,7 +46,7 @@ constexpr int kYPairs = 64;                   // pairs whose Y is staged in shar
 constexpr int kISlots = 32;                   // incident directions staged per K step
 constexpr int kYBytes = kYPairs * 32 * 4;     // one tile's Y (two buffers)
 constexpr int kIBytes = kISlots * kKC * 16;   // one K step's I~ (two buffers)
-constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + (kMaxE + 2) * 4 + 256;
+constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + (kMaxE + 3) * 4 + 256;
 constexpr int kSmemBytes = kStages * kABytes + kCBufs * kCBytes + 2 * kYBytes + 2 * kIBytes + kAuxBytes + 1024;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 static_assert(kYPairs * 8 <= 2 * kGen && kISlots * kKC <= 2 * kGen, "two prefetch registers per builder thread");
@@ -85,10 +85,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
   return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+// bulk asynchronous copy global -> shared (16-byte aligned ends, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -128,13 +129,14 @@ __device__ __forceinline__ uint32_t swz64(int row, int k) {
 }
 
 struct Params {
+  const float* tiles;   // [z][class][tile] pre-swizzled K steps of [N][16]
   const float* Y;       // [z][pair][ntile][16][2]
   const float* Ic;      // [z][o][N][4]
   const int2* work;     // [item] (class, first output entry of the chunk)
   const int* cls;
   float* eb;            // [z][o][N][4]
   int* err;
-  int ncls, ntile, nO, N, npairs;
+  int ncls, ntile, nO, N, npairs, ld;
 };
 
 // barrier over the builder warps only (named barrier 1)
@@ -151,17 +153,19 @@ __device__ __forceinline__ bool gen_all(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p) {
+__global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned base, derived by offset so that the compiler keeps the
+  // shared address space on every pointer below (plain LDS/STS, no generic access)
+  unsigned char* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char* cbuf = sm + kStages * kABytes;                   // [buffer] A_lo, B_hi, B_lo
   float* Ys = (float*)(cbuf + kCBufs * kCBytes);                   // [buffer][pair][16][2]
   float4* Is = (float4*)((unsigned char*)Ys + 2 * kYBytes);      // [buffer][slot][q]
   int* pslot = (int*)((unsigned char*)Is + 2 * kIBytes);         // slot of each local pair
   int* slot_dir = pslot + kYPairs;                                 // direction held in each slot
   int* eptr = slot_dir + kISlots;                                  // local pair range of each output
-  int* nslot_p = eptr + kMaxE + 1;
-  uint64_t* full = (uint64_t*)(((uintptr_t)(nslot_p + 1) + 7) & ~(uintptr_t)7);
+  int* nslot_p = eptr + kMaxE + 1;                                 // staged slots, fast-path flag
+  uint64_t* full = (uint64_t*)(((uintptr_t)(nslot_p + 2) + 7) & ~(uintptr_t)7);
   uint64_t* empty = full + kStages;
   uint64_t* ready = empty + kStages;
   uint64_t* cfree = ready + kCBufs;
@@ -207,6 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const long long slab0 = ((long long)iz * p.ncls + c) * p.ntile;
+  const int nmb = N > 128 ? 2 : 1;               // M blocks holding rows n < N
 
   if (warp == 0) {
     // ---------------- TMA producer
@@ -217,9 +222,11 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
         if (it >= kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1, abort_flag)) break;
         const int ti = it / KCH, kc = it - ti * KCH;
         unsigned char* A = sm + s * kABytes;
-        mbar_expect_tx(&full[s], kABytes);
-        tma_load_3d(A, &tmap, kc * kKC, 0, (int)(slab0 + ti), &full[s]);
-        tma_load_3d(A + kABytes / 2, &tmap, kc * kKC, 128, (int)(slab0 + ti), &full[s]);
+        // rows n >= N of the stage keep stale data: they only reach output rows
+        // that the epilogue never reads
+        const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
+        mbar_expect_tx(&full[s], (uint32_t)N * kKC * 4);
+        bulk_load(A, src, (uint32_t)N * kKC * 4, &full[s]);
       }
       if (*abort_flag) {
         // drain loads that were issued and may not have been consumed
@@ -243,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
         unsigned char* Alo = cbuf + cb * kCBytes;
         unsigned char* Bhi = Alo + kABytes;
         unsigned char* Blo = Bhi + kBBytes;
-        for (int mb = 0; mb < 2; ++mb) {
+        for (int mb = 0; mb < nmb; ++mb) {
           const uint32_t d = tmem + (uint32_t)(mb * NCP);
           for (int ks = 0; ks < 2; ++ks) {
             const int ao = mb * (kABytes / 2) + ks * 32, bo = ks * 32;
@@ -276,6 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
     // incident directions of this CTA's pairs -> staging slots (first kISlots distinct)
     if (gt == 0) {
       int ns = 0;
+      bool all = y_in_smem;
       for (int pl = 0; pl < npl && pl < kYPairs; ++pl) {
         const int op = pair_in[pp0 + pl];
         int sidx = -1;
@@ -283,11 +291,27 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
           if (slot_dir[s2] == op) { sidx = s2; break; }
         if (sidx < 0 && ns < kISlots) { slot_dir[ns] = op; sidx = ns++; }
         pslot[pl] = sidx;
+        all = all && sidx >= 0;
       }
-      *nslot_p = ns;
+      nslot_p[0] = ns;
+      nslot_p[1] = all ? 1 : 0;
     }
     gen_sync();
-    const int ns = *nslot_p;
+    const int ns = nslot_p[0];
+    // fast path: every pair's Y and I~ are staged in shared memory
+    const bool fast = nslot_p[1] != 0;
+    // this thread's two B items (row = (output, Stokes i), 4-k chunk) and their pair ranges
+    int it_row[2], it_kq[2], it_pa[2], it_pb[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int item = gt + r * kGen;
+      it_row[r] = item >> 2;
+      it_kq[r] = item & 3;
+      const int el = it_row[r] >> 2;
+      const bool v = item < NCP * 4 && el < E;
+      it_pa[r] = v ? eptr[el] : 0;
+      it_pb[r] = v ? eptr[el + 1] : 0;
+    }
     const size_t ybase = (size_t)iz * p.npairs + pp0;
     const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
     // prefetch registers: Y of the next tile, I~ of the next K step
@@ -345,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
       {
         float4* a4 = (float4*)A;
         float4* l4 = (float4*)Alo;
-        for (int q = gt; q < kABytes / 16; q += kGen) {
+        for (int q = gt; q < N * (kKC / 4); q += kGen) {
           const float4 v = a4[q];
           float4 h, l;
           h.x = tf32_hi(v.x); l.x = tf32_hi(v.x - h.x);
@@ -360,23 +384,38 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
       // items (row, 4-k chunk): a warp covers 8 rows x 4 chunks = one 512-byte swizzle atom
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const int item = gt + r * kGen;
-        if (item >= NCP * 4) break;
-        const int row = item >> 2, kq = item & 3;
-        const int el = row >> 2, i = row & 3;
+        const int row = it_row[r], kq = it_kq[r], i = row & 3;
+        if (row >= NCP) continue;
+        const int kb = kc * kKC + kq * 4;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
-        if (el < E) {
-          const int pa = eptr[el], pb = eptr[el + 1];
-          for (int pl = pa; pl < pb; ++pl) {
+        if (fast) {
+          // I~ of k >= 2N is staged as zero, so no bound test is needed here
+          bool re[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) re[q] = kb + q < N;
+          for (int pl = it_pa[r]; pl < it_pb[r]; ++pl) {
+            const float4* y4 = reinterpret_cast<const float4*>(Ysb) + pl * 8 + i * 2;
+            const float4 ya = y4[0], yb = y4[1];
+            const float4* I4 = Isb + pslot[pl] * kKC + kq * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 iv = I4[q];
+              const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
+              const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
+              z[q] += re[q] ? sr : -si;
+            }
+          }
+        } else {
+          for (int pl = it_pa[r]; pl < it_pb[r]; ++pl) {
             const float* y = y_in_smem ? Ysb + pl * 32 : p.Y + ((ybase + pl) * p.ntile + ti) * 32;
             const float4 ya = *(const float4*)(y + i * 8), yb = *(const float4*)(y + i * 8 + 4);
             const int sl = (pl < kYPairs) ? pslot[pl] : -1;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const int kl = kq * 4 + q, k = kc * kKC + kl;
+              const int k = kb + q;
               if (k >= 2 * N) continue;
               float4 iv;
-              if (sl >= 0) iv = Isb[sl * kKC + kl];
+              if (sl >= 0) iv = Isb[sl * kKC + kq * 4 + q];
               else iv = *(const float4*)(Icz + ((size_t)pair_in[pp0 + pl] * N + (k < N ? k : k - N)) * 4);
               if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
               else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
@@ -401,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
       const int q = warp & 3;                    // TMEM lane quarter of this warp
       const int par = (warp - 2) >> 2;           // two warps per quarter split the 16-column groups
       const int r = q * 32 + lane;
-      for (int mb = 0; mb < 2; ++mb) {
+      for (int mb = 0; mb < nmb; ++mb) {
         const int n = mb * 128 + r;
         for (int c0 = par * 16; c0 < NCP; c0 += 32) {
           uint32_t v[16];
@@ -438,24 +477,10 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(const __grid_constan
 }  // namespace tc
 
 // Tensor map over the tiles viewed as [slab][n][k] fp32, k = 2N innermost.
+// Work list and error flag of the tensor-core contraction.
 int r2_tc_prepare(Ctx* c) {
   if (c->prec != PRD_FP32) return PRD_OK;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess)
-    return fail(c, PRD_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
-  auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  const int N = c->nnu;
-  const cuuint64_t nslab = (cuuint64_t)c->nz * c->ncls * c->ntile();
-  cuuint64_t dims[3] = {(cuuint64_t)(2 * N), (cuuint64_t)N, nslab};
-  cuuint64_t strides[2] = {(cuuint64_t)c->ld() * 4, (cuuint64_t)N * c->ld() * 4};
-  cuuint32_t box[3] = {tc::kKC, 128, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode((CUtensorMap*)c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->tiles.p, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(c, PRD_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  if (c->nnu > 256 || !c->tiled()) return fail(c, PRD_E_ARG, "tensor-core contraction needs N <= 256 and FP32 tiles");
   if (!c->tc_err.p) {
     int rc = dalloc(c, c->tc_err, sizeof(int));
     if (rc) return rc;
@@ -480,10 +505,11 @@ int r2_tc_prepare(Ctx* c) {
 }
 
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
-  tc::Params p{(const float*)c->Y.p, Ic, (const int2*)c->tc_work.p, (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p,
-               c->ncls, c->ntile(), c->nO, c->nnu, c->npairs};
+  tc::Params p{(const float*)c->tiles.p, (const float*)c->Y.p, Ic, (const int2*)c->tc_work.p,
+               (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p, c->ncls, c->ntile(), c->nO, c->nnu, c->npairs,
+               c->ld()};
   PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
-  tc::r2_tc_kernel<<<dim3(c->tc_nwork, c->nz), tc::kThreads, tc::kSmemBytes, c->stream>>>(*(const CUtensorMap*)c->tmap, p);
+  tc::r2_tc_kernel<<<dim3(c->tc_nwork, c->nz), tc::kThreads, tc::kSmemBytes, c->stream>>>(p);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
