@@ -114,13 +114,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 // v rounded to TF32 (nearest, ties away from zero: half a unit of the 13
 // dropped bits is added to the magnitude bits before they are cleared).  The
-// tensor pipe drops the low 13 bits of a raw FP32 operand, so both parts of a
-// split are stored rounded: hi = rna(v), lo = rna(v - hi) with v - hi exact in
-// FP32 and |v - hi| <= 2^-11 |v|; then |v - hi - lo| <= 2^-22 |v|, and the
-// dropped lo*lo term is <= 2^-22 |a b|.
+// tensor pipe drops the low 13 bits of a raw FP32 operand.  B is split as
+// hi = rna(v), lo = rna(v - hi): v - hi is exact in FP32 and |v - hi| <= 2^-11 |v|,
+// so |v - hi - lo| <= 2^-22 |v|.  A (the stored tile, read raw) has the
+// truncated hi = trunc(a) and lo = rna(a - trunc(a)) with |a - trunc(a)| < 2^-10 |a|,
+// so |a - hi - lo| <= 2^-21 |a|; the dropped lo*lo term is below 2^-21 |a b|.
 __device__ __forceinline__ float tf32_hi(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
+__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
 // byte offset of element (row, k) in a K-major 64-byte-swizzled operand (k < 16)
 __device__ __forceinline__ uint32_t swz64(int row, int k) {
@@ -284,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     if (gt == 0) {
       int ns = 0;
       bool all = y_in_smem;
+      for (int el = 0; el < E; ++el) all = all && pair_ptr[e0 + el + 1] - pair_ptr[e0 + el] <= 2;
       for (int pl = 0; pl < npl && pl < kYPairs; ++pl) {
         const int op = pair_in[pp0 + pl];
         int sidx = -1;
@@ -298,8 +301,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     }
     gen_sync();
     const int ns = nslot_p[0];
-    // fast path: every pair's Y and I~ are staged in shared memory
+    // fast path: every pair's Y and I~ are staged in shared memory and no output
+    // has more than two pairs; each thread then keeps its items' Y and I~ slot
+    // offsets in registers for a whole tile
     const bool fast = nslot_p[1] != 0;
+    float4 yreg[2][2][2];
+    int soff[2][2];
     // this thread's two B items (row = (output, Stokes i), 4-k chunk) and their pair ranges
     int it_row[2], it_kq[2], it_pa[2], it_pb[2];
 #pragma unroll
@@ -367,16 +374,15 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       }
       if (it + 1 < iters) load_i(it + 1);
       {
-        float4* a4 = (float4*)A;
+        const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
         for (int q = gt; q < N * (kKC / 4); q += kGen) {
           const float4 v = a4[q];
-          float4 h, l;
-          h.x = tf32_hi(v.x); l.x = tf32_hi(v.x - h.x);
-          h.y = tf32_hi(v.y); l.y = tf32_hi(v.y - h.y);
-          h.z = tf32_hi(v.z); l.z = tf32_hi(v.z - h.z);
-          h.w = tf32_hi(v.w); l.w = tf32_hi(v.w - h.w);
-          a4[q] = h;
+          float4 l;
+          l.x = tf32_hi(v.x - tf32_trunc(v.x));
+          l.y = tf32_hi(v.y - tf32_trunc(v.y));
+          l.z = tf32_hi(v.z - tf32_trunc(v.z));
+          l.w = tf32_hi(v.w - tf32_trunc(v.w));
           l4[q] = l;
         }
       }
@@ -389,20 +395,35 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         const int kb = kc * kKC + kq * 4;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (fast) {
+          const int npr = it_pb[r] - it_pa[r];
+          if (kc == 0) {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+              const int pl = it_pa[r] + pp;
+              if (pp < npr) {
+                const float4* y4 = reinterpret_cast<const float4*>(Ysb) + pl * 8 + i * 2;
+                yreg[r][pp][0] = y4[0];
+                yreg[r][pp][1] = y4[1];
+                soff[r][pp] = pslot[pl] * kKC + kq * 4;
+              }
+            }
+          }
           // I~ of k >= 2N is staged as zero, so no bound test is needed here
           bool re[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) re[q] = kb + q < N;
-          for (int pl = it_pa[r]; pl < it_pb[r]; ++pl) {
-            const float4* y4 = reinterpret_cast<const float4*>(Ysb) + pl * 8 + i * 2;
-            const float4 ya = y4[0], yb = y4[1];
-            const float4* I4 = Isb + pslot[pl] * kKC + kq * 4;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4 iv = I4[q];
-              const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
-              const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
-              z[q] += re[q] ? sr : -si;
+          for (int pp = 0; pp < 2; ++pp) {
+            if (pp < npr) {
+              const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
+              const float4* I4 = Isb + soff[r][pp];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 iv = I4[q];
+                const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
+                const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
+                z[q] += re[q] ? sr : -si;
+              }
             }
           }
         } else {
