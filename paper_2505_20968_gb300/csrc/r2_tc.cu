@@ -45,7 +45,10 @@ constexpr int kThreads = 64 + kGen;
 constexpr int kYPairs = 64;                   // pairs whose Y is staged in shared memory
 constexpr int kISlots = 32;                   // incident directions staged per K step
 constexpr int kYBytes = kYPairs * 32 * 4;     // one tile's Y (two buffers)
-constexpr int kIBytes = kISlots * kKC * 16;   // one K step's I~ (two buffers)
+// I~ staging: slot sl, K offset kl = 4 kq + q at float4 sl * kIStride + 4 q + kq, so
+// that the four kq of one q are 64 contiguous bytes and two slots sit 16 banks apart
+constexpr int kIStride = kKC + 4;
+constexpr int kIBytes = kISlots * kIStride * 16;   // one K step's I~ (two buffers)
 constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + (kMaxE + 3) * 4 + 256;
 constexpr int kSmemBytes = kStages * kABytes + kCBufs * kCBytes + 2 * kYBytes + 2 * kIBytes + kAuxBytes + 1024;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
@@ -85,12 +88,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
   return false;
 }
 
-// bulk asynchronous copy global -> shared (16-byte aligned ends, size a multiple of 16)
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// bulk asynchronous copy global -> shared (16-byte aligned ends, size a multiple
+// of 16) with an L2 eviction-priority policy
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
+}
+// the tiles are streamed once per apply: first out of L2, so that I~ and Y stay resident
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart
@@ -218,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   if (warp == 0) {
     // ---------------- TMA producer
     if (lane == 0) {
+      const uint64_t pol = policy_evict_first();
       int it = 0;
       for (; it < iters; ++it) {
         const int s = it % kStages;
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         // that the epilogue never reads
         const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
         mbar_expect_tx(&full[s], (uint32_t)N * kKC * 4);
-        bulk_load(A, src, (uint32_t)N * kKC * 4, &full[s]);
+        bulk_load(A, src, (uint32_t)N * kKC * 4, &full[s], pol);
       }
       if (*abort_flag) {
         // drain loads that were issued and may not have been consumed
@@ -358,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       unsigned char* Bhi = Alo + kABytes;
       unsigned char* Blo = Bhi + kBBytes;
       float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
-      float4* Isb = Is + (it & 1) * (kISlots * kKC);
+      float4* Isb = Is + (it & 1) * (kISlots * kIStride);
       if (kc == 0) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -370,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int q = gt + r * kGen;
-        if (q < ns * kKC) Isb[q] = ipre[r];
+        if (q < ns * kKC) Isb[(q / kKC) * kIStride + (q & 3) * 4 + ((q % kKC) >> 2)] = ipre[r];
       }
       if (it + 1 < iters) load_i(it + 1);
       {
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
                 const float4* y4 = reinterpret_cast<const float4*>(Ysb) + pl * 8 + i * 2;
                 yreg[r][pp][0] = y4[0];
                 yreg[r][pp][1] = y4[1];
-                soff[r][pp] = pslot[pl] * kKC + kq * 4;
+                soff[r][pp] = pslot[pl] * kIStride + kq;
               }
             }
           }
@@ -419,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
               const float4* I4 = Isb + soff[r][pp];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
-                const float4 iv = I4[q];
+                const float4 iv = I4[q * 4];
                 const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
                 const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
                 z[q] += re[q] ? sr : -si;
@@ -436,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
               const int k = kb + q;
               if (k >= 2 * N) continue;
               float4 iv;
-              if (sl >= 0) iv = Isb[sl * kKC + kq * 4 + q];
+              if (sl >= 0) iv = Isb[sl * kIStride + q * 4 + kq];
               else iv = *(const float4*)(Icz + ((size_t)pair_in[pp0 + pl] * N + (k < N ? k : k - N)) * 4);
               if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
               else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
