@@ -13,9 +13,9 @@
 // asynchronous copy per K step (the FP32 tiles are stored pre-swizzled, K
 // step by K step, so a step is one contiguous N x 64-byte block) and owns the
 // TMEM allocation; warp 1 issues
-// tcgen05.mma; warps 2-9 build B in shared memory from Y (staged per tile) and
-// I~ (staged per K step; both prefetched into registers one step ahead, so the
-// builders never wait on a global load), split A and B into TF32 hi/lo parts
+// tcgen05.mma; warps 2-9 build B in shared memory from Y (staged per tile,
+// prefetched into registers a tile ahead) and I~ (each lane loads the values
+// it needs one K step ahead into registers), split A and B into TF32 hi/lo parts
 // (3 products: hi*hi + hi*lo + lo*hi, FP32-level accuracy) in a 2-buffer
 // ring of their own, and run the epilogue from TMEM.  The A ring is deeper
 // than the builder ring so that enough tile bytes are in flight per SM to
@@ -32,7 +32,7 @@ namespace prd {
 
 namespace tc {
 
-constexpr int kStages = 7;                    // A (tile) ring
+constexpr int kStages = 7;                    // tile ring
 constexpr int kCBufs = 2;                     // builder ring: A_lo, B_hi, B_lo
 constexpr int kKC = 16;                       // fp32 per stage along K (64-byte rows)
 constexpr int kMaxE = 32;                     // output directions per CTA
@@ -43,17 +43,15 @@ constexpr int kCBytes = kABytes + 2 * kBBytes;
 constexpr int kGen = 256;                     // builder threads (warps 2-9)
 constexpr int kThreads = 64 + kGen;
 constexpr int kYPairs = 64;                   // pairs whose Y is staged in shared memory
-constexpr int kISlots = 32;                   // incident directions staged per K step
 constexpr int kYBytes = kYPairs * 32 * 4;     // one tile's Y (two buffers)
-// I~ staging: slot sl, K offset kl = 4 kq + q at float4 sl * kIStride + 4 q + kq, so
-// that the four kq of one q are 64 contiguous bytes and two slots sit 16 banks apart
-constexpr int kIStride = kKC + 4;
-constexpr int kIBytes = kISlots * kIStride * 16;   // one K step's I~ (two buffers)
-constexpr int kAuxBytes = kYPairs * 4 + kISlots * 4 + (kMaxE + 3) * 4 + 256;
-constexpr int kSmemBytes = kStages * kABytes + kCBufs * kCBytes + 2 * kYBytes + 2 * kIBytes + kAuxBytes + 1024;
+constexpr int kAuxBytes = (kMaxE + 2) * 4 + 256;
+// per builder warp: the next K step's I~ for its (<= 32) pairs, 5-float4 rows (conflict-free reads)
+constexpr int kWStride = 5;
+constexpr int kWBytes = (kGen / 32) * 32 * kWStride * 16;
+constexpr int kSmemBytes = kStages * kABytes + kCBufs * kCBytes + 2 * kYBytes + kWBytes + kAuxBytes + 1024;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
-static_assert(kYPairs * 8 <= 2 * kGen && kISlots * kKC <= 2 * kGen, "two prefetch registers per builder thread");
-static_assert(kNCPMax * 4 <= 2 * kGen, "two B items per builder thread");
+static_assert(kYPairs * 8 <= 2 * kGen, "Y prefetch registers");
+static_assert(kNCPMax == 128 && kGen == 256, "B items: 8 builder warps x 2 (32-row group, 4-k chunk)");
 constexpr long long kSpin = 1ll << 24;        // bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -100,6 +98,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
 
@@ -170,14 +173,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   // 1024-byte aligned base, derived by offset so that the compiler keeps the
   // shared address space on every pointer below (plain LDS/STS, no generic access)
   unsigned char* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
-  unsigned char* cbuf = sm + kStages * kABytes;                   // [buffer] A_lo, B_hi, B_lo
+  unsigned char* cbuf = sm + kStages * kABytes;                    // [buffer] A_lo, B_hi, B_lo
   float* Ys = (float*)(cbuf + kCBufs * kCBytes);                   // [buffer][pair][16][2]
-  float4* Is = (float4*)((unsigned char*)Ys + 2 * kYBytes);      // [buffer][slot][q]
-  int* pslot = (int*)((unsigned char*)Is + 2 * kIBytes);         // slot of each local pair
-  int* slot_dir = pslot + kYPairs;                                 // direction held in each slot
-  int* eptr = slot_dir + kISlots;                                  // local pair range of each output
-  int* nslot_p = eptr + kMaxE + 1;                                 // staged slots, fast-path flag
-  uint64_t* full = (uint64_t*)(((uintptr_t)(nslot_p + 2) + 7) & ~(uintptr_t)7);
+  float4* Wb = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [builder warp][pair][kWStride]
+  int* eptr = (int*)((unsigned char*)Wb + kWBytes);                // local pair range of each output
+  int* fast_p = eptr + kMaxE + 1;                                  // fast-path flag
+  uint64_t* full = (uint64_t*)(((uintptr_t)(fast_p + 1) + 7) & ~(uintptr_t)7);
   uint64_t* empty = full + kStages;
   uint64_t* ready = empty + kStages;
   uint64_t* cfree = ready + kCBufs;
@@ -198,7 +199,10 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int KCH = (2 * N + kKC - 1) / kKC;
   const int iters = p.ntile * KCH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gt = threadIdx.x - 64;               // builder thread index (warps 2..)
   const uint32_t tm_cols = 256u;                 // two M blocks x <= 128 columns
+  const int pp0 = pair_ptr[e0], npl = pair_ptr[e0 + E] - pp0;
+  const bool y_in_smem = npl <= kYPairs;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -213,6 +217,14 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (gt >= 0 && gt <= E) eptr[gt] = pair_ptr[e0 + gt] - pp0;
+  // the fast path needs every pair's Y staged and at most two pairs per output
+  if (gt == 0) {
+    bool all = y_in_smem;
+    for (int el = 0; el < E; ++el) all = all && pair_ptr[e0 + el + 1] - pair_ptr[e0 + el] <= 2;
+    // (so that a builder warp's 16 outputs have at most 32 pairs, one per lane)
+    *fast_p = all ? 1 : 0;
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(tm_cols));
@@ -222,31 +234,33 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  const bool fast = *fast_p != 0;
   const long long slab0 = ((long long)iz * p.ncls + c) * p.ntile;
   const int nmb = N > 128 ? 2 : 1;               // M blocks holding rows n < N
+  const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
 
   if (warp == 0) {
-    // ---------------- TMA producer
+    // ---------------- producer: one bulk copy per tile K step (lane 0)
+    int it = 0;
     if (lane == 0) {
-      const uint64_t pol = policy_evict_first();
-      int it = 0;
+      const uint64_t pol_t = policy_evict_first();
       for (; it < iters; ++it) {
         const int s = it % kStages;
         if (it >= kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1, abort_flag)) break;
         const int ti = it / KCH, kc = it - ti * KCH;
-        unsigned char* A = sm + s * kABytes;
+        const uint32_t abytes = (uint32_t)N * kKC * 4;
         // rows n >= N of the stage keep stale data: they only reach output rows
         // that the epilogue never reads
         const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
-        mbar_expect_tx(&full[s], (uint32_t)N * kKC * 4);
-        bulk_load(A, src, (uint32_t)N * kKC * 4, &full[s], pol);
+        mbar_expect_tx(&full[s], abytes);
+        bulk_load(sm + s * kABytes, src, abytes, &full[s], pol_t);
       }
-      if (*abort_flag) {
-        // drain loads that were issued and may not have been consumed
-        for (int j = max(0, it - kStages); j < it; ++j) {
-          const int s = j % kStages;
-          for (long long i = 0; i < kSpin && !mbar_try(&full[s], (j / kStages) & 1); ++i) {
-          }
+    }
+    if (lane == 0 && *abort_flag) {
+      // drain copies that were issued and may not have been consumed
+      for (int j = max(0, it - kStages); j < it; ++j) {
+        const int s = j % kStages;
+        for (long long i = 0; i < kSpin && !mbar_try(&full[s], (j / kStages) & 1); ++i) {
         }
       }
     }
@@ -289,51 +303,22 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     }
   } else {
     // ---------------- B builders / A splitters, then epilogue
-    const int gt = threadIdx.x - 64;                        // 0..255
-    const int pp0 = pair_ptr[e0], npl = pair_ptr[e0 + E] - pp0;
-    const bool y_in_smem = npl <= kYPairs;
-    if (gt <= E) eptr[gt] = pair_ptr[e0 + gt] - pp0;
-    // incident directions of this CTA's pairs -> staging slots (first kISlots distinct)
-    if (gt == 0) {
-      int ns = 0;
-      bool all = y_in_smem;
-      for (int el = 0; el < E; ++el) all = all && pair_ptr[e0 + el + 1] - pair_ptr[e0 + el] <= 2;
-      for (int pl = 0; pl < npl && pl < kYPairs; ++pl) {
-        const int op = pair_in[pp0 + pl];
-        int sidx = -1;
-        for (int s2 = 0; s2 < ns; ++s2)
-          if (slot_dir[s2] == op) { sidx = s2; break; }
-        if (sidx < 0 && ns < kISlots) { slot_dir[ns] = op; sidx = ns++; }
-        pslot[pl] = sidx;
-        all = all && sidx >= 0;
-      }
-      nslot_p[0] = ns;
-      nslot_p[1] = all ? 1 : 0;
-    }
-    gen_sync();
-    const int ns = nslot_p[0];
-    // fast path: every pair's Y and I~ are staged in shared memory and no output
-    // has more than two pairs; each thread then keeps its items' Y and I~ slot
-    // offsets in registers for a whole tile
-    const bool fast = nslot_p[1] != 0;
-    float4 yreg[2][2][2];
-    int soff[2][2];
-    // this thread's two B items (row = (output, Stokes i), 4-k chunk) and their pair ranges
+    const int bw = warp - 2;                       // builder warp
+    // B items: a warp takes 32 consecutive rows (output el = row / 4, Stokes i = row % 4)
+    // at one 4-k chunk kq, twice; the swizzle spreads each 8 lanes' stores over all banks
     int it_row[2], it_kq[2], it_pa[2], it_pb[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const int item = gt + r * kGen;
-      it_row[r] = item >> 2;
-      it_kq[r] = item & 3;
+      const int pr = bw * 2 + r;
+      it_row[r] = (pr & 3) * 32 + lane;
+      it_kq[r] = pr >> 2;
       const int el = it_row[r] >> 2;
-      const bool v = item < NCP * 4 && el < E;
+      const bool v = it_row[r] < NCP && el < E;
       it_pa[r] = v ? eptr[el] : 0;
       it_pb[r] = v ? eptr[el + 1] : 0;
     }
     const size_t ybase = (size_t)iz * p.npairs + pp0;
-    const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
-    // prefetch registers: Y of the next tile, I~ of the next K step
-    float4 ypre[2], ipre[2];
+    float4 ypre[2];
     auto load_y = [&](int ti) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -342,51 +327,79 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           ypre[r] = *((const float4*)(p.Y + ((ybase + (q >> 3)) * p.ntile + ti) * 32) + (q & 7));
       }
     };
+    // fast path: each lane keeps its items' Y rows for the tile in registers; the
+    // warp's 16 outputs have <= 32 pairs, lane l loads pair l's four I~ values of
+    // the warp's 4-k chunk one K step ahead and shares them through Wb
+    const int kqw = bw >> 1;                       // the warp's 4-k chunk (both items)
+    const int el0 = ((bw * 2) & 3) * 8;            // first output of the warp's 64 rows
+    const int pw0 = el0 < E ? eptr[el0] : 0;
+    const int npw = el0 < E ? eptr[min(el0 + 16, E)] - pw0 : 0;
+    float4* Ww = Wb + bw * (32 * kWStride);
+    float4 yreg[2][2][2];
+    float4 inext[4];
+    const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
+    const int irow = (fast && lane < npw) ? pair_in[pp0 + pw0 + lane] * N : 0;
     auto load_i = [&](int it) {
-      const int kc = it % KCH;
+      const int kb = (it % KCH) * kKC + kqw * 4;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int q = gt + r * kGen;
-        if (q < ns * kKC) {
-          const int sl = q / kKC, k = kc * kKC + (q - sl * kKC);
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (k < 2 * N) v = *(const float4*)(Icz + ((size_t)slot_dir[sl] * N + (k < N ? k : k - N)) * 4);
-          ipre[r] = v;
-        }
+      for (int q = 0; q < 4; ++q) {
+        const int k = kb + q;
+        inext[q] = (lane < npw && k < 2 * N) ? Icz4[irow + (k < N ? k : k - N)] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    if (iters > 0) { load_y(0); load_i(0); }
+    if (fast) load_i(0);
+    load_y(0);
+    bool aborted = false;
     for (int it = 0; it < iters; ++it) {
       const int s = it % kStages, cb = it % kCBufs;
-      // the tile stage has landed and the MMAs that last read builder buffer cb
-      // are done; all builders agree (and are done with the step before)
-      bool got = mbar_wait(&full[s], (it / kStages) & 1, abort_flag);
-      if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag);
-      if (!gen_all(got)) break;
       const int ti = it / KCH, kc = it - ti * KCH;
-      unsigned char* A = sm + s * kABytes;
-      unsigned char* Alo = cbuf + cb * kCBytes;
-      unsigned char* Bhi = Alo + kABytes;
-      unsigned char* Blo = Bhi + kBBytes;
+      bool got = !aborted && mbar_wait(&full[s], (it / kStages) & 1, abort_flag);
+      if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag);
       float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
-      float4* Isb = Is + (it & 1) * (kISlots * kIStride);
+      if (fast) {
+        // this step's I~ into the warp's buffer (the warp is done with the last one)
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Ww[lane * kWStride + q] = inext[q];
+        __syncwarp();
+      }
       if (kc == 0) {
+        // a new tile: stage its Y, then all builders agree to go on (every builder
+        // reaches this barrier, aborted or not, so none waits for one that left)
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int q = gt + r * kGen;
           if (y_in_smem && q < npl * 8) ((float4*)Ysb)[q] = ypre[r];
         }
+        got = gen_all(got);
+        if (got && fast) {
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int npr = it_pb[r] - it_pa[r], i = it_row[r] & 3;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+              if (pp < npr) {
+                const float4* y4 = reinterpret_cast<const float4*>(Ysb) + (it_pa[r] + pp) * 8 + i * 2;
+                yreg[r][pp][0] = y4[0];
+                yreg[r][pp][1] = y4[1];
+              }
+            }
+          }
+        }
         if (ti + 1 < p.ntile) load_y(ti + 1);
       }
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int q = gt + r * kGen;
-        if (q < ns * kKC) Isb[(q / kKC) * kIStride + (q & 3) * 4 + ((q % kKC) >> 2)] = ipre[r];
+      if (!got) {
+        aborted = true;
+        continue;
       }
-      if (it + 1 < iters) load_i(it + 1);
+      unsigned char* A = sm + s * kABytes;
+      unsigned char* Alo = cbuf + cb * kCBytes;
+      unsigned char* Bhi = Alo + kABytes;
+      unsigned char* Blo = Bhi + kBBytes;
       {
         const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
+#pragma unroll 4
         for (int q = gt; q < N * (kKC / 4); q += kGen) {
           const float4 v = a4[q];
           float4 l;
@@ -397,8 +410,6 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           l4[q] = l;
         }
       }
-      gen_sync();
-      // items (row, 4-k chunk): a warp covers 8 rows x 4 chunks = one 512-byte swizzle atom
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int row = it_row[r], kq = it_kq[r], i = row & 3;
@@ -407,30 +418,16 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (fast) {
           const int npr = it_pb[r] - it_pa[r];
-          if (kc == 0) {
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-              const int pl = it_pa[r] + pp;
-              if (pp < npr) {
-                const float4* y4 = reinterpret_cast<const float4*>(Ysb) + pl * 8 + i * 2;
-                yreg[r][pp][0] = y4[0];
-                yreg[r][pp][1] = y4[1];
-                soff[r][pp] = pslot[pl] * kIStride + kq;
-              }
-            }
-          }
-          // I~ of k >= 2N is staged as zero, so no bound test is needed here
           bool re[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) re[q] = kb + q < N;
+          for (int q = 0; q < 4; ++q) re[q] = kb + q < N;   // I~ past 2N was loaded as zero
 #pragma unroll
           for (int pp = 0; pp < 2; ++pp) {
             if (pp < npr) {
               const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
-              const float4* I4 = Isb + soff[r][pp];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
-                const float4 iv = I4[q * 4];
+                const float4 iv = Ww[(it_pa[r] + pp - pw0) * kWStride + q];
                 const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
                 const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
                 z[q] += re[q] ? sr : -si;
@@ -441,14 +438,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           for (int pl = it_pa[r]; pl < it_pb[r]; ++pl) {
             const float* y = y_in_smem ? Ysb + pl * 32 : p.Y + ((ybase + pl) * p.ntile + ti) * 32;
             const float4 ya = *(const float4*)(y + i * 8), yb = *(const float4*)(y + i * 8 + 4);
-            const int sl = (pl < kYPairs) ? pslot[pl] : -1;
+            const float4* ir = reinterpret_cast<const float4*>(Icz) + (size_t)pair_in[pp0 + pl] * N;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int k = kb + q;
               if (k >= 2 * N) continue;
-              float4 iv;
-              if (sl >= 0) iv = Isb[sl * kIStride + q * 4 + kq];
-              else iv = *(const float4*)(Icz + ((size_t)pair_in[pp0 + pl] * N + (k < N ? k : k - N)) * 4);
+              const float4 iv = ir[k < N ? k : k - N];
               if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
               else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
             }
@@ -462,6 +457,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         *(float4*)(Bhi + swz64(row, kq * 4)) = hi;
         *(float4*)(Blo + swz64(row, kq * 4)) = lo;
       }
+      // the next K step's I~, consumed a whole step later
+      if (fast && it + 1 < iters) load_i(it + 1);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&ready[cb]);
     }
