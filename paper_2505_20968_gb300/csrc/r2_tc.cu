@@ -7,22 +7,24 @@
 // basis, Eq. RQIIKKp / Eq. G) and
 //     B[ti][k][(o,i)] = sum_{o' in class, j} Ycomp_{ti,ij}(o,o') I~_j(o', m)
 // with Ycomp = Re Y for k = m < N and -Im Y for k = N + m (so that the sum is
-// Re(T Z) over the complex tile T and Z = Y I~).
+// Re(T Z) over the complex tile T and Z = Y I~).  The MMA computes the
+// transpose, D[(o,i)][n] = sum_k B^T[(o,i)][k] A^T[k][n]: M = 128 Stokes
+// columns, N = all tile rows n (<= 256, padded to 16), so one MMA per K
+// slice covers a whole tile step without padding n to a second M block.
 //
-// Roles (320 threads): warp 0 streams A into a 7-stage ring with one bulk
-// asynchronous copy per K step (the FP32 tiles are stored pre-swizzled, K
+// Roles (320 threads): warp 0 streams the tile into a 7-stage ring with one
+// bulk asynchronous copy per K step (the FP32 tiles are stored pre-swizzled, K
 // step by K step, so a step is one contiguous N x 64-byte block) and owns the
-// TMEM allocation; warp 1 issues
-// tcgen05.mma; warps 2-9 build B in shared memory from Y (staged per tile,
-// prefetched into registers a tile ahead) and I~ (each lane loads the values
-// it needs one K step ahead into registers), split A and B into TF32 hi/lo parts
-// (3 products: hi*hi + hi*lo + lo*hi, FP32-level accuracy) in a 2-buffer
-// ring of their own, and run the epilogue from TMEM.  The A ring is deeper
-// than the builder ring so that enough tile bytes are in flight per SM to
-// cover HBM latency at full bandwidth.
-// Accumulators: two M = 128 blocks (rows n < 256) x NCP columns of TMEM.
-// Every mbarrier wait is bounded; on expiry the CTA records an error flag,
-// drains what it issued and returns.
+// TMEM allocation; warp 1 issues tcgen05.mma; warps 2-9 build B in shared
+// memory from Y (staged per tile, prefetched into registers a tile ahead) and
+// I~ (each lane loads the values its warp needs one K step ahead and shares
+// them through a per-warp buffer), split both operands into TF32 hi/lo parts
+// (3 products: hi*hi + hi*lo + lo*hi, FP32-level accuracy) in a 2-buffer ring
+// of their own, and run the epilogue from TMEM.  The tile ring is deeper than
+// the builder ring so that enough tile bytes are in flight per SM to cover
+// HBM latency at full bandwidth.
+// Accumulator: 128 TMEM lanes x NM columns.  Every mbarrier wait is bounded; on
+// expiry the CTA records an error flag, drains what it issued and returns.
 #include <cstdio>
 #include <vector>
 #include "prd_internal.h"
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int iters = p.ntile * KCH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gt = threadIdx.x - 64;               // builder thread index (warps 2..)
-  const uint32_t tm_cols = 256u;                 // two M blocks x <= 128 columns
+  const uint32_t tm_cols = 256u;                 // D: 128 lanes x NM (<= 256) columns
   const int pp0 = pair_ptr[e0], npl = pair_ptr[e0 + E] - pp0;
   const bool y_in_smem = npl <= kYPairs;
 
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const uint32_t tmem = *tmem_slot;
   const bool fast = *fast_p != 0;
   const long long slab0 = ((long long)iz * p.ncls + c) * p.ntile;
-  const int nmb = N > 128 ? 2 : 1;               // M blocks holding rows n < N
+  const int NM = (N + 15) / 16 * 16;             // MMA N: the tile rows n (<= 256)
   const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
 
   if (warp == 0) {
@@ -267,7 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NCP >> 3) << 17) | ((128u >> 4) << 24);
+      // D[(o,i)][n] (M = 128 Stokes columns of the chunk, N = NM tile rows): the built
+      // operand is A, the streamed tile is B, so one MMA covers every row n
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NM >> 3) << 17) | ((128u >> 4) << 24);
       int issued = 0;
       for (int it = 0; it < iters; ++it) {
         const int s = it % kStages, cb = it % kCBufs;
@@ -277,15 +281,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         unsigned char* Alo = cbuf + cb * kCBytes;
         unsigned char* Bhi = Alo + kABytes;
         unsigned char* Blo = Bhi + kBBytes;
-        for (int mb = 0; mb < nmb; ++mb) {
-          const uint32_t d = tmem + (uint32_t)(mb * NCP);
-          for (int ks = 0; ks < 2; ++ks) {
-            const int ao = mb * (kABytes / 2) + ks * 32, bo = ks * 32;
-            const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
-            mma_tf32(d, sdesc(A + ao), sdesc(Bhi + bo), idesc, acc);
-            mma_tf32(d, sdesc(A + ao), sdesc(Blo + bo), idesc, 1u);
-            mma_tf32(d, sdesc(Alo + ao), sdesc(Bhi + bo), idesc, 1u);
-          }
+        for (int ks = 0; ks < 2; ++ks) {
+          const int o = ks * 32;                   // 8 fp32 of K per MMA
+          const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(tmem, sdesc(Bhi + o), sdesc(A + o), idesc, acc);
+          mma_tf32(tmem, sdesc(Blo + o), sdesc(A + o), idesc, 1u);
+          mma_tf32(tmem, sdesc(Bhi + o), sdesc(Alo + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
         mma_commit(&cfree[cb]);
@@ -468,27 +469,24 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     if (ok) {
       const int q = warp & 3;                    // TMEM lane quarter of this warp
       const int par = (warp - 2) >> 2;           // two warps per quarter split the 16-column groups
-      const int r = q * 32 + lane;
-      for (int mb = 0; mb < nmb; ++mb) {
-        const int n = mb * 128 + r;
-        for (int c0 = par * 16; c0 < NCP; c0 += 32) {
-          uint32_t v[16];
-          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mb * NCP + c0);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(ta));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (n < N) {
+      const int r = q * 32 + lane;               // D row: Stokes column (output el = r / 4, i = r % 4)
+      const bool live = r < 4 * E;
+      const int o = live ? cout_dir[e0 + (r >> 2)] : 0;
+      float* dst = p.eb + (((size_t)iz * p.nO + o) * N) * 4 + (r & 3);
+      for (int c0 = par * 16; c0 < NM; c0 += 32) {
+        uint32_t v[16];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (live) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int col = c0 + j;
-              if (col < 4 * E) {
-                const int o = cout_dir[e0 + col / 4];
-                atomicAdd(p.eb + (((size_t)iz * p.nO + o) * N + n) * 4 + (col & 3), __uint_as_float(v[j]));
-              }
-            }
+          for (int j = 0; j < 16; ++j) {
+            const int n = c0 + j;
+            if (n < N) atomicAdd(dst + (size_t)n * 4, __uint_as_float(v[j]));
           }
         }
       }
