@@ -124,6 +124,12 @@ int prd_sizes(const prd_ctx* ctx, int* nz, int* n_omega, int* nnu, int* n_theta,
 int prd_directions(const prd_ctx* ctx, double* mu, double* chi, double* w);
 /* Bytes of device memory the library holds after setup (tiles + tables). */
 int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes);
+/* Work of one R_II contraction (Eq. G summed over the tiles of every class,
+ * Sect. 4): *flops = 2 x (real multiply-adds of Re(T Z) over all heights,
+ * classes, tiles, rows n, columns k < 2N and Stokes outputs), *bytes = tile
+ * bytes read once per apply.  Either pointer may be NULL.  For roofline
+ * accounting; PRD_E_STATE before prd_setup. */
+int prd_contraction_work(const prd_ctx* ctx, double* flops, double* bytes);
 
 /* b = Lambda eps_th + t  (right-hand side of Eq. linear_system). */
 int prd_rhs(prd_ctx* ctx, void* b_dev);

@@ -36,7 +36,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_workspace_bytes", "prd_rhs", "prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator",
            "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
-           "prd_device_status"]
+           "prd_device_status", "prd_contraction_work"]
 
 
 def lib():
@@ -61,6 +61,7 @@ def lib():
                                 ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]
         L.prd_directions.argtypes = [P, DP, DP, DP]
         L.prd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        L.prd_contraction_work.argtypes = [P, DP, DP]
         for f in ("prd_rhs",):
             getattr(L, f).argtypes = [P, P]
         for f in ("prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator", "prd_apply_preconditioner",
@@ -127,6 +128,12 @@ class PRD:
                                          chi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         self.mu, self.chi, self.w = mu, chi, w
+
+    def contraction_work(self):
+        """(flops, bytes) of one R_II contraction (roofline accounting)."""
+        f, b = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().prd_contraction_work(self.h, ctypes.byref(f), ctypes.byref(b)))
+        return f.value, b.value
 
     def workspace_bytes(self):
         b = ctypes.c_int64()

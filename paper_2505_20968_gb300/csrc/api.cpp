@@ -289,6 +289,18 @@ int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
   return PRD_OK;
 }
 
+int prd_contraction_work(const prd_ctx* ctx, double* flops, double* bytes) {
+  if (!ctx) return PRD_E_ARG;
+  const Ctx* c = &ctx->c;
+  if (!c->ready) return PRD_E_STATE;
+  const double N = c->nnu, per_tile_out = (double)c->ntile() * N * 2.0 * N;   // tile elements per class
+  double outs = 0;                                                               // Stokes outputs per class
+  for (int k = 0; k < c->ncls; ++k) outs += 4.0 * (c->cout_ptr[k + 1] - c->cout_ptr[k]);
+  if (flops) *flops = 2.0 * c->nz * per_tile_out * outs;
+  if (bytes) *bytes = (double)c->nz * c->ncls * per_tile_out * c->esz;
+  return PRD_OK;
+}
+
 int prd_rhs(prd_ctx* ctx, void* b_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();

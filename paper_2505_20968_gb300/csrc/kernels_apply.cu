@@ -90,70 +90,96 @@ __global__ void spline_eval_kernel(const T* __restrict__ y, const T* __restrict_
 }
 
 // ------------------------------------------------------------------ R_III
-// J[z][ku kv] += sum_{o', j} rin[z][o'][q][j] * sum_m r3w[z][q][m] I~[z][o'][m][j]
+// J[z][ku kv] += sum_{o', j} rin[z][o'][q][j] * sum_m r3w[z][q][m] I~[z][o'][m][j],  q = (ku kv, l')
+// One block per (o', z): the direction's comoving row I~[z][o'][.][.] is staged in
+// shared memory and thread q forms S_j = sum_m r3w[q][m] I~_j(m) (arithmetic in A,
+// so the FP32 path runs on the FP32 pipe), then adds sum_j rin_j S_j to J in FP64.
 template <typename T, typename A>
 __global__ void r3_J_kernel(const A* __restrict__ Ic, const T* __restrict__ r3w, const T* __restrict__ rin,
                             double* __restrict__ J, int nO, int N, int nq, int nl) {
-  const int q = blockIdx.x, iz = blockIdx.y;
-  const T* w = r3w + ((size_t)iz * nq + q) * 2 * N;
-  double accr = 0.0, acci = 0.0;
-  for (int idx = threadIdx.x; idx < nO * N; idx += blockDim.x) {
-    const int o = idx / N, m = idx - o * N;
-    const A* iv = Ic + (((size_t)iz * nO + o) * N + m) * 4;
+  using V = typename V4<A>::type;
+  const int o = blockIdx.x, iz = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char r3smem[];
+  V* row = reinterpret_cast<V*>(r3smem);
+  const V* src = reinterpret_cast<const V*>(Ic) + ((size_t)iz * nO + o) * N;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) row[m] = src[m];
+  __syncthreads();
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const T* w = r3w + ((size_t)iz * nq + q) * 2 * N;
+    A sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
+    for (int m = 0; m < N; ++m) {
+      const A wr = (A)w[m], wi = (A)w[N + m];
+      const V iv = row[m];
+      sr[0] += wr * iv.x; sr[1] += wr * iv.y; sr[2] += wr * iv.z; sr[3] += wr * iv.w;
+      si[0] += wi * iv.x; si[1] += wi * iv.y; si[2] += wi * iv.z; si[3] += wi * iv.w;
+    }
     const T* ri = rin + (((size_t)iz * nO + o) * nq + q) * 8;
-    const double wr = (double)w[m], wi = (double)w[N + m];
-    double sr = 0.0, si = 0.0;
+    double jr = 0.0, ji = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      sr += (double)ri[2 * j] * (double)iv[j];
-      si += (double)ri[2 * j + 1] * (double)iv[j];
+      const double rr = (double)ri[2 * j], rm = (double)ri[2 * j + 1];
+      jr += rr * (double)sr[j] - rm * (double)si[j];
+      ji += rr * (double)si[j] + rm * (double)sr[j];
     }
-    accr += wr * sr - wi * si;
-    acci += wr * si + wi * sr;
-  }
-  __shared__ double red[2][256];
-  red[0][threadIdx.x] = accr;
-  red[1][threadIdx.x] = acci;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + s];
-      red[1][threadIdx.x] += red[1][threadIdx.x + s];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
     const int uv = q / nl;
-    atomicAdd(&J[((size_t)iz * (nq / nl) + uv) * 2], red[0][0]);
-    atomicAdd(&J[((size_t)iz * (nq / nl) + uv) * 2 + 1], red[1][0]);
+    atomicAdd(&J[((size_t)iz * (nq / nl) + uv) * 2], jr);
+    atomicAdd(&J[((size_t)iz * (nq / nl) + uv) * 2 + 1], ji);
   }
 }
 
-// eps_bar[z][o][n][i] = Re sum_uv ab[uv] J[uv] sum_kl' O_i(o; uv, kl') prof[uv][kl'][n]
+// eps_bar[z][o][n][i] = Re sum_uv ab[uv] J[uv] sum_l' O_i(o; uv, l') prof[uv][l'][n]
+// One block per (o, z), one thread per n: C = ab J per uv and the direction's
+// O_i coefficients are staged in shared memory; the profile rows are read
+// coalesced along n.  Arithmetic in A.
 template <typename T, typename A>
 __global__ void r3_out_kernel(const double* __restrict__ J, const T* __restrict__ ab, const T* __restrict__ rout,
                               const T* __restrict__ prof, A* __restrict__ eb, int nz, int nO, int N, int nuv,
                               int nl) {
-  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pt >= (long long)nz * nO * N) return;
-  const int n = (int)(pt % N);
-  const int zo = (int)(pt / N), iz = zo / nO;
-  double acc[4] = {0, 0, 0, 0};
-  for (int uv = 0; uv < nuv; ++uv) {
+  const int o = blockIdx.x, iz = blockIdx.y;
+  const int zo = iz * nO + o;
+  extern __shared__ __align__(16) unsigned char r3smem[];
+  A* C = reinterpret_cast<A*>(r3smem);                 // [uv][2]
+  A* R = C + 2 * nuv;                                  // [uv][l'][8]
+  for (int uv = threadIdx.x; uv < nuv; uv += blockDim.x) {
     const double jr = J[((size_t)iz * nuv + uv) * 2], ji = J[((size_t)iz * nuv + uv) * 2 + 1];
     const double ar = (double)ab[((size_t)iz * nuv + uv) * 2], ai = (double)ab[((size_t)iz * nuv + uv) * 2 + 1];
-    const double cr = ar * jr - ai * ji, ci = ar * ji + ai * jr;
-    for (int lp = 0; lp < nl; ++lp) {
-      const T* pp = prof + ((((size_t)iz * nuv + uv) * nl + lp) * N + n) * 2;
-      const double pr = (double)pp[0], pi = (double)pp[1];
-      const double dr = cr * pr - ci * pi, di = cr * pi + ci * pr;
-      const T* ro = rout + (((size_t)zo * nuv + uv) * nl + lp) * 8;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[i] += (double)ro[2 * i] * dr - (double)ro[2 * i + 1] * di;
-    }
+    C[2 * uv] = (A)(ar * jr - ai * ji);
+    C[2 * uv + 1] = (A)(ar * ji + ai * jr);
   }
-  A* o = eb + pt * 4;
-  for (int i = 0; i < 4; ++i) o[i] = (A)acc[i];
+  for (int k = threadIdx.x; k < nuv * nl * 8; k += blockDim.x) R[k] = (A)rout[(size_t)zo * nuv * nl * 8 + k];
+  __syncthreads();
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    A acc[4] = {0, 0, 0, 0};
+    for (int uv = 0; uv < nuv; ++uv) {
+      const A cr = C[2 * uv], ci = C[2 * uv + 1];
+      for (int lp = 0; lp < nl; ++lp) {
+        const T* pp = prof + ((((size_t)iz * nuv + uv) * nl + lp) * N + n) * 2;
+        const A pr = (A)pp[0], pi = (A)pp[1];
+        const A dr = cr * pr - ci * pi, di = cr * pi + ci * pr;
+        const A* ro = R + (uv * nl + lp) * 8;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += ro[2 * i] * dr - ro[2 * i + 1] * di;
+      }
+    }
+    A* out = eb + ((size_t)zo * N + n) * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = acc[i];
+  }
+}
+
+// launchers (shared by the apply and the line-of-sight paths)
+template <typename T, typename A>
+static void launch_r3_J(Ctx* c, const A* Ic, double* J, int nO) {
+  const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st, N = c->nnu;
+  r3_J_kernel<T, A><<<dim3(nO, c->nz), 128, (size_t)N * 4 * sizeof(A), c->stream>>>(
+      Ic, (const T*)c->r3w.p, (const T*)c->r3in.p, J, nO, N, nq, c->nl_st);
+}
+template <typename T, typename A>
+static void launch_r3_out(Ctx* c, const double* J, const T* rout, A* eb, int nO) {
+  const int nuv = c->nu_st * c->nu_st, N = c->nnu;
+  const size_t smem = sizeof(A) * ((size_t)2 * nuv + (size_t)nuv * c->nl_st * 8);
+  r3_out_kernel<T, A><<<dim3(nO, c->nz), N <= 128 ? 128 : 256, smem, c->stream>>>(
+      J, (const T*)c->r3ab.p, rout, (const T*)c->r3prof.p, eb, c->nz, nO, N, nuv, c->nl_st);
 }
 
 // ------------------------------------------------------------------ R_II (SIMT)
@@ -394,11 +420,8 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
   double* J = J_ext ? J_ext : (double*)c->r3J.p;
   PRD_CUDA_TRY(c, cudaMemsetAsync(J, 0, (size_t)nz * nuv * 2 * sizeof(double), c->stream));
-  r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>(Ic, (const T*)c->r3w.p, (const T*)c->r3in.p,
-                                                        J, nO, N, nq, c->nl_st);
-  r3_out_kernel<T, A><<<ceil_div(npt, 128), 128, 0, c->stream>>>((const double*)J, (const T*)c->r3ab.p,
-                                                               (const T*)c->r3out.p, (const T*)c->r3prof.p, eb, nz,
-                                                               nO, N, nuv, c->nl_st);
+  launch_r3_J<T, A>(c, Ic, J, nO);
+  launch_r3_out<T, A>(c, (const double*)J, (const T*)c->r3out.p, eb, nO);
   stage_end(c, ST_S5, e0);
   // S3 + S4
   stage_begin(c, ST_S3, &e0);
@@ -636,10 +659,8 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
   planck_comoving_kernel<A><<<ceil_div(npt, 256), 256, 0, c->stream>>>((A*)Icw.p, (const double*)wtd.p, nz, nO, N);
   PRD_CUDA_TRY(c, cudaMemsetAsync(Jx.p, 0, Jx.bytes, c->stream));
   PRD_CUDA_TRY(c, cudaMemsetAsync(Jw.p, 0, Jw.bytes, c->stream));
-  r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>((const A*)Icx.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
-                                                        (double*)Jx.p, nO, N, nq, nl);
-  r3_J_kernel<T, A><<<dim3(nq, nz), 256, 0, c->stream>>>((const A*)Icw.p, (const T*)c->r3w.p, (const T*)c->r3in.p,
-                                                        (double*)Jw.p, nO, N, nq, nl);
+  launch_r3_J<T, A>(c, (const A*)Icx.p, (double*)Jx.p, nO);
+  launch_r3_J<T, A>(c, (const A*)Icw.p, (double*)Jw.p, nO);
   PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   const double mu1 = 1.0;
   for (int l = 0; l < nlos && !rc; ++l) {
@@ -655,10 +676,8 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       break;
     (void)mu1;
     // R_III parts initialise the comoving rows
-    r3_out_kernel<T, A><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
-        (const double*)Jx.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (A*)es_bar.p, nz, 1, N, nuv, nl);
-    r3_out_kernel<T, A><<<ceil_div((long long)nz * N, 128), 128, 0, c->stream>>>(
-        (const double*)Jw.p, (const T*)c->r3ab.p, (const T*)rout.p, (const T*)c->r3prof.p, (A*)ew_bar.p, nz, 1, N, nuv, nl);
+    launch_r3_out<T, A>(c, (const double*)Jx.p, (const T*)rout.p, (A*)es_bar.p, 1);
+    launch_r3_out<T, A>(c, (const double*)Jw.p, (const T*)rout.p, (A*)ew_bar.p, 1);
     // R_II: tiles of every height for the LOS classes, then the contraction
     for (int iz = 0; iz < nz && !rc; ++iz) {
       std::vector<double> th(L.theta);
