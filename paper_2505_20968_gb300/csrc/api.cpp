@@ -44,7 +44,9 @@ static void free_all(Ctx* c) {
                   &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk, &c->cls_dev, &c->dmu,
                   &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
                   &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
-                  &c->tc_err, &c->tc_work};
+                  &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64, &c->r3out64,
+                  &c->r3prof64, &c->r3ab64};
+  c->has64 = false;
   c->tc_ready = false;
   for (DBuf* b : bufs) dfree(*b);
   for (auto& b : c->krylov) dfree(b);
@@ -107,6 +109,16 @@ static int setup(Ctx* c) {
   PRD_CUDA_TRY(c, cudaMemset(c->tiles.p, 0, tile_bytes));   // row padding (ld > 2N) stays zero
   const int nq = c->nu_st * c->nu_st * c->nl_st;
   if ((rc = dalloc(c, c->r3w, (size_t)c->nz * nq * 2 * c->nnu * c->esz))) return rc;
+  // FP64 Sigma tables for the refinement residuals (FP32 mode), if they fit with room to spare
+  if (c->prec == PRD_FP32) {
+    const size_t t64 = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * c->ld64() * 8;
+    PRD_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
+    if (t64 < fr * 0.6) {
+      if ((rc = dalloc(c, c->tiles64, t64))) return rc;
+      if ((rc = dalloc(c, c->r3w64, (size_t)c->nz * nq * 2 * c->nnu * 8))) return rc;
+      c->has64 = true;
+    }
+  }
   if ((rc = upload(c, c->dmu, c->mu.data(), c->mu.size() * 8))) return rc;
   if ((rc = build_device_tables(c))) return rc;
   if ((rc = dalloc(c, c->gm_t, nvec(c) * c->esz))) return rc;

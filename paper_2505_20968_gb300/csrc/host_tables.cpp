@@ -330,6 +330,7 @@ int build_device_tables(Ctx* c) {
         }
     }
     if ((rc = upload_T(c, c->Y, Y))) return rc;
+    if (c->has64 && (rc = upload(c, c->Y64, Y.data(), Y.size() * 8))) return rc;
   }
   // ---- R_III separable factors
   {
@@ -372,6 +373,10 @@ int build_device_tables(Ctx* c) {
     }
     if ((rc = upload_T(c, c->r3in, rin)) || (rc = upload_T(c, c->r3out, rout)) || (rc = upload_T(c, c->r3prof, prof)) ||
         (rc = upload_T(c, c->r3ab, ab)))
+      return rc;
+    if (c->has64 &&
+        ((rc = upload(c, c->r3in64, rin.data(), rin.size() * 8)) || (rc = upload(c, c->r3out64, rout.data(), rout.size() * 8)) ||
+         (rc = upload(c, c->r3prof64, prof.data(), prof.size() * 8)) || (rc = upload(c, c->r3ab64, ab.data(), ab.size() * 8))))
       return rc;
     if ((rc = dalloc(c, c->r3J, (size_t)nz * nuv * 2 * sizeof(double)))) return rc;
   }

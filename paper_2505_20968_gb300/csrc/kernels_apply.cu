@@ -167,19 +167,31 @@ __global__ void r3_out_kernel(const double* __restrict__ J, const T* __restrict_
   }
 }
 
+// The Sigma tables an apply reads: the ctx precision's, or (FP32 mode, t64) the
+// FP64 copies kept for the refinement residuals.
+struct SigmaTables {
+  const void *tiles, *Y, *r3w, *r3in, *r3out, *r3prof, *r3ab;
+  int ld, tiled;
+};
+static SigmaTables sigma_tables(const Ctx* c, bool t64) {
+  if (t64)
+    return {c->tiles64.p, c->Y64.p, c->r3w64.p, c->r3in64.p, c->r3out64.p, c->r3prof64.p, c->r3ab64.p, c->ld64(), 0};
+  return {c->tiles.p, c->Y.p, c->r3w.p, c->r3in.p, c->r3out.p, c->r3prof.p, c->r3ab.p, c->ld(), c->tiled() ? 1 : 0};
+}
+
 // launchers (shared by the apply and the line-of-sight paths)
 template <typename T, typename A>
-static void launch_r3_J(Ctx* c, const A* Ic, double* J, int nO) {
+static void launch_r3_J(Ctx* c, const A* Ic, double* J, int nO, const SigmaTables& tb) {
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st, N = c->nnu;
   r3_J_kernel<T, A><<<dim3(nO, c->nz), 128, (size_t)N * 4 * sizeof(A), c->stream>>>(
-      Ic, (const T*)c->r3w.p, (const T*)c->r3in.p, J, nO, N, nq, c->nl_st);
+      Ic, (const T*)tb.r3w, (const T*)tb.r3in, J, nO, N, nq, c->nl_st);
 }
 template <typename T, typename A>
-static void launch_r3_out(Ctx* c, const double* J, const T* rout, A* eb, int nO) {
+static void launch_r3_out(Ctx* c, const double* J, const T* rout, A* eb, int nO, const SigmaTables& tb) {
   const int nuv = c->nu_st * c->nu_st, N = c->nnu;
   const size_t smem = sizeof(A) * ((size_t)2 * nuv + (size_t)nuv * c->nl_st * 8);
   r3_out_kernel<T, A><<<dim3(nO, c->nz), N <= 128 ? 128 : 256, smem, c->stream>>>(
-      J, (const T*)c->r3ab.p, rout, (const T*)c->r3prof.p, eb, c->nz, nO, N, nuv, c->nl_st);
+      J, (const T*)tb.r3ab, rout, (const T*)tb.r3prof, eb, c->nz, nO, N, nuv, c->nl_st);
 }
 
 // ------------------------------------------------------------------ R_II (SIMT)
@@ -400,8 +412,9 @@ __global__ void fill_planck_kernel(T* __restrict__ x, const double* __restrict__
 // ------------------------------------------------------------------ launchers
 template <typename T, typename A>
 static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = nullptr, A* M_ext = nullptr,
-                   A* Ic_ext = nullptr, double* J_ext = nullptr) {
+                   A* Ic_ext = nullptr, double* J_ext = nullptr, bool t64 = false) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const SigmaTables tb = sigma_tables(c, t64);
   const long long npt = (long long)nz * nO * N;
   A* Mb = M_ext ? M_ext : (A*)c->scratch1.p;
   A* M = Mb;
@@ -420,14 +433,14 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
   double* J = J_ext ? J_ext : (double*)c->r3J.p;
   PRD_CUDA_TRY(c, cudaMemsetAsync(J, 0, (size_t)nz * nuv * 2 * sizeof(double), c->stream));
-  launch_r3_J<T, A>(c, Ic, J, nO);
-  launch_r3_out<T, A>(c, (const double*)J, (const T*)c->r3out.p, eb, nO);
+  launch_r3_J<T, A>(c, Ic, J, nO, tb);
+  launch_r3_out<T, A>(c, (const double*)J, (const T*)tb.r3out, eb, nO, tb);
   stage_end(c, ST_S5, e0);
   // S3 + S4
   stage_begin(c, ST_S3, &e0);
   const int nchunk = (c->max_cout + kCW - 1) / kCW;
   if constexpr (std::is_same<T, float>::value && std::is_same<A, float>::value) {
-    if (c->use_tc && c->tc_ready) {
+    if (c->use_tc && c->tc_ready && !t64) {
       int rc = r2_tc_launch(c, Ic, eb);
       if (rc) return rc;
       stage_end(c, ST_S3, e0);
@@ -438,8 +451,8 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
   cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
-      (const T*)c->tiles.p, (const T*)c->Y.p, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs, c->ld(),
-      c->tiled());
+      (const T*)tb.tiles, (const T*)tb.Y, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs, tb.ld,
+      tb.tiled);
   stage_end(c, ST_S3, e0);
   }
 s6:
@@ -500,9 +513,10 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
 }
 
 // Kirchhoff factor f = (1-eps) W_T eta_I / [Sigma (W_T,0,0,0)]_I (App. E).  In
-// FP32 mode the unnormalised Sigma is applied to the Planck field with FP64
-// accumulation over the operator's own FP32-stored tables, so that f corrects
-// the photon budget of exactly the matrix used at apply time.
+// FP32 mode the unnormalised Sigma is applied to the Planck field in FP64, with
+// the tables the refinement residuals use, so that f corrects the photon budget
+// of exactly the operator whose solution is returned (the FP32 apply that
+// drives the inner iterations differs from it only at FP32 rounding level).
 int compute_normalisation(Ctx* c) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
@@ -526,8 +540,10 @@ int compute_normalisation(Ctx* c) {
           (const double*)num.p, (const double*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
   } else {
     fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
-    rc = sigma_T<float, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p,
-                                (double*)Ic.p);
+    rc = c->has64 ? sigma_T<double, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p,
+                                            (double*)Mb.p, (double*)Ic.p, nullptr, true)
+                  : sigma_T<float, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p,
+                                           (double*)Ic.p);
     if (!rc)
       normalise_kernel<double, float><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
           (const double*)num.p, (const float*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
@@ -547,12 +563,14 @@ int apply_operator(Ctx* c, const void* x, void* y) {
 
 int rhs(Ctx* c, void* b) { return apply_lambda(c, c->epsth.p, b, nullptr, true); }
 
-// FP32 mode only: y = (Id - Lambda Sigma) x with FP64 vectors and FP64
-// accumulation over the FP32-stored operator (residuals of the refinement).
+// FP32 mode only: y = (Id - Lambda Sigma) x with FP64 vectors, FP64 arithmetic
+// and the FP64 copy of the Sigma tables when it was kept (else the FP32 tables):
+// the residuals of the refinement, which fix the accuracy of the solution.
 int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws /* 4 x nvec doubles */) {
   const size_t nv = nvec(c);
   double* eps = ws;
-  int rc = sigma_T<float, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv);
+  int rc = c->has64 ? sigma_T<double, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv, nullptr, true)
+                     : sigma_T<float, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv);
   if (rc) return rc;
   delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
       eps, (const float*)c->kt.p, (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu, 0, c->WT[0]);
@@ -659,8 +677,9 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
   planck_comoving_kernel<A><<<ceil_div(npt, 256), 256, 0, c->stream>>>((A*)Icw.p, (const double*)wtd.p, nz, nO, N);
   PRD_CUDA_TRY(c, cudaMemsetAsync(Jx.p, 0, Jx.bytes, c->stream));
   PRD_CUDA_TRY(c, cudaMemsetAsync(Jw.p, 0, Jw.bytes, c->stream));
-  launch_r3_J<T, A>(c, (const A*)Icx.p, (double*)Jx.p, nO);
-  launch_r3_J<T, A>(c, (const A*)Icw.p, (double*)Jw.p, nO);
+  const SigmaTables tb = sigma_tables(c, false);
+  launch_r3_J<T, A>(c, (const A*)Icx.p, (double*)Jx.p, nO, tb);
+  launch_r3_J<T, A>(c, (const A*)Icw.p, (double*)Jw.p, nO, tb);
   PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   const double mu1 = 1.0;
   for (int l = 0; l < nlos && !rc; ++l) {
@@ -676,8 +695,8 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       break;
     (void)mu1;
     // R_III parts initialise the comoving rows
-    launch_r3_out<T, A>(c, (const double*)Jx.p, (const T*)rout.p, (A*)es_bar.p, 1);
-    launch_r3_out<T, A>(c, (const double*)Jw.p, (const T*)rout.p, (A*)ew_bar.p, 1);
+    launch_r3_out<T, A>(c, (const double*)Jx.p, (const T*)rout.p, (A*)es_bar.p, 1, tb);
+    launch_r3_out<T, A>(c, (const double*)Jw.p, (const T*)rout.p, (A*)ew_bar.p, 1, tb);
     // R_II: tiles of every height for the LOS classes, then the contraction
     for (int iz = 0; iz < nz && !rc; ++iz) {
       std::vector<double> th(L.theta);

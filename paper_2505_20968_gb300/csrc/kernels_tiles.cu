@@ -412,10 +412,15 @@ int launch_tiles(Ctx* c) {
       group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)c->tiles.p + iz * ztile,
                                                             (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
                                                             c->tiled());
-    else
+    else {
       group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)c->tiles.p + iz * ztile,
                                                            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
                                                            c->tiled());
+      if (c->has64)
+        group_split_kernel<double><<<sb, 256, 0, c->stream>>>(
+            (const double*)scr.p, (double*)c->tiles64.p + (size_t)iz * c->ncls * c->ntile() * N * c->ld64(),
+            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld64(), 0);
+    }
     if (cudaPeekAtLastError() != cudaSuccess) err = 1;
   }
   cudaStreamSynchronize(c->stream);
@@ -430,6 +435,8 @@ int launch_tiles(Ctx* c) {
       r3_kernel<double, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(q, (double*)c->r3w.p, nz);
     else
       r3_kernel<float, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(q, (float*)c->r3w.p, nz);
+    if (c->prec != PRD_FP64 && c->has64)
+      r3_kernel<double, double><<<blocks, 32 * kRowsPerBlock, smem, c->stream>>>(q, (double*)c->r3w64.p, nz);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   dfree(du); dfree(dQ); dfree(da); dfree(dsh); dfree(dtr); dfree(dth); dfree(dath); dfree(daw);

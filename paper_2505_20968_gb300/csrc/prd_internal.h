@@ -89,6 +89,11 @@ struct Ctx {
   std::vector<double> aa_theta, aa_w;     // AA Theta rule
 
   // ---- device
+  // FP32 mode keeps an FP64 copy of the Sigma tables (plain tile layout) for the
+  // residuals of the mixed-precision refinement, when it fits (has64)
+  DBuf tiles64, Y64, r3w64, r3in64, r3out64, r3prof64, r3ab64;
+  bool has64 = false;
+  int ld64() const { return (2 * nnu + 3) / 4 * 4; }
   DBuf tiles;        // [z][c][t][n][2N]    (T)
   DBuf Y;            // [z][pair][t][16]    complex (T2)
   DBuf r3w;          // [z][q3][N] complex  (T2)  R_III incident weights

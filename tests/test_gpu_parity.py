@@ -6,9 +6,10 @@ here from the same seeds).
 
 FP64 mode (two-level slab): every stage within 1e-9 relative, the solution
 within 1e-8.  FP32 mode (two-term Mg II / H I physics on reduced grids, and
-sampled rows of the full Mg II workload): the emissivity within 2e-5 of its
-scale per height; after a solve with mixed-precision refinement the emergent
-I within 3e-5 relative and Q/I, U/I, V/I within 1e-4 absolute.
+sampled rows of the full Mg II workload): the emissivity within 4e-6 of its
+scale per height (1e-6 on the CUDA-core path); after a solve with
+mixed-precision refinement (residuals from the FP64 copy of the Sigma tables)
+the emergent I within 1e-5 relative and Q/I, U/I, V/I within 1e-4 absolute.
 """
 import os
 
@@ -98,13 +99,18 @@ def test_fp32_sigma_and_operator(name, tc):
 
 @pytest.mark.parametrize("name", ["mgii", "hi", "hi_aa"])
 def test_fp32_emergent_stokes_after_solve(name):
+    """FP32 mode at the accuracy target: emergent I within 1e-5 relative and
+    Q/I, U/I, V/I within 1e-4 absolute of the oracle's converged solution.
+    GMRES tol 1e-10 is the largest that meets it on the Mg II case (a sweep
+    measured 2e-4 at 1e-9 and 3e-6 at 1e-10: the small-epsilon scattering
+    problem amplifies the residual by ~1e5 into the top-layer intensity)."""
     cfg, P, G = get(name)
-    xg, info = P.solve(tol=1e-9, max_iter=400, restart=60)
+    xg, info = P.solve(tol=1e-10, max_iter=600, restart=60)
     top = P.mu > 0
     Ig = xg.cpu().numpy()[-1, top].astype(np.float64)
     Io = G["sol"][-1, top]
     d = np.max(np.abs(Ig[..., 0] - Io[..., 0]) / Io[..., 0])
-    assert d < 3e-5, f"I {d:.2e}"
+    assert d < 1e-5, f"I {d:.2e}"
     for s in (1, 2, 3):
         d = np.max(np.abs(Ig[..., s] / Ig[..., 0] - Io[..., s] / Io[..., 0]))
         assert d < 1e-4, f"Stokes {s} {d:.2e}"
@@ -160,7 +166,7 @@ def test_emergent_stokes_off_grid(name):
     los = G["los"]
     out = P.emergent_stokes(_t(G["sol"], P), los[:, 0], los[:, 1]).cpu().numpy().astype(np.float64)
     ref = G["emergent"]
-    tol = 1e-9 if P.prec == 0 else 2e-5
+    tol = 1e-9 if P.prec == 0 else 1e-5
     d = np.max(np.abs(out[..., 0] - ref[..., 0]) / ref[..., 0])
     assert d < tol, f"I {d:.2e}"
     for s in (1, 2, 3):
