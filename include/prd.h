@@ -140,6 +140,21 @@ int prd_apply_sigma(prd_ctx* ctx, const void* x_dev, void* eps_dev);
 int prd_apply_lambda(prd_ctx* ctx, const void* eps_dev, void* out_dev);
 /* y = (Id - Lambda Sigma) x  (one operator apply, Eq. linear_system). */
 int prd_apply_operator(prd_ctx* ctx, const void* x_dev, void* y_dev);
+/* y = (Id - Lambda Sigma)^T x = x - Sigma^T Lambda^T x: the transpose of the
+ * discrete operator of Eq. linear_system (adjoint of the linear system for
+ * gradients of functionals of I w.r.t. the atmosphere, Sect. 5 setting).  Each
+ * stage is transposed exactly (reverse DELO sweep, transposed splines, R_II
+ * tiles and R_III factors); arithmetic is FP64.  x, y: ctx-precision device
+ * vectors [z][Omega][nu][4], distinct.  In FP32 mode it uses the FP64 copy of
+ * the Sigma tables and returns PRD_E_STATE if that copy was not kept (too
+ * little device memory at setup).  Synchronises the ctx stream. */
+int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev);
+/* Adjoint solve (Id - Lambda Sigma)^T lam = g by restarted GMRES on
+ * prd_apply_operator_T, left-preconditioned with the forward preconditioner
+ * (a fixed linear map).  Arguments as prd_solve, with the right-hand side g
+ * given; lam starts from zero.  PRD_E_NOCONV if tol is not reached. */
+int prd_solve_adjoint(prd_ctx* ctx, const void* g_dev, double tol, int max_iter, int restart, void* lam_dev,
+                      int* iters, double* true_rel_res, double* res_history);
 /* x = P^-1 y, P = Id - Lambda* Sigma* on Stokes I (identity on Q,U,V):
  * Sigma* unpolarised, unmagnetised PRD-AA; m_in block-Jacobi-preconditioned
  * Richardson sweeps from zero (Sect. 5.2, App. F). */

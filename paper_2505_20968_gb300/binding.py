@@ -36,7 +36,8 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_workspace_bytes", "prd_rhs", "prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator",
            "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
-           "prd_device_status", "prd_contraction_work"]
+           "prd_device_status", "prd_contraction_work",
+           "prd_apply_operator_T", "prd_solve_adjoint"]
 
 
 def lib():
@@ -62,6 +63,8 @@ def lib():
         L.prd_directions.argtypes = [P, DP, DP, DP]
         L.prd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.prd_contraction_work.argtypes = [P, DP, DP]
+        L.prd_apply_operator_T.argtypes = [P, P, P]
+        L.prd_solve_adjoint.argtypes = [P, P, D, I, I, P, ctypes.POINTER(I), DP, DP]
         for f in ("prd_rhs",):
             getattr(L, f).argtypes = [P, P]
         for f in ("prd_apply_sigma", "prd_apply_lambda", "prd_apply_operator", "prd_apply_preconditioner",
@@ -128,6 +131,26 @@ class PRD:
                                          chi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         self.mu, self.chi, self.w = mu, chi, w
+
+    def apply_operator_T(self, x, out=None):
+        """y = (Id - Lambda Sigma)^T x (FP64 arithmetic)."""
+        self._stream()
+        out = self.empty() if out is None else out
+        self._check(lib().prd_apply_operator_T(self.h, self._vec(x), self._vec(out)))
+        return out
+
+    def solve_adjoint(self, g, tol=1e-8, max_iter=400, restart=60, out=None, check=True):
+        """lam with (Id - Lambda Sigma)^T lam = g."""
+        self._stream()
+        out = self.empty() if out is None else out
+        it = ctypes.c_int()
+        res = ctypes.c_double()
+        hist = np.zeros(max_iter + 2)
+        rc = lib().prd_solve_adjoint(self.h, self._vec(g), tol, max_iter, restart, self._vec(out), ctypes.byref(it),
+                                     ctypes.byref(res), hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if check:
+            self._check(rc)
+        return out, dict(iters=it.value, true_rel_res=res.value, rc=rc)
 
     def contraction_work(self):
         """(flops, bytes) of one R_II contraction (roofline accounting)."""

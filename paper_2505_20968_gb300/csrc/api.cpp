@@ -372,6 +372,31 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
   }
 }
 
+int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !y_dev) return fail(c, PRD_E_ARG, "NULL vector");
+  try {
+    return prd::apply_operator_t(c, x_dev, y_dev);
+  } catch (const std::exception& e) {
+    return fail(c, PRD_E_NOMEM, std::string("host exception: ") + e.what());
+  }
+}
+
+int prd_solve_adjoint(prd_ctx* ctx, const void* g_dev, double tol, int max_iter, int restart, void* lam_dev,
+                      int* iters, double* true_rel_res, double* res_history) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!g_dev || !lam_dev || !(tol > 0) || max_iter < 1 || restart < 1)
+    return fail(c, PRD_E_ARG, "bad adjoint solve arguments");
+  try {
+    return prd::solve_adjoint(c, g_dev, tol, max_iter, restart, lam_dev, iters, true_rel_res, res_history);
+  } catch (const std::exception& e) {
+    c->op_transpose = false;
+    return fail(c, PRD_E_NOMEM, std::string("host exception in adjoint solve: ") + e.what());
+  }
+}
+
 int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu, const double* chi,
                         void* out_dev) {
   CTX_OR_ARG(ctx);

@@ -93,6 +93,7 @@ struct Ctx {
   // residuals of the mixed-precision refinement, when it fits (has64)
   DBuf tiles64, Y64, r3w64, r3in64, r3out64, r3prof64, r3ab64;
   bool has64 = false;
+  bool op_transpose = false;   // GMRES iterates with A^T (adjoint solve)
   int ld64() const { return (2 * nnu + 3) / 4 * 4; }
   DBuf tiles;        // [z][c][t][n][2N]    (T)
   DBuf Y;            // [z][pair][t][16]    complex (T2)
@@ -185,6 +186,9 @@ int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised);
 int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool boundary);
 int apply_operator(Ctx* c, const void* x, void* y);
 int apply_precond(Ctx* c, const void* y, void* x);
+int apply_operator_t(Ctx* c, const void* x, void* y);   // y = A^T x (FP64 arithmetic)
+int solve_adjoint(Ctx* c, const void* g, double tol, int max_iter, int restart, void* lam, int* iters,
+                  double* true_res, double* hist);
 int compute_normalisation(Ctx* c);
 int rhs(Ctx* c, void* b);
 int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x, int* iters,

@@ -131,6 +131,12 @@ struct Vops {
 
 }  // namespace
 
+int apply_operator_t(Ctx* c, const void* x, void* y);
+// the operator GMRES iterates with: A, or A^T for the adjoint solve
+static int op_apply(Ctx* c, const void* x, void* y) {
+  return c->op_transpose ? apply_operator_t(c, x, y) : apply_operator(c, x, y);
+}
+
 // GMRES on A x = b in the ctx precision; x holds the initial guess on entry.
 // inner: correction solve of the mixed-precision refinement.  x is zero on
 // entry and the solve ends as soon as the Arnoldi estimate is below tol (the
@@ -167,7 +173,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
       PRD_CUDA_TRY(c, cudaMemcpyAsync(w.p, b.p, vb, cudaMemcpyDeviceToDevice, c->stream));
       tr = 1.0;
     } else {
-      if ((rc = apply_operator(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
+      if ((rc = op_apply(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
       double rn_true;
       if ((rc = ops.norm(w.p, &rn_true))) break;
       tr = rn_true / bnorm;
@@ -186,7 +192,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
     int j = 0;
     bool breakdown = false, est_ok = false;
     for (; j < m && it < max_iter; ++j) {
-      if ((rc = apply_operator(c, vec(j), w.p)) || (rc = apply_precond(c, w.p, r.p))) break;
+      if ((rc = op_apply(c, vec(j), w.p)) || (rc = apply_precond(c, w.p, r.p))) break;
       ++it;
       // CGS2
       if ((rc = ops.dot_many(V.p, n, j + 1, r.p, h.data())) || (rc = ops.axpy_many(V.p, n, h.data(), j + 1, r.p))) break;
@@ -230,7 +236,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
       break;
     }
     if (breakdown) {
-      if ((rc = apply_operator(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
+      if ((rc = op_apply(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
       double rn;
       if ((rc = ops.norm(w.p, &rn))) break;
       tr = rn / bnorm;
@@ -241,7 +247,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   }
   if (!rc && status == PRD_E_NOCONV && !inner) {
     // final true residual
-    if (!(rc = apply_operator(c, x, w.p)) && !(rc = ops.rsub(b.p, w.p))) {
+    if (!(rc = op_apply(c, x, w.p)) && !(rc = ops.rsub(b.p, w.p))) {
       double rn;
       if (!(rc = ops.norm(w.p, &rn))) {
         tr = rn / bnorm;
@@ -368,6 +374,18 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
   if (rc) return rc;
   if (status != PRD_OK) return fail(c, PRD_E_NOCONV, "refined GMRES reached max_iter before tol");
   return PRD_OK;
+}
+
+// Adjoint solve A^T lam = g (S13): GMRES in the ctx precision on the FP64
+// transposed operator, left-preconditioned with the forward P^-1 (any fixed
+// linear map keeps GMRES exact; it only changes the iteration count).
+int solve_adjoint(Ctx* c, const void* g, double tol, int max_iter, int restart, void* lam, int* iters,
+                  double* true_res, double* hist) {
+  PRD_CUDA_TRY(c, cudaMemsetAsync(lam, 0, nvec(c) * c->esz, c->stream));
+  c->op_transpose = true;
+  const int rc = gmres_core(c, g, lam, tol, max_iter, restart, iters, true_res, hist, 1.0, nullptr);
+  c->op_transpose = false;
+  return rc;
 }
 
 }  // namespace prd

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared():
     src = open(os.path.join(ROOT, "include", "prd.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(prd_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(prd_[A-Za-z_0-9]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():
