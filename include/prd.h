@@ -149,6 +149,18 @@ int prd_apply_operator(prd_ctx* ctx, const void* x_dev, void* y_dev);
  * the Sigma tables and returns PRD_E_STATE if that copy was not kept (too
  * little device memory at setup).  Synchronises the ctx stream. */
 int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev);
+/* Batched solve of n independent problems (ragged sizes allowed: one ctx per
+ * instance, each set up beforehand).  Instance i is solved as by prd_solve
+ * (x0 = 0, tolerance, iteration and restart limits shared) into x_devs[i], on
+ * its own host thread and its own ctx stream, so the instances overlap on the
+ * GPU when their streams differ.  iters, true_rel_res and rcs are arrays of n
+ * (rcs[i] = prd_solve's return code for instance i; any may be NULL).  Returns
+ * PRD_OK if every instance succeeded, else the first failing code.  The ctxs
+ * must be distinct and not used by other threads during the call.  The paper
+ * solves one atmosphere at a time; batching is the throughput form of its
+ * per-atmosphere solve (Sect. 5). */
+int prd_solve_batch(prd_ctx* const* ctxs, int n, double tol, int max_iter, int restart, void* const* x_devs,
+                    int* iters, double* true_rel_res, int* rcs);
 /* Adjoint solve (Id - Lambda Sigma)^T lam = g by restarted GMRES on
  * prd_apply_operator_T, left-preconditioned with the forward preconditioner
  * (a fixed linear map).  Arguments as prd_solve, with the right-hand side g

@@ -37,7 +37,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
            "prd_device_status", "prd_contraction_work",
-           "prd_apply_operator_T", "prd_solve_adjoint"]
+           "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch"]
 
 
 def lib():
@@ -64,6 +64,8 @@ def lib():
         L.prd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.prd_contraction_work.argtypes = [P, DP, DP]
         L.prd_apply_operator_T.argtypes = [P, P, P]
+        L.prd_solve_batch.argtypes = [ctypes.POINTER(P), I, D, I, I, ctypes.POINTER(P), ctypes.POINTER(I), DP,
+                                      ctypes.POINTER(I)]
         L.prd_solve_adjoint.argtypes = [P, P, D, I, I, P, ctypes.POINTER(I), DP, DP]
         for f in ("prd_rhs",):
             getattr(L, f).argtypes = [P, P]
@@ -263,3 +265,30 @@ class PRD:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(problems, tol=1e-6, max_iter=200, restart=30, check=True):
+    """Solve independent problems (PRD instances, ragged sizes allowed) with one
+    prd_solve_batch call: each instance on its own CUDA stream and host thread.
+    Returns the solutions and a list of per-instance info dicts."""
+    n = len(problems)
+    streams = [torch.cuda.Stream(device=P.device) for P in problems]
+    outs = []
+    for P, s in zip(problems, streams):
+        lib().prd_set_stream(P.h, ctypes.c_void_p(s.cuda_stream))
+        with torch.cuda.stream(s):
+            outs.append(P.empty())
+    for s in streams:
+        s.synchronize()
+    hs = (ctypes.c_void_p * n)(*[P.h for P in problems])
+    xs = (ctypes.c_void_p * n)(*[ctypes.c_void_p(o.data_ptr()) for o in outs])
+    it = (ctypes.c_int * n)()
+    res = (ctypes.c_double * n)()
+    rcs = (ctypes.c_int * n)()
+    rc = lib().prd_solve_batch(hs, n, tol, max_iter, restart, xs, it, res, rcs)
+    infos = [dict(iters=it[i], true_rel_res=res[i], rc=rcs[i]) for i in range(n)]
+    if check and rc != 0:
+        bad = [i for i in range(n) if rcs[i] != 0]
+        problems[bad[0]]._check(rcs[bad[0]])
+    return outs, infos
+

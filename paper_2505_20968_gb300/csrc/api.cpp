@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include "prd_internal.h"
 
 namespace prd {
@@ -370,6 +371,41 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
   } catch (const std::exception& e) {
     return fail(c, PRD_E_NOMEM, std::string("host exception in solve: ") + e.what());
   }
+}
+
+int prd_solve_batch(prd_ctx* const* ctxs, int n, double tol, int max_iter, int restart, void* const* x_devs,
+                    int* iters, double* true_rel_res, int* rcs) {
+  if (!ctxs || !x_devs || n < 1 || !(tol > 0) || max_iter < 1 || restart < 1) return PRD_E_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !x_devs[i]) return PRD_E_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return PRD_E_ARG;
+  }
+  std::vector<int> rc(n, PRD_OK), it(n, 0);
+  std::vector<double> res(n, 0.0);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      Ctx* c = &ctxs[i]->c;
+      if (!c->ready) { rc[i] = fail(c, PRD_E_STATE, "call prd_setup first"); return; }
+      if (cudaSetDevice(c->device) != cudaSuccess) { rc[i] = fail(c, PRD_E_CUDA, "cudaSetDevice failed"); return; }
+      try {
+        rc[i] = prd::solve(c, tol, max_iter, restart, nullptr, x_devs[i], &it[i], &res[i], nullptr);
+        if (!rc[i] && c->tc_err.p) rc[i] = prd::r2_tc_check_error(c);
+      } catch (const std::exception& e) {
+        rc[i] = fail(c, PRD_E_NOMEM, std::string("host exception in solve: ") + e.what());
+      }
+    });
+  for (auto& t : th) t.join();
+  int first = PRD_OK;
+  for (int i = 0; i < n; ++i) {
+    if (iters) iters[i] = it[i];
+    if (true_rel_res) true_rel_res[i] = res[i];
+    if (rcs) rcs[i] = rc[i];
+    if (first == PRD_OK && rc[i] != PRD_OK) first = rc[i];
+  }
+  return first;
 }
 
 int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev) {
