@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   if (gt == 0) {
     bool all = y_in_smem;
     for (int el = 0; el < E; ++el) all = all && pair_ptr[e0 + el + 1] - pair_ptr[e0 + el] <= 2;
-    // (so that a builder warp's 16 outputs have at most 32 pairs, one per lane)
+    // (so that an item.s 8 outputs have at most 16 pairs: one per half-warp lane)
     *fast_p = all ? 1 : 0;
   }
   if (warp == 0) {
@@ -305,14 +305,20 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   } else {
     // ---------------- B builders / A splitters, then epilogue
     const int bw = warp - 2;                       // builder warp
-    // B items: a warp takes 32 consecutive rows (output el = row / 4, Stokes i = row % 4)
-    // at one 4-k chunk kq, twice; the swizzle spreads each 8 lanes' stores over all banks
-    int it_row[2], it_kq[2], it_pa[2], it_pb[2];
+    // B items: (32-row group rg, 4-k chunk kq), item = bw + 8 r over the 4 nrg items
+    // of the chunk, so every builder warp has work whatever the chunk's width; a
+    // lane takes row rg*32 + lane (output el = row / 4, Stokes i = row % 4), and
+    // the swizzle spreads each 8 lanes' stores over all banks
+    const int nrg = (NCP + 31) / 32;
+    int it_row[2], it_kq[2], it_pa[2], it_pb[2], it_el0[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const int pr = bw * 2 + r;
-      it_row[r] = (pr & 3) * 32 + lane;
-      it_kq[r] = pr >> 2;
+      const int item = bw + 8 * r;
+      const bool vi = item < nrg * 4;
+      const int rg = vi ? item % nrg : 0;
+      it_row[r] = vi ? rg * 32 + lane : NCP;      // NCP: no item
+      it_kq[r] = vi ? item / nrg : 0;
+      it_el0[r] = rg * 8;
       const int el = it_row[r] >> 2;
       const bool v = it_row[r] < NCP && el < E;
       it_pa[r] = v ? eptr[el] : 0;
@@ -328,24 +334,29 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           ypre[r] = *((const float4*)(p.Y + ((ybase + (q >> 3)) * p.ntile + ti) * 32) + (q & 7));
       }
     };
-    // fast path: each lane keeps its items' Y rows for the tile in registers; the
-    // warp's 16 outputs have <= 32 pairs, lane l loads pair l's four I~ values of
-    // the warp's 4-k chunk one K step ahead and shares them through Wb
-    const int kqw = bw >> 1;                       // the warp's 4-k chunk (both items)
-    const int el0 = ((bw * 2) & 3) * 8;            // first output of the warp's 64 rows
-    const int pw0 = el0 < E ? eptr[el0] : 0;
-    const int npw = el0 < E ? eptr[min(el0 + 16, E)] - pw0 : 0;
+    // fast path: each lane keeps its items' Y rows for the tile in registers; an
+    // item's 8 outputs have <= 16 pairs: lane l loads, for item l / 16, pair
+    // l % 16's four I~ values of the item's 4-k chunk one K step ahead, and the
+    // warp shares them through its rows of Wb (item r at rows 16 r ..)
+    const int ri = lane >> 4, li = lane & 15;
+    const int kqw = it_kq[ri];
+    const int el0 = it_el0[ri];
+    const bool ivalid = it_row[ri] < NCP && el0 < E;
+    const int pw0 = ivalid ? eptr[el0] : 0;
+    const int npw = ivalid ? eptr[min(el0 + 8, E)] - pw0 : 0;
+    const int pw0r[2] = {it_row[0] < NCP && it_el0[0] < E ? eptr[it_el0[0]] : 0,
+                         it_row[1] < NCP && it_el0[1] < E ? eptr[it_el0[1]] : 0};
     float4* Ww = Wb + bw * (32 * kWStride);
     float4 yreg[2][2][2];
     float4 inext[4];
     const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
-    const int irow = (fast && lane < npw) ? pair_in[pp0 + pw0 + lane] * N : 0;
+    const int irow = (fast && li < npw) ? pair_in[pp0 + pw0 + li] * N : 0;
     auto load_i = [&](int it) {
       const int kb = (it % KCH) * kKC + kqw * 4;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int k = kb + q;
-        inext[q] = (lane < npw && k < 2 * N) ? Icz4[irow + (k < N ? k : k - N)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        inext[q] = (li < npw && k < 2 * N) ? Icz4[irow + (k < N ? k : k - N)] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
     if (fast) load_i(0);
@@ -428,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
               const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
-                const float4 iv = Ww[(it_pa[r] + pp - pw0) * kWStride + q];
+                const float4 iv = Ww[(r * 16 + it_pa[r] + pp - pw0r[r]) * kWStride + q];
                 const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
                 const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
                 z[q] += re[q] ? sr : -si;
