@@ -344,10 +344,16 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
   int it_total = 0, nh = 0, status = PRD_E_NOCONV;
   double res = 1.0;
   for (int outer = 0; outer < 12 && it_total < max_iter; ++outer) {
-    if ((rc = apply_operator_acc(c, (const double*)x64.p, (double*)r64.p, (double*)ws.p))) break;
-    sub_kernel<<<G, 256, 0, c->stream>>>((const double*)b64.p, (double*)r64.p, n);
     double rn;
-    if ((rc = dnorm(c, (const double*)r64.p, n, (double*)dsum.p, &rn))) break;
+    if (outer == 0 && !x0) {
+      // x = 0: the residual is b itself (no FP64 apply)
+      PRD_CUDA_TRY(c, cudaMemcpyAsync(r64.p, b64.p, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+      rn = bn;
+    } else {
+      if ((rc = apply_operator_acc(c, (const double*)x64.p, (double*)r64.p, (double*)ws.p))) break;
+      sub_kernel<<<G, 256, 0, c->stream>>>((const double*)b64.p, (double*)r64.p, n);
+      if ((rc = dnorm(c, (const double*)r64.p, n, (double*)dsum.p, &rn))) break;
+    }
     res = rn / bn;
     if (!std::isfinite(res)) { rc = fail(c, PRD_E_NAN, "residual is not finite"); break; }
     if (res < tol) { status = PRD_OK; break; }
