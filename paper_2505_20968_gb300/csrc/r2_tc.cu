@@ -374,6 +374,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) Ww[lane * kWStride + q] = inext[q];
         __syncwarp();
+        // the next K step's I~: issued now, consumed at the start of the next step
+        if (it + 1 < iters) load_i(it + 1);
       }
       if (kc == 0) {
         // a new tile: stage its Y, then all builders agree to go on (every builder
@@ -411,16 +413,21 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       {
         const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
-#pragma unroll 4
-        for (int q = gt; q < N * (kKC / 4); q += kGen) {
-          const float4 v = a4[q];
-          float4 l;
-          l.x = tf32_hi(v.x - tf32_trunc(v.x));
-          l.y = tf32_hi(v.y - tf32_trunc(v.y));
-          l.z = tf32_hi(v.z - tf32_trunc(v.z));
-          l.w = tf32_hi(v.w - tf32_trunc(v.w));
-          l4[q] = l;
-        }
+        const int nq4 = N * (kKC / 4);             // <= 4 kGen
+        float4 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (gt + r * kGen < nq4) v[r] = a4[gt + r * kGen];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (gt + r * kGen < nq4) {
+            float4 l;
+            l.x = tf32_hi(v[r].x - tf32_trunc(v[r].x));
+            l.y = tf32_hi(v[r].y - tf32_trunc(v[r].y));
+            l.z = tf32_hi(v[r].z - tf32_trunc(v[r].z));
+            l.w = tf32_hi(v[r].w - tf32_trunc(v[r].w));
+            l4[gt + r * kGen] = l;
+          }
       }
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -469,8 +476,6 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         *(float4*)(Bhi + swz64(row, kq * 4)) = hi;
         *(float4*)(Blo + swz64(row, kq * 4)) = lo;
       }
-      // the next K step's I~, consumed a whole step later
-      if (fast && it + 1 < iters) load_i(it + 1);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&ready[cb]);
     }
