@@ -309,6 +309,135 @@ __global__ void __launch_bounds__(256) r2_simt_kernel(const T* __restrict__ tile
   }
 }
 
+// ------------------------------------------------------------------ R_II, double-float
+// The same contraction for the FP64 refinement residuals, run on the FP32 pipes
+// (GB300's FP64 rate is 1/64 of its FP32 rate).  Every FP64 operand a is split
+// into a = hi + lo (two floats, |lo| <= 2^-24 |a|); a product of two operands
+// is hi*hi exactly (FMA error term) plus the hi*lo cross terms, and the sum is
+// kept as an unevaluated float pair (s, c) with the error-free two-sum of s
+// (Dekker / Knuth double-single arithmetic).  Dropped: lo*lo (2^-48 relative)
+// and the rounding of c; the result carries ~2^-44 relative error per term,
+// far below the 1e-10 residuals the refinement needs.
+struct F2 { float hi, lo; };
+__device__ __forceinline__ F2 split2(double a) {
+  const float h = (float)a;
+  return {h, (float)(a - (double)h)};
+}
+// (s, c) += x (x exact float); error-free two-sum of s and x into s, error into c
+__device__ __forceinline__ void dd_add(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  c += (s - (t - bb)) + (x - bb);
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) r2_dd_kernel(const double* __restrict__ tiles, const double* __restrict__ Y,
+                                                    const double* __restrict__ Ic, const int* __restrict__ cls,
+                                                    double* __restrict__ eb, int ncls, int ntrip, int nO, int N,
+                                                    int npairs, int ld) {
+  const int chunk = blockIdx.x, c = blockIdx.y, iz = blockIdx.z;
+  const int* cout_ptr = cls;
+  const int* cout_dir = cls + ncls + 1;
+  const int ne_tot = cout_ptr[ncls];
+  const int* pair_ptr = cout_dir + ne_tot;
+  const int* pair_in = pair_ptr + ne_tot + 1;
+  const int e0 = cout_ptr[c] + chunk * kCW;
+  const int e_end = cout_ptr[c + 1];
+  if (e0 >= e_end) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4 (*Zs)[kCW * 4] = reinterpret_cast<float4 (*)[kCW * 4]>(smraw);        // [mm][col]: zr hi/lo, zi hi/lo
+  float2* Asb = reinterpret_cast<float2*>(smraw + sizeof(float4) * kMB * kCW * 4);  // [(h N + n)(kMB+1) + mm]
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int e_mine = e0 + tx;
+  float accs[kMaxRows][4], accc[kMaxRows][4];
+#pragma unroll
+  for (int r = 0; r < kMaxRows; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { accs[r][i] = 0.f; accc[r][i] = 0.f; }
+  const int nrows = (N + 15) / 16;
+  const size_t tile_sz = (size_t)N * ld;
+  const double* tbase = tiles + ((size_t)iz * ncls + c) * ntrip * tile_sz;
+  const int ze = tid & 15, zm = tid >> 4;
+  const int e_z = e0 + ze;
+  for (int t = 0; t < ntrip; ++t) {
+    const double* tile = tbase + (size_t)t * tile_sz;
+    for (int m0 = 0; m0 < N; m0 += kMB) {
+      {
+        const int m = m0 + zm;
+        double zr[4] = {0, 0, 0, 0}, zi[4] = {0, 0, 0, 0};
+        if (e_z < e_end && m < N) {
+          for (int p = pair_ptr[e_z]; p < pair_ptr[e_z + 1]; ++p) {
+            const double* iv = Ic + (((size_t)iz * nO + pair_in[p]) * N + m) * 4;
+            const double* y = Y + (((size_t)iz * npairs + p) * ntrip + t) * 32;
+            const double i0 = iv[0], i1 = iv[1], i2 = iv[2], i3 = iv[3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const double* yi = y + i * 8;
+              zr[i] += yi[0] * i0 + yi[2] * i1 + yi[4] * i2 + yi[6] * i3;
+              zi[i] += yi[1] * i0 + yi[3] * i1 + yi[5] * i2 + yi[7] * i3;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const F2 a = split2(zr[i]), b = split2(zi[i]);
+          Zs[zm][ze * 4 + i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+      }
+      for (int idx = tid; idx < N * 2 * kMB; idx += 256) {
+        const int mm = idx % kMB;
+        const int h = (idx / kMB) & 1;
+        const int n = idx / (2 * kMB);
+        const int m = m0 + mm;
+        const F2 v = split2(m < N ? tile[(size_t)n * ld + h * N + m] : 0.0);
+        Asb[(h * N + n) * (kMB + 1) + mm] = make_float2(v.hi, v.lo);
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int mm = 0; mm < kMB; ++mm) {
+        float4 z[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[i] = Zs[mm][tx * 4 + i];
+#pragma unroll
+        for (int r = 0; r < kMaxRows; ++r) {
+          if (r < nrows) {
+            const int n = ty + 16 * r;
+            if (n < N) {
+              const float2 ar = Asb[n * (kMB + 1) + mm], ai = Asb[(N + n) * (kMB + 1) + mm];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                // ar * zr - ai * zi
+                const float p1 = ar.x * z[i].x;
+                const float q1 = fmaf(ar.x, z[i].x, -p1);
+                const float p2 = -ai.x * z[i].z;
+                const float q2 = fmaf(-ai.x, z[i].z, -p2);
+                const float lo = q1 + q2 + fmaf(ar.x, z[i].y, ar.y * z[i].x) - fmaf(ai.x, z[i].w, ai.y * z[i].z);
+                dd_add(accs[r][i], accc[r][i], p1);
+                dd_add(accs[r][i], accc[r][i], p2);
+                accc[r][i] += lo;
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (e_mine < e_end) {
+    const int o = cout_dir[e_mine];
+#pragma unroll
+    for (int r = 0; r < kMaxRows; ++r) {
+      const int n = ty + 16 * r;
+      if (r < nrows && n < N) {
+        double* dst = eb + (((size_t)iz * nO + o) * N + n) * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) atomicAdd(dst + i, (double)accs[r][i] + (double)accc[r][i]);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ DELO
 // One thread per ray (Omega, nu): I_k = (Id + b K'_k)^-1 [(e Id - a K'_{k-1}) I_{k-1}
 //   + a S_{k-1} + b S_k], S = eps/eta1, K' = K/eta1 - Id.  Optional: out = x - I.
@@ -443,6 +572,17 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
     if (c->use_tc && c->tc_ready && !t64) {
       int rc = r2_tc_launch(c, Ic, eb);
       if (rc) return rc;
+      stage_end(c, ST_S3, e0);
+      goto s6;
+    }
+  }
+  if constexpr (std::is_same<T, double>::value && std::is_same<A, double>::value) {
+    if (t64) {
+      const size_t smem = sizeof(float4) * (size_t)kMB * kCW * 4 + sizeof(float2) * (size_t)2 * N * (kMB + 1);
+      cudaFuncSetAttribute(r2_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      r2_dd_kernel<<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
+          (const double*)tb.tiles, (const double*)tb.Y, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N,
+          c->npairs, tb.ld);
       stage_end(c, ST_S3, e0);
       goto s6;
     }
