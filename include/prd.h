@@ -149,6 +149,17 @@ int prd_apply_operator(prd_ctx* ctx, const void* x_dev, void* y_dev);
  * the Sigma tables and returns PRD_E_STATE if that copy was not kept (too
  * little device memory at setup).  Synchronises the ctx stream. */
 int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev);
+/* Gradient of a functional J of the solution I with respect to the magnetic
+ * field of every height: dJ_dp[z*3 + 0..2] = dJ/dB_z [1/G], dJ/dtheta_B,z,
+ * dJ/dchi_B,z [1/rad].  x_dev: the solution of A I = b (ctx precision);
+ * dJdI_dev: dJ/dI at x (ctx precision, [z][Omega][nu][4]).  Adjoint method on
+ * Eq. linear_system: one adjoint solve A^T lam = dJ/dI (tol 1e-10), then
+ * dJ/dp = lam^T (db/dp - (dA/dp) I) with the parameter derivative taken as a
+ * central difference of b - A I, each side a full FP64 setup of the perturbed
+ * atmosphere (6 setups per height: meant for reduced problems).  Steps: 1e-3
+ * relative, 0.1 G for B = 0 (one-sided there), 1e-3 rad for angles at 0.  The
+ * paper solves forward problems only; it has no gradient.  Synchronises. */
+int prd_grad_B(prd_ctx* ctx, const void* x_dev, const void* dJdI_dev, double* dJ_dp);
 /* Batched solve of n independent problems (ragged sizes allowed: one ctx per
  * instance, each set up beforehand).  Instance i is solved as by prd_solve
  * (x0 = 0, tolerance, iteration and restart limits shared) into x_devs[i], on

@@ -37,7 +37,8 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_apply_preconditioner", "prd_set_precond_sweeps", "prd_solve", "prd_emergent_stokes",
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
            "prd_device_status", "prd_contraction_work",
-           "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch"]
+           "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch",
+           "prd_grad_B"]
 
 
 def lib():
@@ -64,6 +65,7 @@ def lib():
         L.prd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.prd_contraction_work.argtypes = [P, DP, DP]
         L.prd_apply_operator_T.argtypes = [P, P, P]
+        L.prd_grad_B.argtypes = [P, P, P, DP]
         L.prd_solve_batch.argtypes = [ctypes.POINTER(P), I, D, I, I, ctypes.POINTER(P), ctypes.POINTER(I), DP,
                                       ctypes.POINTER(I)]
         L.prd_solve_adjoint.argtypes = [P, P, D, I, I, P, ctypes.POINTER(I), DP, DP]
@@ -153,6 +155,14 @@ class PRD:
         if check:
             self._check(rc)
         return out, dict(iters=it.value, true_rel_res=res.value, rc=rc)
+
+    def grad_B(self, x, dJdI):
+        """dJ/d(B, theta_B, chi_B) per height, shape (nz, 3), by the adjoint method."""
+        self._stream()
+        g = np.zeros((self.nz, 3))
+        self._check(lib().prd_grad_B(self.h, self._vec(x), self._vec(dJdI),
+                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return g
 
     def contraction_work(self):
         """(flops, bytes) of one R_II contraction (roofline accounting)."""

@@ -373,6 +373,18 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
   }
 }
 
+int prd_grad_B(prd_ctx* ctx, const void* x_dev, const void* dJdI_dev, double* dJ_dp) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !dJdI_dev || !dJ_dp) return fail(c, PRD_E_ARG, "NULL argument");
+  try {
+    return prd::grad_b(c, x_dev, dJdI_dev, 1e-10, dJ_dp);
+  } catch (const std::exception& e) {
+    c->op_transpose = false;
+    return fail(c, PRD_E_NOMEM, std::string("host exception in gradient: ") + e.what());
+  }
+}
+
 int prd_solve_batch(prd_ctx* const* ctxs, int n, double tol, int max_iter, int restart, void* const* x_devs,
                     int* iters, double* true_rel_res, int* rcs) {
   if (!ctxs || !x_devs || n < 1 || !(tol > 0) || max_iter < 1 || restart < 1) return PRD_E_ARG;

@@ -189,6 +189,7 @@ int apply_precond(Ctx* c, const void* y, void* x);
 int apply_operator_t(Ctx* c, const void* x, void* y);   // y = A^T x (FP64 arithmetic)
 int solve_adjoint(Ctx* c, const void* g, double tol, int max_iter, int restart, void* lam, int* iters,
                   double* true_res, double* hist);
+int grad_b(Ctx* c, const void* x, const void* dJdI, double tol, double* dJdp);
 int compute_normalisation(Ctx* c);
 int rhs(Ctx* c, void* b);
 int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x, int* iters,

@@ -80,3 +80,38 @@ def test_adjoint_solve_fp64(name, tol):
     lhs, rhs = _dot(g, x), _dot(lam, b)
     assert abs(lhs - rhs) < 1e3 * tol * abs(lhs), (lhs, rhs, ainfo["iters"])
     P.close()
+
+
+def test_grad_B_matches_finite_differences_of_J():
+    """dJ/d(B, theta_B) from prd_grad_B (one adjoint solve) against central
+    differences of J over two forward solves, for J = sum of the emergent
+    intensities of the top layer (linear in I) on a small two-term case."""
+    from paper_2505_20968_gb300.binding import PRD
+    mk = lambda: inputs.mgii(n_z=6, n_core_each=5, n_wing=4, n_mu_half=1, n_chi=4, seed=23)
+    cfg = mk()
+    P = PRD(cfg, precision="fp64", device=0)
+    x, _ = P.solve(tol=1e-12, max_iter=600, restart=80)
+    top = P.mu > 0
+    dJdI = torch.zeros_like(x)
+    dJdI[-1, torch.from_numpy(top).to(x.device), :, 0] = 1.0
+    g = P.grad_B(x, dJdI)
+    assert np.all(np.isfinite(g))
+
+    def J_of(atm_key, iz, val):
+        c = mk()
+        c["atm"][atm_key] = np.array(c["atm"][atm_key], dtype=np.float64)
+        c["atm"][atm_key][iz] = val
+        Q = PRD(c, precision="fp64", device=0)
+        xq, _ = Q.solve(tol=1e-12, max_iter=600, restart=80)
+        v = float(xq[-1, torch.from_numpy(top).to(xq.device), :, 0].sum().item())
+        Q.close()
+        return v
+
+    for key, k, iz in (("B_G", 0, 2), ("thetaB", 1, 4)):
+        p0 = float(cfg["atm"][key][iz])
+        h = max(1e-3 * abs(p0), 0.1 if k == 0 else 1e-3)
+        lo = p0 if (k == 0 and p0 - h < 0) else p0 - h
+        fd = (J_of(key, iz, p0 + h) - J_of(key, iz, lo)) / (p0 + h - lo)
+        scale = float(x[-1, torch.from_numpy(top).to(x.device), :, 0].sum().item())
+        assert abs(g[iz, k] - fd) < 1e-4 * abs(fd) + 1e-9 * scale, (key, iz, g[iz, k], fd)
+    P.close()
