@@ -39,7 +39,7 @@ constexpr int kCBufs = 2;                     // builder ring: A_lo, B_hi, B_lo
 constexpr int kKC = 16;                       // fp32 per stage along K (64-byte rows)
 constexpr int kMaxE = 32;                     // output directions per CTA
 constexpr int kNCPMax = 4 * kMaxE;            // MMA N (Stokes columns)
-constexpr int kABytes = 2 * 128 * kKC * 4;    // two M blocks
+constexpr int kABytes = 256 * kKC * 4;        // one K step of up to 256 tile rows
 constexpr int kBBytes = kNCPMax * kKC * 4;
 constexpr int kCBytes = kABytes + 2 * kBBytes;
 constexpr int kGen = 256;                     // builder threads (warps 2-9)
