@@ -7,7 +7,7 @@ their inputs from paper_2505_20968_gb300.inputs, which holds no arithmetic of
 the method.
 
 The oracle computes, plainly and slowly, the discrete operator the library
-implements (readings of the paper listed in the design doc):
+implements, module by module:
   * faddeeva      W(a,v) = w(v + i a)                 (Sect. 2.3)
   * spline        natural cubic spline, constant extension (Sect. 6.2)
   * geometry      angular grid, scattering angles, polarisation basis (Sect. 4.2)
