@@ -12,13 +12,14 @@
 // columns, N = all tile rows n (<= 256, padded to 16), so one MMA per K
 // slice covers a whole tile step without padding n to a second M block.
 //
-// Roles (320 threads): warp 0 streams the tile into a 7-stage ring with one
+// Roles (320 threads): warp 0 streams the tile into a 5-stage ring with one
 // bulk asynchronous copy per K step (the FP32 tiles are stored pre-swizzled, K
-// step by K step, so a step is one contiguous N x 64-byte block) and owns the
-// TMEM allocation; warp 1 issues tcgen05.mma; warps 2-9 build B in shared
-// memory from Y (staged per tile, prefetched into registers a tile ahead) and
-// I~ (each lane loads the values its warp needs one K step ahead and shares
-// them through a per-warp buffer), split both operands into TF32 hi/lo parts
+// step by K step, so a step is one contiguous N x 64-byte block), stages the
+// step's I~ of every incident direction of the CTA beside it (its 32 lanes
+// load and store; the ring depth hides the load latency) and owns the TMEM
+// allocation; warp 1 issues tcgen05.mma; warps 2-9 build B in shared memory
+// from Y (staged per tile, prefetched into registers a tile ahead) and the
+// staged I~, split both operands into TF32 hi/lo parts
 // (3 products: hi*hi + hi*lo + lo*hi, FP32-level accuracy) in a 2-buffer ring
 // of their own, and run the epilogue from TMEM.  The tile ring is deeper than
 // the builder ring so that enough tile bytes are in flight per SM to cover
@@ -34,7 +35,7 @@ namespace prd {
 
 namespace tc {
 
-constexpr int kStages = 7;                    // tile ring
+constexpr int kStages = 5;                    // tile + I~ ring
 constexpr int kCBufs = 2;                     // builder ring: A_lo, B_hi, B_lo
 constexpr int kKC = 16;                       // fp32 per stage along K (64-byte rows)
 constexpr int kMaxE = 32;                     // output directions per CTA
@@ -46,11 +47,13 @@ constexpr int kGen = 256;                     // builder threads (warps 2-9)
 constexpr int kThreads = 64 + kGen;
 constexpr int kYPairs = 64;                   // pairs whose Y is staged in shared memory
 constexpr int kYBytes = kYPairs * 32 * 4;     // one tile's Y (two buffers)
-constexpr int kAuxBytes = (kMaxE + 2) * 4 + 256;
-// per builder warp: the next K step's I~ for its (<= 32) pairs, 5-float4 rows (conflict-free reads)
-constexpr int kWStride = 5;
-constexpr int kWBytes = (kGen / 32) * 32 * kWStride * 16;
-constexpr int kSmemBytes = kStages * kABytes + kCBufs * kCBytes + 2 * kYBytes + kWBytes + kAuxBytes + 1024;
+constexpr int kISlots = 32;                   // incident directions staged per K step
+// I~ of one K step: slot sl, column kl at float4 sl * kIStride + kl; the odd stride
+// puts the slots of a warp's 8 outputs in 8 distinct bank groups
+constexpr int kIStride = kKC + 1;
+constexpr int kIBytes = kISlots * kIStride * 16;
+constexpr int kAuxBytes = (kMaxE + 3 + kYPairs + kISlots) * 4 + 256;
+constexpr int kSmemBytes = kStages * (kABytes + kIBytes) + kCBufs * kCBytes + 2 * kYBytes + kAuxBytes + 1024;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 static_assert(kYPairs * 8 <= 2 * kGen, "Y prefetch registers");
 static_assert(kNCPMax == 128 && kGen == 256, "B items: 8 builder warps x 2 (32-row group, 4-k chunk)");
@@ -177,10 +180,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   unsigned char* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char* cbuf = sm + kStages * kABytes;                    // [buffer] A_lo, B_hi, B_lo
   float* Ys = (float*)(cbuf + kCBufs * kCBytes);                   // [buffer][pair][16][2]
-  float4* Wb = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [builder warp][pair][kWStride]
-  int* eptr = (int*)((unsigned char*)Wb + kWBytes);                // local pair range of each output
-  int* fast_p = eptr + kMaxE + 1;                                  // fast-path flag
-  uint64_t* full = (uint64_t*)(((uintptr_t)(fast_p + 1) + 7) & ~(uintptr_t)7);
+  float4* Is = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [stage][slot][kIStride]
+  int* eptr = (int*)((unsigned char*)Is + kStages * kIBytes);      // local pair range of each output
+  int* fast_p = eptr + kMaxE + 1;                                  // fast-path flag, staged slots
+  int* pslot = fast_p + 2;                                         // slot of each local pair
+  int* slot_dir = pslot + kYPairs;                                 // direction held in each slot
+  uint64_t* full = (uint64_t*)(((uintptr_t)(slot_dir + kISlots) + 7) & ~(uintptr_t)7);
   uint64_t* empty = full + kStages;
   uint64_t* ready = empty + kStages;
   uint64_t* cfree = ready + kCBufs;
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
+      mbar_init(&full[s], 1 + 32);   // tile copy armed by lane 0, I~ staged by the 32 producer lanes
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < kCBufs; ++b) {
@@ -220,12 +225,23 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (gt >= 0 && gt <= E) eptr[gt] = pair_ptr[e0 + gt] - pp0;
-  // the fast path needs every pair's Y staged and at most two pairs per output
+  // incident directions of this CTA's pairs -> I~ slots (first kISlots distinct); the
+  // fast path needs every pair's Y and I~ staged and at most two pairs per output
   if (gt == 0) {
+    int ns = 0;
     bool all = y_in_smem;
     for (int el = 0; el < E; ++el) all = all && pair_ptr[e0 + el + 1] - pair_ptr[e0 + el] <= 2;
-    // (so that an item.s 8 outputs have at most 16 pairs: one per half-warp lane)
-    *fast_p = all ? 1 : 0;
+    for (int pl = 0; pl < npl && pl < kYPairs; ++pl) {
+      const int op = pair_in[pp0 + pl];
+      int sidx = -1;
+      for (int s2 = 0; s2 < ns; ++s2)
+        if (slot_dir[s2] == op) { sidx = s2; break; }
+      if (sidx < 0 && ns < kISlots) { slot_dir[ns] = op; sidx = ns++; }
+      pslot[pl] = sidx;
+      all = all && sidx >= 0;
+    }
+    fast_p[0] = all ? 1 : 0;
+    fast_p[1] = ns;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -236,20 +252,27 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const bool fast = *fast_p != 0;
+  const bool fast = fast_p[0] != 0;
+  const int ns = fast_p[1];
   const long long slab0 = ((long long)iz * p.ncls + c) * p.ntile;
   const int NM = (N + 15) / 16 * 16;             // MMA N: the tile rows n (<= 256)
   const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
 
   if (warp == 0) {
-    // ---------------- producer: one bulk copy per tile K step (lane 0)
+    // ---------------- producer warp: lane 0 waits for a free stage and copies the tile
+    // K step (one bulk copy); all 32 lanes stage the step's I~ of every slot (loads
+    // issued together, latency hidden by the ring) and arrive on the stage barrier
     int it = 0;
-    if (lane == 0) {
-      const uint64_t pol_t = policy_evict_first();
-      for (; it < iters; ++it) {
-        const int s = it % kStages;
-        if (it >= kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1, abort_flag)) break;
-        const int ti = it / KCH, kc = it - ti * KCH;
+    const uint64_t pol_t = policy_evict_first();
+    const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
+    for (; it < iters; ++it) {
+      const int s = it % kStages;
+      int ok = 1;
+      if (lane == 0 && it >= kStages) ok = mbar_wait(&empty[s], ((it / kStages) - 1) & 1, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      const int ti = it / KCH, kc = it - ti * KCH;
+      if (lane == 0) {
         const uint32_t abytes = (uint32_t)N * kKC * 4;
         // rows n >= N of the stage keep stale data: they only reach output rows
         // that the epilogue never reads
@@ -257,6 +280,22 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         mbar_expect_tx(&full[s], abytes);
         bulk_load(sm + s * kABytes, src, abytes, &full[s], pol_t);
       }
+      float4* Isb = Is + (size_t)s * (kISlots * kIStride);
+      float4 v[kISlots * kKC / 32];
+#pragma unroll
+      for (int r = 0; r < kISlots * kKC / 32; ++r) {
+        const int q = lane + 32 * r;
+        const int sl = q / kKC, k = kc * kKC + (q - sl * kKC);
+        v[r] = (q < ns * kKC && k < 2 * N) ? Icz4[(size_t)slot_dir[sl] * N + (k < N ? k : k - N)]
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int r = 0; r < kISlots * kKC / 32; ++r) {
+        const int q = lane + 32 * r;
+        const int sl = q / kKC;
+        if (q < ns * kKC) Isb[sl * kIStride + (q - sl * kKC)] = v[r];
+      }
+      mbar_arrive(&full[s]);
     }
     if (lane == 0 && *abort_flag) {
       // drain copies that were issued and may not have been consumed
@@ -310,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     // lane takes row rg*32 + lane (output el = row / 4, Stokes i = row % 4), and
     // the swizzle spreads each 8 lanes' stores over all banks
     const int nrg = (NCP + 31) / 32;
-    int it_row[2], it_kq[2], it_pa[2], it_pb[2], it_el0[2];
+    int it_row[2], it_kq[2], it_pa[2], it_pb[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int item = bw + 8 * r;
@@ -318,7 +357,6 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       const int rg = vi ? item % nrg : 0;
       it_row[r] = vi ? rg * 32 + lane : NCP;      // NCP: no item
       it_kq[r] = vi ? item / nrg : 0;
-      it_el0[r] = rg * 8;
       const int el = it_row[r] >> 2;
       const bool v = it_row[r] < NCP && el < E;
       it_pa[r] = v ? eptr[el] : 0;
@@ -334,32 +372,10 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           ypre[r] = *((const float4*)(p.Y + ((ybase + (q >> 3)) * p.ntile + ti) * 32) + (q & 7));
       }
     };
-    // fast path: each lane keeps its items' Y rows for the tile in registers; an
-    // item's 8 outputs have <= 16 pairs: lane l loads, for item l / 16, pair
-    // l % 16's four I~ values of the item's 4-k chunk one K step ahead, and the
-    // warp shares them through its rows of Wb (item r at rows 16 r ..)
-    const int ri = lane >> 4, li = lane & 15;
-    const int kqw = it_kq[ri];
-    const int el0 = it_el0[ri];
-    const bool ivalid = it_row[ri] < NCP && el0 < E;
-    const int pw0 = ivalid ? eptr[el0] : 0;
-    const int npw = ivalid ? eptr[min(el0 + 8, E)] - pw0 : 0;
-    const int pw0r[2] = {it_row[0] < NCP && it_el0[0] < E ? eptr[it_el0[0]] : 0,
-                         it_row[1] < NCP && it_el0[1] < E ? eptr[it_el0[1]] : 0};
-    float4* Ww = Wb + bw * (32 * kWStride);
+    // fast path: each lane keeps its items' Y rows and I~ slot offsets for the tile
+    // in registers; the I~ of every K step is staged in shared memory by the producer
     float4 yreg[2][2][2];
-    float4 inext[4];
-    const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
-    const int irow = (fast && li < npw) ? pair_in[pp0 + pw0 + li] * N : 0;
-    auto load_i = [&](int it) {
-      const int kb = (it % KCH) * kKC + kqw * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = kb + q;
-        inext[q] = (li < npw && k < 2 * N) ? Icz4[irow + (k < N ? k : k - N)] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    };
-    if (fast) load_i(0);
+    int soff[2][2];
     load_y(0);
     bool aborted = false;
     for (int it = 0; it < iters; ++it) {
@@ -368,15 +384,6 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       bool got = !aborted && mbar_wait(&full[s], (it / kStages) & 1, abort_flag);
       if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag);
       float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
-      if (fast) {
-        // this step's I~ into the warp's buffer (the warp is done with the last one)
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Ww[lane * kWStride + q] = inext[q];
-        __syncwarp();
-        // the next K step's I~: issued now, consumed at the start of the next step
-        if (it + 1 < iters) load_i(it + 1);
-      }
       if (kc == 0) {
         // a new tile: stage its Y, then all builders agree to go on (every builder
         // reaches this barrier, aborted or not, so none waits for one that left)
@@ -396,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
                 const float4* y4 = reinterpret_cast<const float4*>(Ysb) + (it_pa[r] + pp) * 8 + i * 2;
                 yreg[r][pp][0] = y4[0];
                 yreg[r][pp][1] = y4[1];
+                soff[r][pp] = pslot[it_pa[r] + pp] * kIStride + it_kq[r] * 4;
               }
             }
           }
@@ -410,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       unsigned char* Alo = cbuf + cb * kCBytes;
       unsigned char* Bhi = Alo + kABytes;
       unsigned char* Blo = Bhi + kBBytes;
+      const float4* Isb = Is + (size_t)s * (kISlots * kIStride);
       {
         const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
@@ -446,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
               const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
-                const float4 iv = Ww[(r * 16 + it_pa[r] + pp - pw0r[r]) * kWStride + q];
+                const float4 iv = Isb[soff[r][pp] + q];
                 const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
                 const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
                 z[q] += re[q] ? sr : -si;
@@ -457,12 +466,13 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           for (int pl = it_pa[r]; pl < it_pb[r]; ++pl) {
             const float* y = y_in_smem ? Ysb + pl * 32 : p.Y + ((ybase + pl) * p.ntile + ti) * 32;
             const float4 ya = *(const float4*)(y + i * 8), yb = *(const float4*)(y + i * 8 + 4);
+            const int sl = (pl < kYPairs) ? pslot[pl] : -1;
             const float4* ir = reinterpret_cast<const float4*>(Icz) + (size_t)pair_in[pp0 + pl] * N;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int k = kb + q;
               if (k >= 2 * N) continue;
-              const float4 iv = ir[k < N ? k : k - N];
+              const float4 iv = sl >= 0 ? Isb[sl * kIStride + kq * 4 + q] : ir[k < N ? k : k - N];
               if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
               else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
             }
