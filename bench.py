@@ -242,7 +242,7 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("kernel") == "r2_tc_kernel" and tr.get("workload") == "mgii" and tr.get("layout") == "bulk-v2":
+        if tr.get("kernel") == "r2_tc_kernel" and tr.get("workload") == "mgii" and tr.get("layout") == "bulk-v3":
             traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
