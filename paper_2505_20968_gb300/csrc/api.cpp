@@ -295,7 +295,9 @@ int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
   const prd::DBuf* bufs[] = {&c->tiles, &c->Y, &c->r3w, &c->r3in, &c->r3out, &c->r3prof, &c->r3J, &c->r3ab,
                              &c->kt, &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk,
                              &c->cls_dev, &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M,
-                             &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t};
+                             &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t, &c->dmu, &c->pc_s1, &c->pc_s2,
+                             &c->pc_s3, &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64,
+                             &c->r3out64, &c->r3prof64, &c->r3ab64};
   int64_t s = 0;
   for (auto* b : bufs) s += (int64_t)b->bytes;
   *bytes = s;
