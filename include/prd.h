@@ -79,6 +79,19 @@ int prd_destroy(prd_ctx* ctx);
 const char* prd_last_error(const prd_ctx* ctx);
 /* Issue all further work on this cudaStream_t (passed as a pointer). */
 int prd_set_stream(prd_ctx* ctx, void* cuda_stream);
+/* Device memory of the library from the caller's allocator (e.g. a caching
+ * allocator of the host framework) instead of cudaMalloc/cudaFree.
+ * alloc(bytes, user, stream) returns a device pointer of at least `bytes`
+ * bytes on the ctx device, 256-byte aligned, usable on `stream` (the ctx
+ * stream at the time of the call), or NULL on failure (-> PRD_E_NOMEM);
+ * free(ptr, user) releases it.  Both NULL: back to cudaMalloc/cudaFree.  Every
+ * buffer is released with the deallocator it was obtained from, so the call
+ * can come at any time; set it before prd_setup to route the workspace
+ * (tiles and tables) through it.  prd_apply_sigma_noalloc allocates nothing
+ * either way. */
+typedef void* (*prd_alloc_fn)(size_t bytes, void* user, void* stream);
+typedef void (*prd_free_fn)(void* ptr, void* user);
+int prd_set_allocator(prd_ctx* ctx, prd_alloc_fn alloc, prd_free_fn free_fn, void* user);
 
 /* Sect. 2.2 / Table 1. */
 int prd_set_atom(prd_ctx* ctx, const prd_atom* atom);

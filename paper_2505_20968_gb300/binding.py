@@ -38,7 +38,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
            "prd_device_status", "prd_contraction_work",
            "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch",
-           "prd_grad_B"]
+           "prd_grad_B", "prd_set_allocator"]
 
 
 def lib():
@@ -55,6 +55,7 @@ def lib():
         L.prd_last_error.argtypes = [P]
         L.prd_last_error.restype = ctypes.c_char_p
         L.prd_set_stream.argtypes = [P, P]
+        L.prd_set_allocator.argtypes = [P, _ALLOC_FN, _FREE_FN, P]
         L.prd_set_atom.argtypes = [P, ctypes.POINTER(_Atom)]
         L.prd_set_atmosphere.argtypes = [P, I] + [DP] * 12
         L.prd_set_quadrature.argtypes = [P, I, DP, I, I, I, I, I]
@@ -90,10 +91,35 @@ def _dp(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-class PRD:
-    """One library context: a configured problem resident on one GPU."""
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
-    def __init__(self, cfg, precision=None, device=0, mode=None, setup=True):
+
+def _torch_allocator(device, stats):
+    """prd_set_allocator callbacks backed by PyTorch's caching allocator;
+    stats counts the bytes handed out and the pointers still live."""
+    def alloc(nbytes, user, stream):
+        try:
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=int(stream or 0))
+        except Exception:   # out of memory: the library reports PRD_E_NOMEM
+            return None
+        stats["bytes"] += int(nbytes)
+        stats["live"][p] = int(nbytes)
+        return p
+
+    def free(ptr, user):
+        stats["live"].pop(int(ptr), None)
+        torch.cuda.caching_allocator_delete(int(ptr))
+    return _ALLOC_FN(alloc), _FREE_FN(free)
+
+
+class PRD:
+    """One library context: a configured problem resident on one GPU.
+
+    allocator="torch" routes the library's device memory through PyTorch's
+    caching allocator (prd_set_allocator) instead of cudaMalloc."""
+
+    def __init__(self, cfg, precision=None, device=0, mode=None, setup=True, allocator=None):
         L = lib()
         prec = cfg.get("precision", "fp32") if precision is None else precision
         self.prec = PRD_FP64 if prec in ("fp64", PRD_FP64) else PRD_FP32
@@ -114,6 +140,14 @@ class PRD:
         g, gp = _dp(q["grid"])
         self._check(L.prd_set_quadrature(self.h, len(g), gp, q["grid_kind"], q["n_mu_half"], q["n_chi"],
                                          q.get("mu_rule", 0), q.get("mode", 0) if mode is None else mode))
+        self._alloc = None
+        self.alloc_stats = {"bytes": 0, "live": {}}
+        if allocator == "torch":
+            self._alloc = _torch_allocator(device, self.alloc_stats)   # kept alive as long as the ctx
+            self._stream()
+            self._check(L.prd_set_allocator(self.h, self._alloc[0], self._alloc[1], None))
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
         if setup:
             self.setup()
 

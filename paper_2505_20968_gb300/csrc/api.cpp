@@ -17,20 +17,35 @@ int fail(Ctx* c, int code, const std::string& msg) {
 int dalloc(Ctx* c, DBuf& b, size_t bytes) {
   dfree(b);
   if (bytes == 0) bytes = 16;
+  if (c->alloc_fn) {
+    b.p = c->alloc_fn(bytes, c->alloc_user, (void*)c->stream);
+    if (!b.p) return fail(c, PRD_E_NOMEM, "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    b.fr = c->free_fn;
+    b.user = c->alloc_user;
+    b.bytes = bytes;
+    return PRD_OK;
+  }
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     b.p = nullptr;
     cudaGetLastError();
     return fail(c, PRD_E_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
   }
+  b.fr = nullptr;
+  b.user = nullptr;
   b.bytes = bytes;
   return PRD_OK;
 }
 
 void dfree(DBuf& b) {
-  if (b.p) cudaFree(b.p);
+  if (b.p) {
+    if (b.fr) b.fr(b.p, b.user);
+    else cudaFree(b.p);
+  }
   b.p = nullptr;
   b.bytes = 0;
+  b.fr = nullptr;
+  b.user = nullptr;
 }
 
 int upload(Ctx* c, DBuf& b, const void* host, size_t bytes) {
@@ -52,7 +67,7 @@ static void free_all(Ctx* c) {
   for (DBuf* b : bufs) dfree(*b);
   for (auto& b : c->krylov) dfree(b);
   c->krylov.clear();
-  for (void* p : c->owned) cudaFree(p);
+  for (auto& b : c->owned) dfree(b);
   c->owned.clear();
 }
 
@@ -180,6 +195,15 @@ const char* prd_last_error(const prd_ctx* ctx) { return ctx ? ctx->c.err.c_str()
 int prd_set_stream(prd_ctx* ctx, void* stream) {
   CTX_OR_ARG(ctx);
   c->stream = (cudaStream_t)stream;
+  return PRD_OK;
+}
+
+int prd_set_allocator(prd_ctx* ctx, prd_alloc_fn alloc, prd_free_fn free_fn, void* user) {
+  CTX_OR_ARG(ctx);
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(c, PRD_E_ARG, "give both alloc and free, or neither");
+  c->alloc_fn = alloc;
+  c->free_fn = free_fn;
+  c->alloc_user = user;
   return PRD_OK;
 }
 

@@ -29,6 +29,8 @@ constexpr int kWeidemanN32 = 20;   // Faddeeva expansion terms, FP32 paths
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  prd_free_fn fr = nullptr;     // caller's deallocator (NULL: cudaFree)
+  void* user = nullptr;
 };
 
 struct Ctx {
@@ -125,7 +127,10 @@ struct Ctx {
   // GMRES
   std::vector<DBuf> krylov;
   DBuf gm_w, gm_r, gm_t, gm_dots;
-  std::vector<void*> owned;
+  std::vector<DBuf> owned;
+  prd_alloc_fn alloc_fn = nullptr;   // caller's allocator (prd_set_allocator), NULL: cudaMalloc
+  prd_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
   // tensor-core contraction (r2_tc.cu)
   DBuf tc_err;
   DBuf tc_work;      // tcgen05 contraction work items: (class, first output entry) pairs

@@ -200,7 +200,7 @@ int launch_precond_setup(Ctx* c) {
   if ((rc = up(c->pc_phi, phi)) || (rc = up(c->pc_M, Mm))) return rc;
   DBuf w;
   if ((rc = upload(c, w, c->wang.data(), nO * 8))) return rc;
-  c->owned.push_back(w.p);   // angular weights (double), freed with the ctx
+  c->owned.push_back(w);     // angular weights (double), freed with the ctx
   c->pc_w = w.p;
   const size_t vb = nvec(c) * c->esz;
   if ((rc = dalloc(c, c->pc_s1, vb)) || (rc = dalloc(c, c->pc_s2, vb)) || (rc = dalloc(c, c->pc_s3, vb)) ||
