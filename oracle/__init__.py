@@ -17,4 +17,6 @@ implements, module by module:
   * problem       K, eps_th, DELO-linear Lambda, Sigma, Kirchhoff
                   normalisation, GMRES, emergent Stokes (Sects. 2.6, 3, 4, 5;
                   App. B, E, F)
+                  and the transposed operator A^T = Id - Sigma^T Lambda^T
+                  with its GMRES solve (not in the paper: the adjoint)
 """

@@ -402,6 +402,41 @@ class Problem:
     def shape(self):
         return (self.nz, self.nO, self.nN, 4)
 
+    # ------------------------------------------------------------------ transpose
+    # Not in the paper (which solves forward problems only): the transposed
+    # operator A^T = Id - Sigma^T Lambda^T, written out as the definition.
+    # Sigma is block diagonal over heights (sigma_mats); Lambda is block
+    # diagonal over rays (Omega, n), each block the (4 nz) x (4 nz) matrix whose
+    # column (k, s) is the formal solution of a unit emissivity at height k in
+    # Stokes s on that ray.
+    def lambda_rays(self):
+        if not hasattr(self, "_Lrays"):
+            nz = self.nz
+            L = np.zeros((self.nO, self.nN, nz, 4, nz, 4))
+            for k in range(nz):
+                for s in range(4):
+                    e = np.zeros(self.shape())
+                    e[k, :, :, s] = 1.0
+                    L[:, :, :, :, k, s] = self.formal_solution(e).transpose(1, 2, 0, 3)
+            self._Lrays = L.reshape(self.nO, self.nN, 4 * nz, 4 * nz)
+        return self._Lrays
+
+    def apply_AT(self, y):
+        L = self.lambda_rays()
+        yr = y.transpose(1, 2, 0, 3).reshape(self.nO, self.nN, 4 * self.nz)
+        w = np.einsum("onji,onj->oni", L, yr)            # Lambda^T y, ray by ray
+        w = w.reshape(self.nO, self.nN, self.nz, 4).transpose(2, 0, 1, 3)
+        mats = self.sigma_mats()
+        out = np.empty_like(y)
+        for iz in range(self.nz):
+            out[iz] = (mats[iz].T @ w[iz].ravel()).reshape(y.shape[1:])
+        return y - out
+
+    def solve_adjoint(self, g, tol=1e-13, maxiter=4000, restart=400):
+        lam, hist = gmres(lambda v: self.apply_AT(v.reshape(g.shape)).ravel(), g.ravel(),
+                          tol=tol, maxiter=maxiter, restart=restart)
+        return lam.reshape(g.shape), hist
+
 
 def gmres(A, b, tol, maxiter, restart, x0=None):
     """Restarted GMRES with modified Gram-Schmidt (plain FP64)."""

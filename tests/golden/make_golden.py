@@ -2,11 +2,16 @@
 
 Calls only oracle/ and the seeded input generator; never the CUDA library.
 Run from the repository root:  python tests/golden/make_golden.py [names...]
-Outputs tests/golden/<name>.npz.
+Outputs tests/golden/<name>.npz (forward operator and solution),
+<name>_adj.npz (transposed operator and adjoint solve) and grad_mgii_small.npz
+(derivatives of an emergent-intensity functional by central differences of
+forward solves).
 """
 import os
 import sys
 import time
+from concurrent.futures import ProcessPoolExecutor
+from multiprocessing import get_context
 
 import numpy as np
 
@@ -51,6 +56,67 @@ def make_case(name):
                         rhs=P.rhs(), Ax=P.apply_A(x), sol=sol, mu=P.mu, f=P.f, los=los, emergent=em)
 
 
+# transposed operator and adjoint solve, on the reduced forward cases; y and g
+# are drawn as the GPU tests draw their vectors (polarisation 10x smaller)
+ADJOINT = ("twolevel", "mgii", "hi", "hi_aa")
+
+
+def adj_vec(shape, seed):
+    v = inputs.seeded_vector(shape, seed, 0.1, 1.0)
+    v[..., 1:] = v[..., 1:] * 0.1 - 0.05
+    return v
+
+
+def make_adjoint(name):
+    P = Problem(CASES[name]())
+    y, g = adj_vec(P.shape(), 2), adj_vec(P.shape(), 7)
+    lam, hist = P.solve_adjoint(g, tol=1e-13)
+    np.savez_compressed(os.path.join(HERE, name + "_adj.npz"), y=y, ATy=P.apply_AT(y), g=g, lam=lam,
+                        res=hist[-1])
+
+
+# dJ/d(B, theta_B, chi_B) per height for J = sum of the emergent Stokes I
+# (top height, mu > 0, every frequency) of the forward solution: central
+# differences of J at steps h and h/2, h = max(1e-3 |p|, 0.1 G for B, 1e-3 rad)
+GRAD_KEYS = ("B_G", "thetaB", "chiB")
+
+
+def grad_case():
+    return inputs.mgii(n_z=6, n_core_each=5, n_wing=4, n_mu_half=1, n_chi=4, seed=23)
+
+
+def grad_step(k, p0):
+    return max(1e-3 * abs(p0), 0.1 if k == 0 else 1e-3)
+
+
+def J_of(job):
+    k, iz, val = job
+    cfg = grad_case()
+    if k >= 0:
+        cfg["atm"][GRAD_KEYS[k]] = np.array(cfg["atm"][GRAD_KEYS[k]], dtype=np.float64)
+        cfg["atm"][GRAD_KEYS[k]][iz] = val
+    P = Problem(cfg)
+    x, _ = P.solve(tol=1e-13)
+    return float(x[-1, P.mu > 0, :, 0].sum())
+
+
+def make_grad():
+    cfg = grad_case()
+    nz = len(cfg["atm"]["z_km"])
+    jobs, steps = [(-1, 0, 0.0)], np.zeros((nz, 3))
+    for iz in range(nz):
+        for k in range(3):
+            p0 = float(cfg["atm"][GRAD_KEYS[k]][iz])
+            h = steps[iz, k] = grad_step(k, p0)
+            jobs += [(k, iz, p0 + h), (k, iz, p0 - h), (k, iz, p0 + h / 2), (k, iz, p0 - h / 2)]
+    with ProcessPoolExecutor(max_workers=os.cpu_count(), mp_context=get_context("spawn")) as ex:
+        J = list(ex.map(J_of, jobs))
+    Jp = np.array(J[1:]).reshape(nz, 3, 4)
+    fd = (Jp[..., 0] - Jp[..., 1]) / (2 * steps)
+    fd_half = (Jp[..., 2] - Jp[..., 3]) / steps
+    np.savez_compressed(os.path.join(HERE, "grad_mgii_small.npz"), fd=fd, fd_half=fd_half, step=steps, J0=J[0])
+
+
 def make_sample(name):
     mk, sig_pts, ray_pts = SAMPLES[name]
     cfg = mk()
@@ -67,8 +133,17 @@ def make_sample(name):
 
 
 if __name__ == "__main__":
-    names = sys.argv[1:] or list(CASES) + list(SAMPLES)
+    names = sys.argv[1:] or list(CASES) + list(SAMPLES) + [a + "_adj" for a in ADJOINT] + ["grad"]
     for nm in names:
         t0 = time.time()
-        (make_case if nm in CASES else make_sample)(nm)
+        if nm in CASES:
+            make_case(nm)
+        elif nm in SAMPLES:
+            make_sample(nm)
+        elif nm.endswith("_adj"):
+            make_adjoint(nm[:-4])
+        elif nm == "grad":
+            make_grad()
+        else:
+            raise SystemExit(f"unknown golden set {nm}")
         print(f"{nm}: {time.time() - t0:.1f} s", flush=True)

@@ -1,11 +1,17 @@
-"""S13: the transposed operator and the adjoint solve, through the C ABI.
+"""S13: the transposed operator, the adjoint solve and the field gradient,
+through the C ABI.
 
-A^T is fixed by A, and A is pinned to the oracle (test_gpu_parity.py), so the
-transpose is checked by the identity <y, A x> = <A^T y, x> on seeded vectors
-(a property of any size), in FP64 mode on the two-level slab and on the
-two-term Mg II and H I physics.  The adjoint solve is checked by its residual
-and by <g, x> = <lam, b> for A x = b and A^T lam = g.
+A^T y is compared element by element with the oracle's A^T = Id - Sigma^T
+Lambda^T (tests/golden/<case>_adj.npz; the oracle's transpose is pinned
+against a brute-force matrix), and checked by the identity <y, A x> =
+<A^T y, x> on seeded vectors (a property of any size).  The adjoint solve is
+compared with the oracle's and checked by its residual and by <g, x> =
+<lam, b> for A x = b and A^T lam = g.  The gradient of an emergent-intensity
+functional with respect to (B, theta_B, chi_B) is compared with central
+differences of the oracle's forward solves (tests/golden/grad_mgii_small.npz).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +19,8 @@ from paper_2505_20968_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 CASES = {
     "twolevel": lambda: inputs.twolevel_slab(n_z=8, n_x=11, n_mu_half=2, n_chi=4, eps=1e-2),
@@ -31,6 +39,37 @@ def _vec(P, seed):
 
 def _dot(a, b):
     return float(torch.sum(a.double() * b.double()).item())
+
+
+def _gold(name):
+    return dict(np.load(os.path.join(GOLD, name + "_adj.npz")))
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("name,prec,tol", [("twolevel", "fp64", 1e-8), ("mgii", "fp64", 1e-8),
+                                           ("hi", "fp64", 1e-8), ("hi_aa", "fp64", 1e-8),
+                                           ("mgii", "fp32", 1e-6), ("hi", "fp32", 1e-6)])
+def test_transpose_matches_oracle(name, prec, tol):
+    """A^T y against the oracle, element by element, within a bound of
+    max|A^T y|.  FP64 mode: 1e-8.  The library and the oracle integrate the
+    redistribution tiles by different quadratures, each within 1e-9 of the
+    exact integral (App. C; the oracle's is pinned against adaptive
+    Gauss-Kronrod); measured 7e-12 (two-level), 2e-12 (H I), 1.7e-10 (Mg II),
+    1.5e-9 (H I, angle-averaged).  FP32 mode: 1e-6.  A^T runs in FP64 on the
+    FP64 copy of the tables, and only the FP32 input and output vectors are
+    rounded (2^-24 each); measured 3.8e-8."""
+    from paper_2505_20968_gb300.binding import PRD
+    G = _gold(name)
+    P = PRD(CASES[name](), precision=prec, device=0)
+    y = torch.from_numpy(G["y"]).to(device=P.device, dtype=P.dtype)
+    out = P.apply_operator_T(y).cpu().numpy().astype(np.float64)
+    d = _rel(out, G["ATy"])
+    print(f"A^T y {name} {prec}: {d:.2e}")
+    assert d < tol, f"{name} {prec}: {d:.2e}"
+    P.close()
 
 
 @pytest.mark.parametrize("name", ["twolevel", "mgii", "hi", "hi_aa"])
@@ -70,48 +109,51 @@ def test_adjoint_solve_fp64(name, tol):
     two-term case is solved to 1e-10 (more iterations than the forward solve)."""
     from paper_2505_20968_gb300.binding import PRD
     P = PRD(CASES[name](), precision="fp64", device=0)
+    G = _gold(name)
     b = P.rhs()
     x, info = P.solve(tol=1e-12, max_iter=600, restart=80)
-    g = _vec(P, 7)
+    g = torch.from_numpy(G["g"]).to(device=P.device, dtype=P.dtype)
     lam, ainfo = P.solve_adjoint(g, tol=tol, max_iter=3000, restart=120, check=False)
     assert ainfo["rc"] == 0, ainfo
     r = g - P.apply_operator_T(lam)
     assert float(torch.linalg.norm(r.double()) / torch.linalg.norm(g.double())) < 10 * tol
     lhs, rhs = _dot(g, x), _dot(lam, b)
     assert abs(lhs - rhs) < 1e3 * tol * abs(lhs), (lhs, rhs, ainfo["iters"])
+    # against the oracle's adjoint solution (converged to 1e-13): the residual
+    # tolerance times the amplification of A^-T (measured 0.8 of tol on both)
+    d = _rel(lam.cpu().numpy(), G["lam"])
+    print(f"lambda {name}: {d:.2e} after {ainfo['iters']} iterations")
+    assert d < 1e2 * tol, f"lambda {name}: {d:.2e}"
     P.close()
 
 
-def test_grad_B_matches_finite_differences_of_J():
-    """dJ/d(B, theta_B) from prd_grad_B (one adjoint solve) against central
-    differences of J over two forward solves, for J = sum of the emergent
-    intensities of the top layer (linear in I) on a small two-term case."""
+def test_grad_B_matches_oracle_finite_differences():
+    """dJ/d(B, theta_B, chi_B) at every height from prd_grad_B (one adjoint
+    solve plus central differences of the residual) against central
+    differences of J over the oracle's forward solves, for J = sum of the
+    emergent intensities of the top layer (linear in I) on a small two-term
+    case.  The oracle reference is the Richardson combination of its central
+    differences at h and h/2 (h = 1e-3 of the parameter, 0.1 G for B < 100 G),
+    accurate to O(h^4); the library differences the residual at step h, an
+    O(h^2) approximation whose truncation is of the size the oracle's h and
+    h/2 differences show (up to 7e-5 of the largest component of a kind), so
+    the bound is 2e-4 of the largest component of each kind (measured 2.4e-5
+    for B, 1.8e-6 for theta_B, 2.1e-5 for chi_B)."""
     from paper_2505_20968_gb300.binding import PRD
-    mk = lambda: inputs.mgii(n_z=6, n_core_each=5, n_wing=4, n_mu_half=1, n_chi=4, seed=23)
-    cfg = mk()
+    G = dict(np.load(os.path.join(GOLD, "grad_mgii_small.npz")))
+    cfg = inputs.mgii(n_z=6, n_core_each=5, n_wing=4, n_mu_half=1, n_chi=4, seed=23)
     P = PRD(cfg, precision="fp64", device=0)
     x, _ = P.solve(tol=1e-12, max_iter=600, restart=80)
-    top = P.mu > 0
+    top = torch.from_numpy(P.mu > 0).to(x.device)
+    J = float(x[-1, top, :, 0].sum().item())
+    # residual 1e-12, amplified up to ~1e5 into the top-layer intensity
+    assert abs(J - float(G["J0"])) < 1e-6 * abs(J), (J, float(G["J0"]))
     dJdI = torch.zeros_like(x)
-    dJdI[-1, torch.from_numpy(top).to(x.device), :, 0] = 1.0
+    dJdI[-1, top, :, 0] = 1.0
     g = P.grad_B(x, dJdI)
-    assert np.all(np.isfinite(g))
-
-    def J_of(atm_key, iz, val):
-        c = mk()
-        c["atm"][atm_key] = np.array(c["atm"][atm_key], dtype=np.float64)
-        c["atm"][atm_key][iz] = val
-        Q = PRD(c, precision="fp64", device=0)
-        xq, _ = Q.solve(tol=1e-12, max_iter=600, restart=80)
-        v = float(xq[-1, torch.from_numpy(top).to(xq.device), :, 0].sum().item())
-        Q.close()
-        return v
-
-    for key, k, iz in (("B_G", 0, 2), ("thetaB", 1, 4)):
-        p0 = float(cfg["atm"][key][iz])
-        h = max(1e-3 * abs(p0), 0.1 if k == 0 else 1e-3)
-        lo = p0 if (k == 0 and p0 - h < 0) else p0 - h
-        fd = (J_of(key, iz, p0 + h) - J_of(key, iz, lo)) / (p0 + h - lo)
-        scale = float(x[-1, torch.from_numpy(top).to(x.device), :, 0].sum().item())
-        assert abs(g[iz, k] - fd) < 1e-4 * abs(fd) + 1e-9 * scale, (key, iz, g[iz, k], fd)
+    fd = (4.0 * G["fd_half"] - G["fd"]) / 3.0
+    for k, kind in enumerate(("B", "theta_B", "chi_B")):
+        d = np.max(np.abs(g[:, k] - fd[:, k])) / np.max(np.abs(fd[:, k]))
+        print(f"dJ/d{kind}: {d:.2e}")
+        assert d < 2e-4, f"dJ/d{kind}: {d:.2e}"
     P.close()
