@@ -293,6 +293,59 @@ def test_zero_field_1d_symmetries():
     assert np.max(np.abs(xi - xi[:, :, :1])) < 1e-10 * np.max(np.abs(x))
 
 
+def test_r2_marginal_is_doppler_averaged_kramers_heisenberg():
+    """Fixes which factor of Eq. RQIIKKp carries the conjugate, with alpha of
+    App. B, by the physics of one atom rather than by the printed formula.
+
+    An atom at rest scatters lower state k_l -> k_l' with the amplitude
+    (Kramers-Heisenberg) T = sum_{k_u} M(k_u) / (x_{k_u} - i a), x in Doppler
+    units, a = Gamma / (4 pi Dnu_D).  Partial fractions give
+        A_u A_v^* = alpha_uv / (2a) [Phi(x_u) + Phi(x_v)^*],  Phi(x) = 1/(a + i x),
+    with alpha_uv = 1 / (1 + i (x_u - x_v) / (2a)), and the Doppler average of
+    Phi(x)^* is sqrt(pi) W(a, x).  Under a flat incident spectrum F integrates
+    to sqrt(pi) W, so the block of R_II (R_III off: eps = 0, no elastic
+    collisions) must equal 2a times the Doppler average of Tr(sigma_i T
+    sigma_j T^+), which is computed here directly by quadrature over the
+    velocity, without alpha or W.  Zeeman splittings comparable to the
+    damping width (B = 360 G, a = 0.05) make the upper-level interference
+    matter.  Swapping the conjugated factor changes the result at O(1),
+    conjugating alpha by 5e-4; the oracle agrees to ~1e-13."""
+    cfg = inputs.mgii(n_z=2, n_core_each=8, n_wing=3, n_mu_half=1, n_chi=4, seed=7)
+    atm = cfg["atm"]
+    nz = len(atm["z_km"])
+    for key, val in (("a", 0.05), ("eps", 0.0), ("r_el", 0.0), ("B_G", 360.0), ("thetaB", 0.7),
+                     ("chiB", 0.4)):
+        atm[key] = np.full(nz, val)
+    atm["v_kms"] = np.zeros((nz, 3))
+    P = Problem(cfg, normalise=False)
+    from oracle.problem import SIG
+    iz, o, op = 0, 1, 6
+    assert 0.0 < P.thetas[P.cls[o, op]] < np.pi
+    N, a = P.nN, P.a[iz]
+    c2 = 3.0 / (8.0 * np.pi * P.S2)
+    flat = P.block(iz, o, op).reshape(N, 4, N, 4).sum(axis=2) / (P.k[iz] * P.wang[op] * c2 * 2.0 * a)
+    ampO, ampI, s = P.amp[iz][o], P.amp[iz][op], P.shift[iz]
+
+    def kramers_heisenberg(xn):
+        def f(y):
+            acc = np.zeros((4, 4))
+            for kl in range(P.nl_states):
+                for klp in range(P.nl_states):
+                    T = np.zeros((2, 2), complex)
+                    for ku in range(P.nu_states):
+                        T += np.outer(ampO[:, ku, klp].conj(), ampI[:, ku, kl]) / (xn + s[ku, klp] - y - 1j * a)
+                    acc += np.einsum("iab,bc,jcd,ad->ij", SIG, T, SIG, T.conj()).real
+            return acc * np.exp(-y * y) / np.sqrt(np.pi)
+        poles = sorted({xn + s[ku, klp] for ku in range(P.nu_states) for klp in range(P.nl_states)})
+        pts = [-12.0] + [q for q in poles if -12.0 < q < 12.0] + [12.0]
+        return sum(quad_vec(f, lo, hi, epsabs=1e-14, epsrel=1e-12, limit=2000)[0]
+                   for lo, hi in zip(pts[:-1], pts[1:]))
+
+    for n in (0, 4, 9, 14, N - 1):           # wings and both line cores
+        k = kramers_heisenberg(P.u[iz][n])
+        assert np.max(np.abs(k - flat[n])) < 1e-10 * np.max(np.abs(k)), n
+
+
 def test_gmres_matches_dense_solve():
     """Brute force on a tiny grid: assemble A column by column, solve by LU;
     the same for A^T and the adjoint solve."""
