@@ -284,13 +284,22 @@ def test_crd_limit():
 
 
 def test_zero_field_1d_symmetries():
-    """Static, unmagnetised 1D slab: U = V = 0 and no chi dependence."""
+    """Static, unmagnetised 1D slab: U = V = 0 and no chi dependence; at the
+    disk centre Q = 0 (axial symmetry), and near the limb the line-core
+    scattering polarisation is parallel to the limb, Q/I > 0 (positive Q
+    along the limb, as the figures of Sect. 6.3 take it; the radiation field
+    at the surface is limb-darkened, so its anisotropy is positive)."""
     cfg = inputs.twolevel_slab(n_z=8, n_x=9, n_mu_half=2, n_chi=4, eps=1e-2)
     P = Problem(cfg)
     x, _ = P.solve(tol=1e-12)
     assert np.max(np.abs(x[..., 2:])) < 1e-12 * np.max(np.abs(x[..., 0]))
     xi = x.reshape(P.nz, 4, 4, P.nN, 4)          # [z, mu, chi, n, s]
     assert np.max(np.abs(xi - xi[:, :, :1])) < 1e-10 * np.max(np.abs(x))
+    centre = P.emergent(x, 1.0, 0.0)
+    assert np.max(np.abs(centre[:, 1:])) < 1e-12 * np.max(centre[:, 0])
+    limb = P.emergent(x, 0.1, 0.0)
+    core = P.nN // 2                               # x = 0 on the symmetric grid
+    assert limb[core, 1] / limb[core, 0] > 1e-3
 
 
 def test_r2_marginal_is_doppler_averaged_kramers_heisenberg():
