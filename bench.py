@@ -22,6 +22,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle legs report one core: keep numpy's BLAS single-threaded
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np   # noqa: E402
 
@@ -79,10 +82,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def oracle_sample(cfg, n_dirs_in=4, n_rays=64, seed=5):
-    """Time the oracle on a bounded sample; return (seconds per full apply, description)."""
+def oracle_problem(cfg):
+    """The oracle's set-up for the workload (atom, K, DELO tables); not timed."""
     from oracle.problem import Problem
-    P = Problem(cfg, normalise=False)
+    return Problem(cfg, normalise=False)
+
+
+def oracle_sample(P, n_dirs_in=4, n_rays=64, seed=5):
+    """Time the oracle on a bounded sample; return (seconds per full apply, description).
+    Its tile caches are emptied first, so every sample computes its tiles."""
+    P._tiles.clear()
+    P._r3.clear()
     x = np.random.default_rng(seed).uniform(0.1, 1.0, P.shape())
     iz, o = P.nz // 2, P.nO - 3
     t0 = time.perf_counter()
@@ -122,8 +132,9 @@ def run_reference(args, cfg, workload):
     threads = 1
     per = []
     desc = ""
+    P = oracle_problem(cfg)
     for step in range(args.warmup + args.steps):
-        t, desc, _ = oracle_sample(cfg, n_dirs_in=2 if step < args.warmup else 4, seed=step)
+        t, desc, _ = oracle_sample(P, n_dirs_in=1 if step < args.warmup else 2, seed=step)
         if step >= args.warmup:
             per.append(t)
     value = 1.0 / statistics.median(per)
@@ -265,7 +276,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        per, desc, _ = oracle_sample(cfg)
+        per, desc, _ = oracle_sample(oracle_problem(cfg))
         cpu = {"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
     if rank == 0:
