@@ -27,8 +27,16 @@ def test_library_exports_every_declared_symbol():
 
 def test_binding_lists_the_same_symbols():
     from paper_2505_20968_gb300 import binding
-    assert sorted(binding.EXPORTS) == [n for n in declared() if n != "prd_last_error"] or \
-        set(binding.EXPORTS) <= set(declared())
+    assert sorted(binding.EXPORTS) == declared()
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library the binding raises."""
+    from paper_2505_20968_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libprd.so"))
+    with pytest.raises(ImportError):
+        binding.lib()
 
 
 def test_errors_without_setup_and_bad_arguments():
