@@ -83,8 +83,9 @@ int prd_set_stream(prd_ctx* ctx, void* cuda_stream);
  * allocator of the host framework) instead of cudaMalloc/cudaFree.
  * alloc(bytes, user, stream) returns a device pointer of at least `bytes`
  * bytes on the ctx device, 256-byte aligned, usable on `stream` (the ctx
- * stream at the time of the call), or NULL on failure (-> PRD_E_NOMEM);
- * free(ptr, user) releases it.  Both NULL: back to cudaMalloc/cudaFree.  Every
+ * stream at the time of the call), or NULL on failure (-> PRD_E_NOMEM); a
+ * pointer that is not 256-byte aligned is handed back to free and the call
+ * that needed it fails with PRD_E_ARG; free(ptr, user) releases it.  Both NULL: back to cudaMalloc/cudaFree.  Every
  * buffer is released with the deallocator it was obtained from, so the call
  * can come at any time; set it before prd_setup to route the workspace
  * (tiles and tables) through it.  prd_apply_sigma_noalloc allocates nothing

@@ -1,6 +1,7 @@
 // C ABI entry points (include/prd.h): argument checks, ordering, setup
 // orchestration.  No exception leaves this file.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -20,6 +21,11 @@ int dalloc(Ctx* c, DBuf& b, size_t bytes) {
   if (c->alloc_fn) {
     b.p = c->alloc_fn(bytes, c->alloc_user, (void*)c->stream);
     if (!b.p) return fail(c, PRD_E_NOMEM, "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    if (reinterpret_cast<uintptr_t>(b.p) & 255u) {   // bulk copies and vector loads need the alignment
+      c->free_fn(b.p, c->alloc_user);
+      b.p = nullptr;
+      return fail(c, PRD_E_ARG, "the caller's allocator returned a pointer that is not 256-byte aligned");
+    }
     b.fr = c->free_fn;
     b.user = c->alloc_user;
     b.bytes = bytes;
