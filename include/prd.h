@@ -18,9 +18,13 @@
  *   - host arrays are read during the call and copied; the caller keeps them.
  *   - "device" pointers are caller-owned CUDA allocations on the ctx's device,
  *     contiguous, layout [z][Omega][nu][4], element type double for
- *     PRD_FP64 and float for PRD_FP32.  The library never frees them.
- *   - the library owns its workspace (cudaMalloc at prd_setup, freed at
- *     prd_destroy or at the next prd_setup).
+ *     PRD_FP64 and float for PRD_FP32, starting on a whole Stokes point
+ *     (address a multiple of 4 elements: 32 bytes in FP64, 16 in FP32;
+ *     otherwise PRD_E_ARG, as the kernels move one point per access).  The
+ *     library never frees them.
+ *   - the library owns its workspace (cudaMalloc at prd_setup, or the
+ *     caller's allocator of prd_set_allocator; freed at prd_destroy or at the
+ *     next prd_setup).
  *   - work is issued on the ctx stream (prd_set_stream, default: the legacy
  *     stream) and is asynchronous, except prd_setup, prd_solve and calls that
  *     return host scalars, which synchronise the stream.

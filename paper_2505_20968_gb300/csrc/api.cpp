@@ -167,6 +167,10 @@ using prd::fail;
 #define NEED_READY()                                              \
   if (!c->ready) return fail(c, PRD_E_STATE, "call prd_setup first");
 
+#define NEED_ALIGNED(p)                 \
+  if (!prd::point_aligned(c, (p)))      \
+    return fail(c, PRD_E_ARG, #p " does not start on a whole Stokes point (4 elements)");
+
 extern "C" {
 
 int prd_create(prd_ctx** out, int device, int precision) {
@@ -350,6 +354,7 @@ int prd_rhs(prd_ctx* ctx, void* b_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!b_dev) return fail(c, PRD_E_ARG, "b_dev is NULL");
+  NEED_ALIGNED(b_dev);
   return prd::rhs(c, b_dev);
 }
 
@@ -357,6 +362,8 @@ int prd_apply_sigma(prd_ctx* ctx, const void* x_dev, void* eps_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !eps_dev || x_dev == eps_dev) return fail(c, PRD_E_ARG, "x_dev/eps_dev NULL or aliased");
+  NEED_ALIGNED(x_dev);
+  NEED_ALIGNED(eps_dev);
   return prd::apply_sigma(c, x_dev, eps_dev, true);
 }
 
@@ -364,6 +371,8 @@ int prd_apply_lambda(prd_ctx* ctx, const void* eps_dev, void* out_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!eps_dev || !out_dev || eps_dev == out_dev) return fail(c, PRD_E_ARG, "eps_dev/out_dev NULL or aliased");
+  NEED_ALIGNED(eps_dev);
+  NEED_ALIGNED(out_dev);
   return prd::apply_lambda(c, eps_dev, out_dev, nullptr, false);
 }
 
@@ -371,6 +380,8 @@ int prd_apply_operator(prd_ctx* ctx, const void* x_dev, void* y_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !y_dev || x_dev == y_dev) return fail(c, PRD_E_ARG, "x_dev/y_dev NULL or aliased");
+  NEED_ALIGNED(x_dev);
+  NEED_ALIGNED(y_dev);
   return prd::apply_operator(c, x_dev, y_dev);
 }
 
@@ -378,6 +389,8 @@ int prd_apply_preconditioner(prd_ctx* ctx, const void* y_dev, void* x_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !y_dev || x_dev == y_dev) return fail(c, PRD_E_ARG, "x_dev/y_dev NULL or aliased");
+  NEED_ALIGNED(x_dev);
+  NEED_ALIGNED(y_dev);
   return prd::apply_precond(c, y_dev, x_dev);
 }
 
@@ -393,6 +406,8 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !(tol > 0) || max_iter < 1 || restart < 1) return fail(c, PRD_E_ARG, "bad solve arguments");
+  NEED_ALIGNED(x0_dev);
+  NEED_ALIGNED(x_dev);
   try {
     int rc = prd::solve(c, tol, max_iter, restart, x0_dev, x_dev, iters, true_rel_res, res_history);
     if (c->tc_err.p) {
@@ -409,6 +424,8 @@ int prd_grad_B(prd_ctx* ctx, const void* x_dev, const void* dJdI_dev, double* dJ
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !dJdI_dev || !dJ_dp) return fail(c, PRD_E_ARG, "NULL argument");
+  NEED_ALIGNED(x_dev);
+  NEED_ALIGNED(dJdI_dev);
   try {
     return prd::grad_b(c, x_dev, dJdI_dev, 1e-10, dJ_dp);
   } catch (const std::exception& e) {
@@ -422,6 +439,8 @@ int prd_solve_batch(prd_ctx* const* ctxs, int n, double tol, int max_iter, int r
   if (!ctxs || !x_devs || n < 1 || !(tol > 0) || max_iter < 1 || restart < 1) return PRD_E_ARG;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || !x_devs[i]) return PRD_E_ARG;
+    if (!prd::point_aligned(&ctxs[i]->c, x_devs[i]))
+      return fail(&ctxs[i]->c, PRD_E_ARG, "x_devs[i] does not start on a whole Stokes point (4 elements)");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return PRD_E_ARG;
   }
@@ -456,6 +475,8 @@ int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !y_dev) return fail(c, PRD_E_ARG, "NULL vector");
+  NEED_ALIGNED(x_dev);
+  NEED_ALIGNED(y_dev);
   try {
     return prd::apply_operator_t(c, x_dev, y_dev);
   } catch (const std::exception& e) {
@@ -469,6 +490,8 @@ int prd_solve_adjoint(prd_ctx* ctx, const void* g_dev, double tol, int max_iter,
   NEED_READY();
   if (!g_dev || !lam_dev || !(tol > 0) || max_iter < 1 || restart < 1)
     return fail(c, PRD_E_ARG, "bad adjoint solve arguments");
+  NEED_ALIGNED(g_dev);
+  NEED_ALIGNED(lam_dev);
   try {
     return prd::solve_adjoint(c, g_dev, tol, max_iter, restart, lam_dev, iters, true_rel_res, res_history);
   } catch (const std::exception& e) {
@@ -482,6 +505,8 @@ int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double*
   CTX_OR_ARG(ctx);
   NEED_READY();
   if (!x_dev || !out_dev || nlos < 1 || !mu || !chi) return fail(c, PRD_E_ARG, "bad emergent_stokes arguments");
+  NEED_ALIGNED(x_dev);
+  NEED_ALIGNED(out_dev);
   for (int i = 0; i < nlos; ++i)
     if (!(mu[i] > 0 && mu[i] <= 1)) return fail(c, PRD_E_ARG, "line-of-sight mu must be in (0, 1]");
   try {

@@ -937,6 +937,8 @@ extern "C" int prd_apply_sigma_noalloc(prd_ctx* ctx, const void* x_dev, void* ep
   cudaSetDevice(c->device);
   if (!c->ready) return prd::fail(c, PRD_E_STATE, "call prd_setup first");
   if (!x_dev || !eps_dev || x_dev == eps_dev) return prd::fail(c, PRD_E_ARG, "x_dev/eps_dev NULL or aliased");
+  if (!prd::point_aligned(c, x_dev) || !prd::point_aligned(c, eps_dev))
+    return prd::fail(c, PRD_E_ARG, "x_dev/eps_dev do not start on a whole Stokes point (4 elements)");
   if (c->prec == PRD_FP64) return prd::sigma_static_T<double>(c, (const double*)x_dev, (double*)eps_dev);
   return prd::sigma_static_T<float>(c, (const float*)x_dev, (float*)eps_dev);
 }

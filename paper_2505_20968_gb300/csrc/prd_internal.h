@@ -147,6 +147,12 @@ struct Ctx {
   ~Ctx();
 };
 
+// Caller vectors [z][Omega][nu][4] are moved one Stokes point (4 elements) per
+// access, so each must start on a multiple of 4 * esz bytes (NULL passes).
+inline bool point_aligned(const Ctx* c, const void* p) {
+  return !p || reinterpret_cast<uintptr_t>(p) % (4 * c->esz) == 0;
+}
+
 // ---- errors
 int fail(Ctx* c, int code, const std::string& msg);
 #define PRD_CUDA_TRY(ctx, expr)                                                     \
