@@ -529,7 +529,6 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 
 }  // namespace tc
 
-// Tensor map over the tiles viewed as [slab][n][k] fp32, k = 2N innermost.
 // Work list and error flag of the tensor-core contraction.
 int r2_tc_prepare(Ctx* c) {
   if (c->prec != PRD_FP32) return PRD_OK;
