@@ -1,4 +1,6 @@
-"""Thin Python binding of libprd.so (include/prd.h): argument marshalling only.
+"""Thin Python binding of libprd.so (include/prd.h): argument marshalling only,
+plus a torch.autograd.Function that routes gradients with respect to the
+magnetic field through prd_grad_B (solve_with_field).
 
 PyTorch provides device memory and the current CUDA stream; every step of the
 operator runs in the library's CUDA kernels.  There is no CPU fallback: if the
@@ -336,3 +338,42 @@ def solve_batch(problems, tol=1e-6, max_iter=200, restart=30, check=True):
         problems[bad[0]]._check(rcs[bad[0]])
     return outs, infos
 
+
+
+class _FieldSolve(torch.autograd.Function):
+    """The solution I(p) of A(p) I = b(p) as a function of the magnetic field
+    p = (B [G], theta_B, chi_B [rad]) of every height, shape (nz, 3).  Forward
+    sets the problem up with that field and solves it (prd_solve); backward is
+    the adjoint method of prd_grad_B: one solve A^T lam = dJ/dI, then
+    dJ/dp = lam^T (db/dp - (dA/dp) I)."""
+
+    @staticmethod
+    def forward(ctx, field, cfg, make, solve_kw):
+        f = field.detach().to("cpu", torch.float64).numpy()
+        atm = dict(cfg["atm"], B_G=f[:, 0].copy(), thetaB=f[:, 1].copy(), chiB=f[:, 2].copy())
+        P = make(dict(cfg, atm=atm))
+        x, _ = P.solve(**solve_kw)
+        ctx.P = P
+        ctx.field_like = (field.dtype, field.device)
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        g = ctx.P.grad_B(x, gx.to(x.dtype).contiguous())
+        ctx.P.close()
+        dtype, device = ctx.field_like
+        return torch.as_tensor(g, dtype=dtype, device=device), None, None, None
+
+
+def solve_with_field(cfg, field, precision="fp64", device=0, tol=1e-12, max_iter=600, restart=80, make=None):
+    """Solve the problem `cfg` with its magnetic field replaced by `field`
+    ((nz, 3): B, theta_B, chi_B per height) and return the Stokes field
+    I[z][Omega][nu][4] as a differentiable function of `field`: the gradient of
+    any scalar built from I reaches `field` through one adjoint solve.  `make`
+    builds the solver object from a problem dict (default: PRD)."""
+    if make is None:
+        def make(c):
+            return PRD(c, precision=precision, device=device)
+    return _FieldSolve.apply(field, cfg, make, dict(tol=tol, max_iter=max_iter, restart=restart))
