@@ -1,0 +1,59 @@
+"""The FP32 tile layout of the tensor-core contraction (tile_off in
+csrc/prd_internal.h), checked on the host: within a tile of N rows and ld
+columns it is a bijection onto [0, N ld); every 16-column K step is one
+contiguous block of N x 64 bytes (one bulk copy, 16-byte aligned start and
+size); and inside a block each row's 64 bytes are permuted by the 64-byte
+shared-memory swizzle, written here in its own form (byte address bits [4:5]
+XOR bits [7:8]), which is the layout the MMA descriptors declare."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SRC = r'''
+#include <cstdio>
+#include <vector>
+#include "prd_internal.h"
+int main() {
+  const int Ns[] = {1, 7, 8, 9, 150, 200, 208, 255, 256};
+  for (int N : Ns) {
+    const int ld = (2 * N + 15) / 16 * 16;
+    std::vector<char> seen((size_t)N * ld, 0);
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < ld; ++k) {
+        const size_t off = prd::tile_off(n, k, N, ld, true);
+        if (off >= (size_t)N * ld || seen[off]) { std::printf("N=%d n=%d k=%d: off %zu\n", N, n, k, off); return 1; }
+        seen[off] = 1;
+        const int kc = k / 16, kl = k % 16;
+        const size_t base = (size_t)kc * N * 16;            // floats
+        if (off < base || off >= base + (size_t)N * 16) { std::printf("N=%d: step %d not contiguous\n", N, kc); return 2; }
+        const unsigned lin = (unsigned)(n * 64 + kl * 4);   // bytes, unswizzled row-major [n][16]
+        const unsigned swz = lin ^ (((lin >> 7) & 3u) << 4);
+        if ((off - base) * 4 != swz) { std::printf("N=%d n=%d k=%d: swizzle\n", N, n, k); return 3; }
+      }
+    if (((size_t)N * ld * 4) % 64 || ((size_t)N * 64) % 16) { std::printf("N=%d: alignment\n", N); return 4; }
+    if (prd::tile_off(N - 1, 2 * N - 1, N, 2 * N + 4, false) != (size_t)(N - 1) * (2 * N + 4) + 2 * N - 1) return 5;
+  }
+  std::printf("ok\n");
+  return 0;
+}
+'''
+
+
+def test_fp32_tile_layout_is_a_swizzled_bijection(tmp_path):
+    gxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if not gxx or not os.path.isdir(cuda_inc):
+        pytest.skip("g++ or the CUDA headers are missing")
+    src = tmp_path / "layout.cpp"
+    exe = tmp_path / "layout"
+    src.write_text(SRC)
+    csrc = os.path.join(ROOT, "paper_2505_20968_gb300", "csrc")
+    r = subprocess.run([gxx, "-std=c++17", "-O1", "-I", csrc, "-I", cuda_inc, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
