@@ -119,3 +119,132 @@ def test_angle_classes_and_pair_tables(tmp_path):
     assert r.returncode == 0, r.stderr[-3000:]
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), (r.returncode, r.stdout, r.stderr[-2000:])
+
+
+DUMP = r'''
+#include <cstdio>
+#include <vector>
+#include "prd_internal.h"
+// reads a problem (text), builds the library's host tables and prints them
+int main(int argc, char** argv) {
+  FILE* f = std::fopen(argv[1], "r");
+  if (!f) return 2;
+  prd_atom at{};
+  int twoS, nz;
+  if (std::fscanf(f, "%d %lf %lf %lf %lf %d", &twoS, &at.E_u_cm[0], &at.E_u_cm[1], &at.mass_amu, &at.g_s, &nz) != 6)
+    return 3;
+  at.twoS = twoS;
+  at.kind = twoS ? PRD_TWO_TERM : PRD_TWO_LEVEL;
+  std::vector<std::vector<double>> A(11, std::vector<double>(nz));
+  for (auto& arr : A) for (auto& x : arr) if (std::fscanf(f, "%lf", &x) != 1) return 4;
+  std::vector<double> v(3 * nz);
+  for (auto& x : v) if (std::fscanf(f, "%lf", &x) != 1) return 5;
+  int nnu, kind, nmu, nchi;
+  if (std::fscanf(f, "%d %d %d %d", &nnu, &kind, &nmu, &nchi) != 4) return 6;
+  std::vector<double> grid(nnu);
+  for (auto& x : grid) if (std::fscanf(f, "%lf", &x) != 1) return 7;
+  std::fclose(f);
+  prd_ctx* h = new prd_ctx();
+  prd::Ctx* c = &h->c;
+  if (prd_set_atom(h, &at)) return 8;
+  if (prd_set_atmosphere(h, nz, A[0].data(), A[1].data(), A[2].data(), A[3].data(), A[4].data(), A[5].data(),
+                         A[6].data(), A[7].data(), A[8].data(), A[9].data(), A[10].data(), v.data())) return 9;
+  if (prd_set_quadrature(h, nnu, grid.data(), kind, nmu, nchi, PRD_MU_GL_HEMISPHERES, PRD_MODE_AD)) return 10;
+  if (prd::build_host_tables(c)) return 11;
+  const int nu = c->nu_st, nl = c->nl_st, nO = c->nO;
+  std::printf("%d %d %d %d\n", nz, nO, nu, nl);
+  for (int iz = 0; iz < nz; ++iz) std::printf("%.17g\n", c->dnuD[iz]);
+  for (double x : c->shift) std::printf("%.17g\n", x);
+  for (auto z : c->alpha) std::printf("%.17g %.17g\n", z.real(), z.imag());
+  for (auto z : c->beta) std::printf("%.17g %.17g\n", z.real(), z.imag());
+  for (auto z : c->amp) std::printf("%.17g %.17g\n", z.real(), z.imag());
+  delete h;
+  return 0;
+}
+'''
+
+
+def _build_exe(tmp_path, name, src_text):
+    from paper_2505_20968_gb300 import build
+    gxx = shutil.which("g++")
+    cuda = "/usr/local/cuda"
+    if not gxx or not os.path.isdir(os.path.join(cuda, "include")):
+        pytest.skip("g++ or the CUDA toolkit is missing")
+    libdir = os.path.dirname(build.build())
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.exists(os.path.join(d, "libcudart.so"))), None)
+    if cudalib is None:
+        pytest.skip("libcudart.so not found")
+    src, exe = tmp_path / (name + ".cpp"), tmp_path / name
+    src.write_text(src_text)
+    csrc = os.path.join(ROOT, "paper_2505_20968_gb300", "csrc")
+    r = subprocess.run([gxx, "-std=c++17", "-O1", "-I", csrc, "-I", os.path.join(cuda, "include"), str(src),
+                        "-o", str(exe), "-L", libdir, "-lprd", "-Wl,-rpath," + libdir, "-L", cudalib, "-lcudart",
+                        "-Wl,-rpath," + cudalib], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe
+
+
+def test_atom_tables_match_the_oracle(tmp_path):
+    """S0 host tables of the library against the oracle, on Mg II physics with
+    a strong-field (Paschen-Back) height added: Doppler widths, the upper-state
+    energies seen as shifts from each lower state, the branching ratios
+    alpha/beta of every upper-state pair (App. B), and the products of
+    polarisation amplitudes conj(a(k_u, k_l')) a(k_u, k_l) of every direction
+    pair, which do not depend on the phase of each eigenvector.  The library
+    diagonalises the Hamiltonian in fixed-M 2 x 2 blocks, the oracle as a full
+    matrix; states are matched by energy."""
+    import numpy as np
+    from paper_2505_20968_gb300 import inputs
+    from oracle.problem import Problem
+    cfg = inputs.mgii(n_z=4, n_core_each=4, n_wing=4, n_mu_half=1, n_chi=4, seed=17)
+    atm = cfg["atm"]
+    atm["B_G"] = np.array(atm["B_G"], dtype=np.float64)
+    atm["B_G"][2] = 3000.0
+    exe = _build_exe(tmp_path, "dump", DUMP)
+    at = cfg["atom"]
+    keys = ("z_km", "T_K", "xi_kms", "a", "eps", "r_el", "k_line", "W_T", "B_G", "thetaB", "chiB")
+    lines = [f"{at['twoS']} {at['E_u_cm'][0]!r} {at['E_u_cm'][1]!r} {at['mass_amu']!r} {at['g_s']!r} {len(atm['z_km'])}"]
+    lines += [" ".join(repr(float(x)) for x in np.asarray(atm[k], dtype=np.float64)) for k in keys]
+    lines.append(" ".join(repr(float(x)) for x in np.asarray(atm["v_kms"], dtype=np.float64).ravel()))
+    q = cfg["quad"]
+    lines.append(f"{len(q['grid'])} {q['grid_kind']} {q['n_mu_half']} {q['n_chi']}")
+    lines.append(" ".join(repr(float(x)) for x in q["grid"]))
+    (tmp_path / "problem.txt").write_text("\n".join(lines) + "\n")
+    r = subprocess.run([str(exe), str(tmp_path / "problem.txt")], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    tok = r.stdout.split()
+    nz, nO, nu, nl = map(int, tok[:4])
+    vals = np.array([float(t) for t in tok[4:]])
+    pos = 0
+
+    def take(n):
+        nonlocal pos
+        out = vals[pos:pos + n]
+        pos += n
+        return out
+    dnuD = take(nz)
+    shift = take(nz * nu * nl).reshape(nz, nu, nl)
+    cz = lambda n: take(2 * n).reshape(-1, 2) @ np.array([1.0, 1j])
+    alpha = cz(nz * nu * nu).reshape(nz, nu, nu)
+    beta = cz(nz * nu * nu).reshape(nz, nu, nu)
+    amp = cz(nz * nO * 2 * nu * nl).reshape(nz, nO, 2, nu, nl)
+    assert pos == vals.size
+    P = Problem(cfg, normalise=False)
+    assert P.nO == nO and P.nu_states == nu and P.nl_states == nl
+    assert np.max(np.abs(dnuD / P.dnuD - 1.0)) < 1e-14
+    for iz in range(nz):
+        pl = np.argsort(shift[iz][:, 0], kind="stable")
+        po = np.argsort(P.shift[iz][:, 0], kind="stable")
+        assert np.max(np.abs(shift[iz][pl] - P.shift[iz][po])) < 1e-9 * np.max(np.abs(P.shift[iz]))
+        # energies ~3e12 Hz carry ~6e-4 Hz of rounding; over Gamma ~1e8 s^-1 that is ~4e-11 in alpha
+        assert np.max(np.abs(alpha[iz][np.ix_(pl, pl)] - P.alpha[iz][np.ix_(po, po)])) < 1e-10
+        assert np.max(np.abs(beta[iz][np.ix_(pl, pl)] - P.beta[iz][np.ix_(po, po)])) < 1e-10
+        if P.cfg["atm"]["B_G"][iz] < 1.0:
+            continue                      # near-degenerate states: per-state products are not unique
+        for o, op in ((0, 1), (2, 7), (5, 5)):
+            for kl in range(nl):
+                for klp in range(nl):
+                    ml = np.einsum("au,gu->uag", amp[iz, o, :, :, klp].conj(), amp[iz, op, :, :, kl])[pl]
+                    mo = np.einsum("au,gu->uag", P.amp[iz][o][:, :, klp].conj(), P.amp[iz][op][:, :, kl])[po]
+                    assert np.max(np.abs(ml - mo)) < 1e-12, (iz, o, op, kl, klp)
