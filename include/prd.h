@@ -64,7 +64,7 @@ typedef struct prd_ctx prd_ctx;
  * twoS = 1: S_1/2 -> P_1/2,3/2 two-term atom with J-state interference and
  * Paschen-Back levels).  E_u_cm: upper J-level energies in cm^-1 (J = L-S
  * first; for twoS = 0 only E_u_cm[0] is used).  nu0_hz = 0 selects the
- * (2J+1)-weighted centroid as the reference frequency nu0 (Sect. 2.3). */
+ * (2J+1)-weighted centroid as the reference frequency nu0 (Sect. 2.4). */
 typedef struct {
   int kind;          /* PRD_TWO_LEVEL or PRD_TWO_TERM (must agree with twoS) */
   int twoS;          /* 0 or 1 */
@@ -101,7 +101,7 @@ int prd_set_allocator(prd_ctx* ctx, prd_alloc_fn alloc, prd_free_fn free_fn, voi
 /* Sect. 2.2 / Table 1. */
 int prd_set_atom(prd_ctx* ctx, const prd_atom* atom);
 
-/* Atmosphere on nz >= 2 heights (Sects. 2.3, 2.5, 6.1), each array of
+/* Atmosphere on nz >= 2 heights (Sects. 2.3-2.5, 6.1), each array of
  * length nz except v_kms [nz][3]:
  *   z_km ascending; T_K; xi_kms microturbulence; a damping constant
  *   (Gamma_R+Gamma_I+Gamma_E)/(4 pi dnu_D); eps = Gamma_I/(Gamma_R+Gamma_I)
@@ -117,7 +117,7 @@ int prd_set_atmosphere(prd_ctx* ctx, int nz, const double* z_km, const double* T
                        const double* B_G, const double* thetaB, const double* chiB,
                        const double* v_kms);
 
-/* Frequency and angular quadrature (Sects. 2.5, 4.2).  grid: nnu ascending
+/* Frequency and angular quadrature (Sects. 2.6, 4.2, 4.3).  grid: nnu ascending
  * values, vacuum wavelengths in Angstrom (PRD_GRID_LAMBDA) or reduced
  * frequencies x with nu = nu0 - x dnu_D(z_0) (PRD_GRID_X).  mu_rule
  * PRD_MU_GL_HEMISPHERES puts n_mu_half Gauss-Legendre nodes on each of

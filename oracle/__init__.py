@@ -8,7 +8,7 @@ the method.
 
 The oracle computes, plainly and slowly, the discrete operator the library
 implements, module by module:
-  * faddeeva      W(a,v) = w(v + i a)                 (Sect. 2.3)
+  * faddeeva      W(a,v) = w(v + i a)                 (Sect. 2.4)
   * spline        natural cubic spline, constant extension (Sect. 6.2)
   * geometry      angular grid, scattering angles, polarisation basis (Sect. 4.2)
   * atom          two-level / two-term atom with Paschen-Back levels (Sect. 2.2)

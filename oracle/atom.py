@@ -18,7 +18,7 @@ from .constants import CM_TO_HZ, MU_B_OVER_H, GAUSS
 
 
 def nu0_of(atom):
-    """Reference frequency: (2J+1)-weighted centroid of the upper levels (Sect. 2.3)."""
+    """Reference frequency: (2J+1)-weighted centroid of the upper levels (Sect. 2.4)."""
     if atom.get("nu0_hz", 0.0):
         return float(atom["nu0_hz"])
     E = atom["E_u_cm"]

@@ -3,7 +3,7 @@
 Test infrastructure: only tests/, the smoke check and bench.py's CPU-baseline
 leg may import anything under oracle/.
 
-The paper writes the Voigt-Faraday pair as W(a, v) := w(v + i a) (Sect. 2.3,
+The paper writes the Voigt-Faraday pair as W(a, v) := w(v + i a) (Sect. 2.4,
 F after Eq. G; Eq. RIIIQKKp).  It does not say how W is evaluated, so this
 module follows a named published method: J.A.C. Weideman, "Computation of the
 complex error function", SIAM J. Numer. Anal. 31 (1994) 1497, written here from

@@ -1,7 +1,7 @@
 """R_II-AD kernel F, its Theta = 0 and Theta = pi limits, and the integrals of
 F and of the R_III profiles against the natural-spline basis (oracle).
 
-Sect. 2.3 (after Eq. G):
+Sect. 2.4 (after Eq. G):
     F(Theta, u', u) = 1/sin(Theta) exp[-((u-u')/(2 sin(Theta/2)))^2]
                       W(a/cos(Theta/2), (u+u')/(2 cos(Theta/2)))
 Sect. 4.3 / App. C rule i:  F(0, u, u') = sqrt(pi) delta(u-u') W(a, u').

@@ -92,7 +92,7 @@ def _chromosphere(rng, n_z, T_top_extra, z_lo=-100.0, z_hi=2219.43):
 
 
 def _velocity(z, vmax):
-    """Bulk velocity law of Sect. 6.3 (v_z Gaussian x erf, horizontal 0.7|v_z|
+    """Bulk velocity law of Sect. 6.4 (v_z Gaussian x erf, horizontal 0.7|v_z|
     rotating with height), rescaled to max|v| = vmax km/s."""
     from math import erf
     zmin, zmax = z.min(), z.max()

@@ -68,7 +68,7 @@ def test_number_of_scattering_angles_paper_grid():
 @pytest.mark.parametrize("a", [1e-2, 1e-4])
 def test_F_marginal_is_complex_voigt(theta, a):
     """int F(Theta, x', x) dx' = sqrt(pi) W(a, x) for every Theta: the complex
-    form of Hummer's R_II-A marginal (R_II-A = Re F / pi, Sect. 2.3)."""
+    form of Hummer's R_II-A marginal (R_II-A = Re F / pi, Sect. 2.4)."""
     for x in (0.0, 0.8, -2.5, 4.0):
         g = 2 * np.sin(theta / 2)
         pts = sorted([x, -x])
@@ -275,7 +275,7 @@ def test_generalised_kirchhoff_all_stokes_magnetic():
 
 
 def test_crd_limit():
-    """r_E -> 1 (alpha = 0): R = (1-eps) phi(u') phi(u) x Rayleigh (Sect. 2.3):
+    """r_E -> 1 (alpha = 0): R = (1-eps) phi(u') phi(u) x Rayleigh (Sect. 2.4):
     the I->I part of Sigma_bar is rank one in frequency."""
     P = Problem(_static_twolevel(r_el=1 - 1e-12, n_x=9))
     blk = P.block(1, 0, 5)[:, 0, :, 0]
