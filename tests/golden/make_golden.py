@@ -35,6 +35,9 @@ CASES = {
 SAMPLES = {
     "mgii_full": (lambda: inputs.mgii(), [(35, 45)], [(45, 120), (3, 60)]),
     "twolevel_full": (lambda: inputs.twolevel_slab(), [(20, 5), (0, 2)], [(6, 10), (1, 0)]),
+    # H I Ly-alpha size (90 x 96 x 150): work items with more than 32 incident directions
+    "hi_full": (lambda: inputs.hi_lya(), [(45, 60)], [(60, 75), (5, 10)]),
+    "hi_aa_full": (lambda: inputs.hi_lya(mode=inputs.MODE_AA), [(45, 60)], []),
 }
 
 
