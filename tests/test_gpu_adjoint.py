@@ -158,26 +158,3 @@ def test_grad_B_matches_oracle_finite_differences():
         assert d < 2e-4, f"dJ/d{kind}: {d:.2e}"
     P.close()
 
-
-def test_autograd_field_gradient_matches_oracle():
-    """The same functional and field as the test above, its gradient taken by
-    torch autograd through binding.solve_with_field (the autograd.Function
-    around prd_solve and prd_grad_B), against the same oracle differences and
-    bound."""
-    from paper_2505_20968_gb300.binding import PRD, solve_with_field
-    G = dict(np.load(os.path.join(GOLD, "grad_mgii_small.npz")))
-    cfg = inputs.mgii(n_z=6, n_core_each=5, n_wing=4, n_mu_half=1, n_chi=4, seed=23)
-    P = PRD(cfg, precision="fp64", device=0)
-    top = torch.from_numpy(P.mu > 0)
-    P.close()
-    a = cfg["atm"]
-    field = torch.tensor(np.stack([a["B_G"], a["thetaB"], a["chiB"]], 1), dtype=torch.float64,
-                         requires_grad=True)
-    x = solve_with_field(cfg, field)
-    x[-1, top.to(x.device), :, 0].sum().backward()
-    g = field.grad.numpy()
-    fd = (4.0 * G["fd_half"] - G["fd"]) / 3.0
-    for k, kind in enumerate(("B", "theta_B", "chi_B")):
-        d = np.max(np.abs(g[:, k] - fd[:, k])) / np.max(np.abs(fd[:, k]))
-        print(f"autograd dJ/d{kind}: {d:.2e}")
-        assert d < 2e-4, f"dJ/d{kind}: {d:.2e}"
