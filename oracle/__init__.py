@@ -14,9 +14,10 @@ implements, module by module:
   * atom          two-level / two-term atom with Paschen-Back levels (Sect. 2.2)
   * redistribution  F, G tiles against the spline basis; R_III profiles
                   (Eqs. RQIIKKp, G, RIIIQKKp; App. C)
+  * preconditioner  P = Id - Lambda* Sigma* and its block inverse (Sect. 5.2, App. F)
   * problem       K, eps_th, DELO-linear Lambda, Sigma, Kirchhoff
-                  normalisation, GMRES, emergent Stokes (Sects. 2.6, 3, 4, 5;
-                  App. B, E, F)
+                  normalisation, GMRES, emergent Stokes (Sects. 2.6-2.7, 3, 4, 5;
+                  App. B, E)
                   and the transposed operator A^T = Id - Sigma^T Lambda^T
                   with its GMRES solve (not in the paper: the adjoint)
 """

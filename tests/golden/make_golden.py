@@ -3,7 +3,8 @@
 Calls only oracle/ and the seeded input generator; never the CUDA library.
 Run from the repository root:  python tests/golden/make_golden.py [names...]
 Outputs tests/golden/<name>.npz (forward operator and solution),
-<name>_adj.npz (transposed operator and adjoint solve) and grad_mgii_small.npz
+<name>_adj.npz (transposed operator and adjoint solve), <name>_pc.npz (the
+preconditioner with 1 and 2 sweeps) and grad_mgii_small.npz
 (derivatives of an emergent-intensity functional by central differences of
 forward solves).
 """
@@ -78,6 +79,18 @@ def make_adjoint(name):
                         res=hist[-1])
 
 
+# preconditioner (Sect. 5.2, App. F) applied to a seeded vector with 1 and 2 sweeps
+PRECOND = ("twolevel", "mgii", "hi")
+
+
+def make_precond(name):
+    from oracle.preconditioner import Preconditioner
+    P = Problem(CASES[name](), normalise=False)
+    C = Preconditioner(P)
+    y = inputs.seeded_vector(P.shape(), 11, -1.0, 1.0)
+    np.savez_compressed(os.path.join(HERE, name + "_pc.npz"), y=y, m1=C.apply_inv(y, 1), m2=C.apply_inv(y, 2))
+
+
 # dJ/d(B, theta_B, chi_B) per height for J = sum of the emergent Stokes I
 # (top height, mu > 0, every frequency) of the forward solution: central
 # differences of J at steps h and h/2, h = max(1e-3 |p|, 0.1 G for B, 1e-3 rad)
@@ -136,7 +149,8 @@ def make_sample(name):
 
 
 if __name__ == "__main__":
-    names = sys.argv[1:] or list(CASES) + list(SAMPLES) + [a + "_adj" for a in ADJOINT] + ["grad"]
+    names = sys.argv[1:] or (list(CASES) + list(SAMPLES) + [a + "_adj" for a in ADJOINT] + ["grad"]
+                             + [a + "_pc" for a in PRECOND])
     for nm in names:
         t0 = time.time()
         if nm in CASES:
@@ -145,6 +159,8 @@ if __name__ == "__main__":
             make_sample(nm)
         elif nm.endswith("_adj"):
             make_adjoint(nm[:-4])
+        elif nm.endswith("_pc"):
+            make_precond(nm[:-3])
         elif nm == "grad":
             make_grad()
         else:

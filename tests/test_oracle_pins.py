@@ -392,6 +392,46 @@ def test_sampled_rows_match_the_full_operator():
         assert np.max(np.abs(P.lambda_ray(x, o, n) - lam[:, o, n])) < 1e-14 * np.max(np.abs(lam))
 
 
+@pytest.mark.parametrize("case", ["mgii", "twolevel"])
+def test_preconditioner_oracle(case):
+    """Sect. 5.2 / App. F preconditioner (oracle/preconditioner.py):
+    * one sweep from zero is P_hat^-1, which equals the dense inverse of
+      Id - Lambda_ii Sigma_hat at every height (brute force);
+    * the Richardson sweeps converge to the exact inverse of P: P (P^-1 y) = y;
+    * Q, U, V pass through, and zero sweeps are the identity;
+    * Sigma*'s photon budget: under a flat isotropic field the R_II part of
+      Phi_bar returns alpha0 k phi* exactly (every F integrates to sqrt(pi) W)
+      and the R_III part (beta0 - alpha0) k phi* times the profile's area
+      inside the grid span (adaptive quadrature here)."""
+    from oracle.preconditioner import Preconditioner, _levels
+    if case == "mgii":
+        cfg = inputs.mgii(n_z=4, n_core_each=4, n_wing=4, n_mu_half=1, n_chi=4, seed=19)
+    else:
+        cfg = inputs.twolevel_slab(n_z=6, n_x=9, n_mu_half=1, n_chi=4, eps=1e-2)
+    P = Problem(cfg, normalise=False)
+    C = Preconditioner(P)
+    nz, nO, N = P.nz, P.nO, P.nN
+    y = inputs.seeded_vector(P.shape(), 3, -1.0, 1.0)
+    x1 = C.apply_inv(y, 1)
+    for iz in range(nz):
+        S = np.broadcast_to(C.Phi[iz][None, :, None, :] * P.wang[None, None, :, None], (nO, N, nO, N))
+        B = np.eye(nO * N) - C.lii[iz].ravel()[:, None] * S.reshape(nO * N, nO * N)
+        ref = np.linalg.solve(B, y[iz, ..., 0].ravel())
+        assert np.max(np.abs(x1[iz, ..., 0].ravel() - ref)) < 1e-12 * np.max(np.abs(ref))
+    x = C.apply_inv(y, 60)
+    assert np.linalg.norm(C.apply_P(x) - y) < 1e-12 * np.linalg.norm(y)
+    assert np.array_equal(x[..., 1:], y[..., 1:]) and np.array_equal(C.apply_inv(y, 0), y)
+    E, cg = _levels(P.atom, P.nu0)
+    for iz in range(nz):
+        a, u = P.a[iz], P.u[iz]
+        prof = lambda v: sum(c * voigt_faraday(a, v + Eg / P.dnuD[iz]).real for Eg, c in zip(E, cg)) / np.sqrt(np.pi)
+        span = quad(prof, u[0], u[-1], limit=400, points=[-Eg / P.dnuD[iz] for Eg in E], epsabs=1e-13)[0]
+        a0 = (1 - P.eps[iz]) * (1 - P.rE[iz])
+        b0 = 1 - P.eps[iz]
+        ref = P.k[iz] * prof(u) * (a0 + (b0 - a0) * span)
+        assert np.max(np.abs(C.Phi[iz].sum(axis=1) - ref)) < 1e-9 * np.max(ref)
+
+
 def test_gmres_matches_dense_solve():
     """Brute force on a tiny grid: assemble A column by column, solve by LU;
     the same for A^T and the adjoint solve."""
