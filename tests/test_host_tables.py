@@ -248,3 +248,74 @@ def test_atom_tables_match_the_oracle(tmp_path):
                     ml = np.einsum("au,gu->uag", amp[iz, o, :, :, klp].conj(), amp[iz, op, :, :, kl])[pl]
                     mo = np.einsum("au,gu->uag", P.amp[iz][o][:, :, klp].conj(), P.amp[iz][op][:, :, kl])[po]
                     assert np.max(np.abs(ml - mo)) < 1e-12, (iz, o, op, kl, klp)
+
+
+LOS = DUMP.replace('''  const int nu = c->nu_st, nl = c->nl_st, nO = c->nO;
+  std::printf("%d %d %d %d\\n", nz, nO, nu, nl);
+  for (int iz = 0; iz < nz; ++iz) std::printf("%.17g\\n", c->dnuD[iz]);
+  for (double x : c->shift) std::printf("%.17g\\n", x);
+  for (auto z : c->alpha) std::printf("%.17g %.17g\\n", z.real(), z.imag());
+  for (auto z : c->beta) std::printf("%.17g %.17g\\n", z.real(), z.imag());
+  for (auto z : c->amp) std::printf("%.17g %.17g\\n", z.real(), z.imag());''', '''  prd::LosTables L;
+  const double mu = std::atof(argv[2]), chi = std::atof(argv[3]);
+  prd::los_tables(c, mu, chi, L);
+  std::printf("%d %d\\n", nz, nnu);
+  for (double x : L.kt) std::printf("%.17g\\n", x);
+  for (double x : L.epsth) std::printf("%.17g\\n", x);''').replace("#include <cstdio>", "#include <cstdio>\n#include <cstdlib>")
+
+
+def test_line_of_sight_tables_match_the_oracle(tmp_path):
+    """S11 host tables of an off-grid line of sight (los_tables in
+    csrc/host_tables.cpp) against the oracle's emergent-Stokes set-up, on
+    magnetised Mg II physics with bulk velocities: the propagation matrix K
+    (absorption and magneto-optical terms, Sect. 2.1; from the forward
+    scattering amplitudes) as K_ij / eta_I and 1 / eta_I, the thermal
+    emissivity eps W_T K[:, 0] (Sect. 2.3) and the DELO-linear weights of
+    every step along the line of sight (Sect. 3)."""
+    import numpy as np
+    from paper_2505_20968_gb300 import inputs
+    from oracle.problem import Problem, delo_coeffs
+    from oracle.geometry import unit_vector
+    cfg = inputs.mgii(n_z=4, n_core_each=4, n_wing=4, n_mu_half=1, n_chi=4, seed=17)
+    cfg["atm"]["B_G"] = np.array(cfg["atm"]["B_G"], dtype=np.float64)
+    cfg["atm"]["B_G"][1] = 800.0
+    exe = _build_exe(tmp_path, "los", LOS)
+    at, atm, q = cfg["atom"], cfg["atm"], cfg["quad"]
+    keys = ("z_km", "T_K", "xi_kms", "a", "eps", "r_el", "k_line", "W_T", "B_G", "thetaB", "chiB")
+    lines = [f"{at['twoS']} {at['E_u_cm'][0]!r} {at['E_u_cm'][1]!r} {at['mass_amu']!r} {at['g_s']!r} {len(atm['z_km'])}"]
+    lines += [" ".join(repr(float(x)) for x in np.asarray(atm[k], dtype=np.float64)) for k in keys]
+    lines.append(" ".join(repr(float(x)) for x in np.asarray(atm["v_kms"], dtype=np.float64).ravel()))
+    lines.append(f"{len(q['grid'])} {q['grid_kind']} {q['n_mu_half']} {q['n_chi']}")
+    lines.append(" ".join(repr(float(x)) for x in q["grid"]))
+    (tmp_path / "problem.txt").write_text("\n".join(lines) + "\n")
+    P = Problem(cfg, normalise=False)
+    nz, N = P.nz, P.nN
+    v = np.asarray(atm["v_kms"], dtype=np.float64)
+    for mu, chi in ((0.3, 0.7), (0.95, 4.0)):
+        r = subprocess.run([str(exe), str(tmp_path / "problem.txt"), repr(mu), repr(chi)],
+                           capture_output=True, text=True, timeout=120)
+        assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+        tok = r.stdout.split()
+        assert (int(tok[0]), int(tok[1])) == (nz, N)
+        vals = np.array([float(t) for t in tok[2:]])
+        kt = vals[:nz * N * 10].reshape(nz, N, 10)
+        epsth = vals[nz * N * 10:].reshape(nz, N, 4)
+        n_l = unit_vector(np.array([mu]), np.array([chi]))[0]
+        K = np.stack([P.K_from_kappa(P.kappa(iz, P.amplitudes(iz, mu, chi), (v[iz] @ n_l) / P.vD_kms[iz], P.u[iz]))
+                      for iz in range(nz)])                           # [z][n][4][4]
+        e1 = K[..., 0, 0]
+        ref = np.stack([K[..., 0, 1], K[..., 0, 2], K[..., 0, 3], K[..., 1, 2], K[..., 1, 3], K[..., 2, 3]], -1)
+        # Far in the wings eta_I is ~1e-9 of its core value, and both sides' Faddeeva values
+        # carry ~1e-15 |w| of absolute error, i.e. up to ~1e-9 relative in H = Re w (|w| / H ~ v / a);
+        # the magneto-optical ratios there are differences of nearly equal dispersion profiles.
+        # K / eta_I multiplies I in the transfer equation: 1e-8 relative plus 1e-9 absolute.
+        r = ref / e1[..., None]
+        assert np.all(np.abs(kt[..., :6] - r) <= 1e-8 * np.abs(r) + 1e-9)
+        assert np.max(np.abs(kt[..., 6] * e1 - 1.0)) < 1e-8
+        eth = (P.eps * P.WT)[:, None, None] * K[..., :, 0]
+        assert np.max(np.abs(epsth - eth)) < 1e-12 * np.max(np.abs(eth))
+        dtau = 0.5 * (e1[:-1] + e1[1:]) * np.diff(P.z)[:, None] / mu
+        e, al, be = delo_coeffs(dtau)
+        # the optical depths inherit eta_I's far-wing difference (~1e-9 relative)
+        for got, want in ((kt[1:, :, 7], e), (kt[1:, :, 8], al), (kt[1:, :, 9], be)):
+            assert np.max(np.abs(got - want)) < 1e-10
