@@ -355,3 +355,79 @@ def test_host_faddeeva_against_scipy(tmp_path):
         assert abs(L - ref.imag) <= 1e-14 * abs(ref) + 1e-300, (v, a)
         bound = 1e-12 if abs(v) <= 2.0 else max(1e-12, 1e-14 * abs(v) / a)
         assert abs(H - ref.real) <= bound * abs(ref.real), (v, a, abs(H - ref.real) / abs(ref.real))
+
+
+YDUMP = DUMP.replace('''  const int nu = c->nu_st, nl = c->nl_st, nO = c->nO;
+  std::printf("%d %d %d %d\\n", nz, nO, nu, nl);
+  for (int iz = 0; iz < nz; ++iz) std::printf("%.17g\\n", c->dnuD[iz]);
+  for (double x : c->shift) std::printf("%.17g\\n", x);
+  for (auto z : c->alpha) std::printf("%.17g %.17g\\n", z.real(), z.imag());
+  for (auto z : c->beta) std::printf("%.17g %.17g\\n", z.real(), z.imag());
+  for (auto z : c->amp) std::printf("%.17g %.17g\\n", z.real(), z.imag());''', '''  prd::LosTables L;
+  const double mu = std::atof(argv[2]), chi = std::atof(argv[3]);
+  prd::los_tables(c, mu, chi, L);
+  const int nu = c->nu_st, nl = c->nl_st, nO = c->nO, nt = c->ntrip, ng = c->ngrp;
+  std::printf("%d %d %d %d %d %d\\n", nz, nO, nu, nl, nt, ng);
+  for (int t = 0; t < nt; ++t) std::printf("%d %d %d\\n", c->trip_k[t], c->trip_l[t], c->trip_lp[t]);
+  for (double x : c->shift) std::printf("%.17g\\n", x);
+  for (double x : L.theta) std::printf("%.17g\\n", x);
+  for (double x : L.Y) std::printf("%.17g\\n", x);''').replace("#include <cstdio>", "#include <cstdio>\n#include <cstdlib>")
+
+
+def test_rii_coefficients_rebuild_the_oracle_block(tmp_path):
+    """S3+S4 regrouping: the library writes R_II between a line of sight and a
+    grid direction as Re sum_t Y^t G_t over triples t = (k, k_l, k_l') (one
+    coefficient matrix per triple, Eq. RQIIKKp with the amplitude products
+    factorised), the oracle as the trace over upper-state pairs with
+    alpha [G(k_u') + G(k_u)^*].  Y^t from los_tables, combined with the oracle's
+    own tiles G_t, must rebuild the oracle's comoving block (R_III switched off
+    by r_E = 0, so that beta = alpha), on magnetised Mg II physics."""
+    import numpy as np
+    from paper_2505_20968_gb300 import inputs
+    from oracle.problem import Problem
+    from oracle.geometry import unit_vector, scattering_angle
+    cfg = inputs.mgii(n_z=3, n_core_each=4, n_wing=3, n_mu_half=1, n_chi=4, seed=29)
+    atm = cfg["atm"]
+    atm["r_el"] = np.zeros(3)
+    atm["B_G"] = np.array([40.0, 700.0, 5.0])
+    exe = _build_exe(tmp_path, "ydump", YDUMP)
+    at, q = cfg["atom"], cfg["quad"]
+    keys = ("z_km", "T_K", "xi_kms", "a", "eps", "r_el", "k_line", "W_T", "B_G", "thetaB", "chiB")
+    lines = [f"{at['twoS']} {at['E_u_cm'][0]!r} {at['E_u_cm'][1]!r} {at['mass_amu']!r} {at['g_s']!r} {len(atm['z_km'])}"]
+    lines += [" ".join(repr(float(x)) for x in np.asarray(atm[k], dtype=np.float64)) for k in keys]
+    lines.append(" ".join(repr(float(x)) for x in np.asarray(atm["v_kms"], dtype=np.float64).ravel()))
+    lines.append(f"{len(q['grid'])} {q['grid_kind']} {q['n_mu_half']} {q['n_chi']}")
+    lines.append(" ".join(repr(float(x)) for x in q["grid"]))
+    (tmp_path / "problem.txt").write_text("\n".join(lines) + "\n")
+    mu, chi = 0.4, 2.2
+    r = subprocess.run([str(exe), str(tmp_path / "problem.txt"), repr(mu), repr(chi)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    tok = r.stdout.split()
+    nz, nO, nu, nl, nt, ng = map(int, tok[:6])
+    pos = 6
+    trip = np.array(tok[pos:pos + 3 * nt], dtype=int).reshape(nt, 3)
+    pos += 3 * nt
+    vals = np.array([float(s) for s in tok[pos:]])
+    shift = vals[:nz * nu * nl].reshape(nz, nu, nl)
+    theta = vals[nz * nu * nl:nz * nu * nl + nO]
+    Y = vals[nz * nu * nl + nO:].reshape(nz, nO, ng + nt, 4, 4, 2)
+    Y = Y[..., 0] + 1j * Y[..., 1]
+    P = Problem(cfg, normalise=False)
+    N = P.nN
+    n_l = unit_vector(np.array([mu]), np.array([chi]))[0]
+    for iz in range(nz):
+        pl = np.argsort(shift[iz][:, 0], kind="stable")
+        po = np.argsort(P.shift[iz][:, 0], kind="stable")
+        to_oracle = dict(zip(pl, po))                      # library upper state -> oracle state
+        amp = P.amplitudes(iz, mu, chi)
+        for op in (1, 6):
+            th = scattering_angle(n_l, P.nvec[op])
+            assert abs(th - theta[op]) < 1e-12
+            ref = P.block(iz, None, op, amp_o=amp, theta=th).reshape(N, 4, N, 4)
+            rebuilt = np.zeros((N, 4, N, 4))
+            for t, (k, l, lp) in enumerate(trip):
+                ku = to_oracle[k]
+                G = P.tile(iz, th, P.shift[iz][ku, l], P.shift[iz][ku, lp])
+                rebuilt += np.einsum("ij,nm->nimj", Y[iz, op, ng + t], G).real
+            assert np.max(np.abs(rebuilt - ref)) < 1e-10 * np.max(np.abs(ref)), (iz, op)
