@@ -19,6 +19,9 @@ with alpha, beta the branching ratios of App. B, G = F evaluated at the
 shifted reduced frequencies (Eq. G), Stokes I = Tr(rho), Q = Tr(sigma_z rho),
 U = Tr(sigma_x rho), V = S_V Tr(sigma_y rho) and rho the coherency matrix of
 (E_a, E_b).  The factor 3/2 makes oint R_11 = (1 - eps) phi at B = 0 (App. E).
+The conjugate pairing of R^II is pinned by the Kramers-Heisenberg limit of a
+single atom (tests); R^III uses the same conventions, but its own pairing is
+parity unpinned (no test fixes it separately).
 
 Propagation matrix from the forward-scattering amplitude (LL04 Ch. 7, cited in
 Sect. 2.2): kappa = k/(2 sqrt(pi)(2S+1)) sum_{k_u k_l} (a_l^*)(a_l)^T W(x)^*,
