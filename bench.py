@@ -167,8 +167,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = inputs.mgii(seed=2 + rank) if args.workload == "mgii" else inputs.mgii(n_z=8, seed=2 + rank)
-    workload = {"workload": "mgii_hk_like: two-term Mg II h&k, 70 heights, 200 wavelengths, "
-                            "4+4 GL mu x 8 chi (64 directions), B<=100 G, |v|<=5 km/s, N=3,584,000",
+    nz, nnu = len(cfg["atm"]["z_km"]), len(cfg["quad"]["grid"])
+    nmu, nchi = cfg["quad"]["n_mu_half"], cfg["quad"]["n_chi"]
+    workload = {"workload": f"mgii_hk_like: two-term Mg II h&k, {nz} heights, {nnu} wavelengths, "
+                            f"{nmu}+{nmu} GL mu x {nchi} chi ({2 * nmu * nchi} directions), B<=100 G, |v|<=5 km/s, "
+                            f"N={4 * nz * nnu * 2 * nmu * nchi:,}",
                 "precision": "fp32 tiles/vectors, fp64 reductions", "parallelism": f"{world} independent instances",
                 "l2": "inputs larger than L2 (R_II tiles ~40 GB streamed per apply)"}
     if args.impl == "reference":
