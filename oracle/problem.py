@@ -20,8 +20,15 @@ shifted reduced frequencies (Eq. G), Stokes I = Tr(rho), Q = Tr(sigma_z rho),
 U = Tr(sigma_x rho), V = S_V Tr(sigma_y rho) and rho the coherency matrix of
 (E_a, E_b).  The factor 3/2 makes oint R_11 = (1 - eps) phi at B = 0 (App. E).
 The conjugate pairing of R^II is pinned by the Kramers-Heisenberg limit of a
-single atom (tests); R^III uses the same conventions, but its own pairing is
-parity unpinned (no test fixes it separately).
+single atom (tests); both brackets of R^III are pinned against R^II: under
+incident light flat in frequency the two emit the same spectrum, and
+integrated over the outgoing frequency they absorb alike (tests).  At B = 0
+and v = 0 the point-valued R is symmetric, R(nu, Omega; nu', Omega') =
+R(nu', Omega'; nu, Omega)^T (tests).  The polarised DELO-linear step converges
+at second order to the matrix-exponential solution of a homogeneous slab
+(tests).
+
+Test infrastructure only: nothing in the library imports or calls this module.
 
 Propagation matrix from the forward-scattering amplitude (LL04 Ch. 7, cited in
 Sect. 2.2): kappa = k/(2 sqrt(pi)(2S+1)) sum_{k_u k_l} (a_l^*)(a_l)^T W(x)^*,
