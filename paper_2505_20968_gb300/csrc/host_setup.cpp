@@ -241,12 +241,12 @@ int build_host_tables(Ctx* c) {
   // AA Theta rule: composite GL on [0, pi/2] and [pi/2, pi]
   if (c->mode == PRD_MODE_AA) {
     std::vector<double> x, w;
-    gauss_legendre(32, x, w);
+    gauss_legendre(kAAThetaNodes, x, w);
     c->aa_theta.clear();
     c->aa_w.clear();
     for (int h = 0; h < 2; ++h) {
       const double lo = h * 0.5 * kPi, hi = lo + 0.5 * kPi;
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < kAAThetaNodes; ++i) {
         const double t = 0.5 * (hi - lo) * x[i] + 0.5 * (hi + lo);
         c->aa_theta.push_back(t);
         c->aa_w.push_back(0.5 * 0.5 * (hi - lo) * w[i] * std::sin(t));

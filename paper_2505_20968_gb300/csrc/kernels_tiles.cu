@@ -80,7 +80,9 @@ __device__ void interval_moments(int kind, double theta, double s2, double c2, d
       w = fmin(hG, fmax(0.25 * hV, 0.5 * dist));
       if (uV > xl && uV < x1) {
         const double gap = uV - xl;
-        w = (gap > 0.25 * hV) ? fmin(w, fmax(0.5 * gap, 0.25 * hV)) : gap;
+        // never wider than the Gaussian limit: a panel that stopped at the W centre
+        // but spanned several Gaussian widths was under-resolved by 8 nodes
+        w = (gap > 0.25 * hV) ? fmin(w, fmax(0.5 * gap, 0.25 * hV)) : fmin(w, gap);
       }
     } else {
       // R_III profiles: smooth on scale 1 around -s1, -s2
@@ -497,10 +499,10 @@ int launch_pc_tiles(Ctx* c, const std::vector<double>& shift_g, std::vector<doub
   if (rc) return rc;
   const int nz = c->nz, N = c->nnu, ng = c->ngrp;
   std::vector<double> x, w, th, tw;
-  gauss_legendre(32, x, w);
+  gauss_legendre(kAAThetaNodes, x, w);
   for (int h = 0; h < 2; ++h) {
     const double lo = h * 0.5 * kPi, hi = lo + 0.5 * kPi;
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < kAAThetaNodes; ++i) {
       const double t = 0.5 * (hi - lo) * x[i] + 0.5 * (hi + lo);
       th.push_back(t);
       tw.push_back(0.5 * 0.5 * (hi - lo) * w[i] * std::sin(t));

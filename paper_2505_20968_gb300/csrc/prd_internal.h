@@ -24,6 +24,9 @@ constexpr double kSqrtPi = 1.77245385090551602730;
 
 constexpr int kWeidemanN64 = 36;   // Faddeeva expansion terms, FP64 paths
 constexpr int kWeidemanN32 = 20;   // Faddeeva expansion terms, FP32 paths
+// Angle-averaged R_II (Eq. R_AA): composite Gauss-Legendre in Theta with this
+// many nodes on each of [0, pi/2] and [pi/2, pi]
+constexpr int kAAThetaNodes = 48;
 
 // device buffer with byte size
 struct DBuf {
@@ -35,6 +38,9 @@ struct DBuf {
 
 struct Ctx {
   int device = 0;
+  int nsm = 1;                  // streaming multiprocessors of the device (queried at create)
+  // grid of the grid-stride elementwise and reduction kernels: 4 CTAs per SM
+  int grid_ew() const { return 4 * (nsm > 0 ? nsm : 1); }
   int prec = PRD_FP32;
   size_t esz = 4;               // element size of vectors (4 or 8)
   cudaStream_t stream = nullptr;
@@ -96,6 +102,8 @@ struct Ctx {
   DBuf tiles64, Y64, r3w64, r3in64, r3out64, r3prof64, r3ab64;
   bool has64 = false;
   bool op_transpose = false;   // GMRES iterates with A^T (adjoint solve)
+  int test_zero_op = 0;        // GMRES iterates with the zero map (failure injection for tests)
+  double refine_floor = 3e-5;  // FP32 refinement: floor of the inner GMRES relative tolerance
   int ld64() const { return (2 * nnu + 3) / 4 * 4; }
   DBuf tiles;        // [z][c][t][n][2N]    (T)
   DBuf Y;            // [z][pair][t][16]    complex (T2)
@@ -116,12 +124,12 @@ struct Ctx {
   DBuf dmu;          // [nO] mu of each direction (double)
   DBuf scratch1, scratch2, scratch3;  // N-vector scratch (T)
   // preconditioner
-  DBuf pc_phi;       // [z][N][N] Phi_bar (T)
-  DBuf pc_M;         // [z][N][N] Phi_bar (Id - A)^-1 (T)
+  DBuf pc_phi;       // [z][N][N] Phi_bar (double)
+  DBuf pc_M;         // [z][N][N] Phi_bar (Id - A)^-1 (double)
   DBuf pc_lii;       // [z][o][n] Lambda_ii (T)
   DBuf pc_eta;       // [z][o][n]: eta1 (T)  (scalar Lambda*)
   DBuf pc_delo;      // [z][o][n][3] (T)
-  DBuf pc_s1, pc_s2, pc_s3;   // scalar N/4 scratch
+  DBuf pc_s1, pc_s2, pc_s3, pc_s4, pc_s5;   // FP64 N-vector scratch of the sweeps
   std::vector<double> pc_lii_host;
   void* pc_w = nullptr;   // device angular weights (double), owned via `owned`
   // GMRES
@@ -137,6 +145,7 @@ struct Ctx {
   int tc_nwork = 0;
   bool tc_ready = false;
   int use_tc = 0;
+  long long tc_spin = 0;   // poll limit of the contraction's pipeline waits (0: the default)
   // stage timing (prd_set_profiling): events on the ctx stream around each stage
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -206,6 +215,8 @@ int rhs(Ctx* c, void* b);
 int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x, int* iters,
           double* true_res, double* hist);
 int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, void* out);
+int narrowband(Ctx* c, const void* x, int nlos, const double* mu, const double* chi, double lam0, double fwhm,
+               double half, double* out);
 int upload_faddeeva_coeffs(Ctx* c);
 
 size_t nvec(const Ctx* c);   // 4*nz*nO*nnu

@@ -49,16 +49,18 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("name,prec,tol", [("twolevel", "fp64", 1e-8), ("mgii", "fp64", 1e-8),
-                                           ("hi", "fp64", 1e-8), ("hi_aa", "fp64", 1e-8),
+@pytest.mark.parametrize("name,prec,tol", [("twolevel", "fp64", 1e-9), ("mgii", "fp64", 1e-9),
+                                           ("hi", "fp64", 1e-9), ("hi_aa", "fp64", 1e-9),
                                            ("mgii", "fp32", 1e-6), ("hi", "fp32", 1e-6)])
 def test_transpose_matches_oracle(name, prec, tol):
     """A^T y against the oracle, element by element, within a bound of
-    max|A^T y|.  FP64 mode: 1e-8.  The library and the oracle integrate the
-    redistribution tiles by different quadratures, each within 1e-9 of the
-    exact integral (App. C; the oracle's is pinned against adaptive
-    Gauss-Kronrod); measured 7e-12 (two-level), 2e-12 (H I), 1.7e-10 (Mg II),
-    1.5e-9 (H I, angle-averaged).  FP32 mode: 1e-6.  A^T runs in FP64 on the
+    max|A^T y|.  FP64 mode: 1e-9.  The library and the oracle integrate the
+    redistribution tiles over the incident frequency by different
+    quadratures, each within 1e-9 of the exact integral (App. C; the oracle's
+    is pinned against adaptive Gauss-Kronrod), and the angle-averaged tiles
+    (Eq. R_AA) with the same Theta rule (composite Gauss-Legendre, 48 nodes
+    on each half of [0, pi]); measured before the Theta rules were aligned:
+    7e-12 (two-level), 2e-12 (H I), 1.7e-10 (Mg II).  FP32 mode: 1e-6.  A^T runs in FP64 on the
     FP64 copy of the tables, and only the FP32 input and output vectors are
     rounded (2^-24 each); measured 3.8e-8."""
     from paper_2505_20968_gb300.binding import PRD
