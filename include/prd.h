@@ -205,8 +205,24 @@ int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
 
 /* Options.  PRD_OPT_TENSOR_CORES (FP32 only): 1 runs the R_II contraction on
  * the tcgen05 tensor cores (TMA-fed tiles, TMEM accumulators, 3xTF32 split
- * products), 0 on the CUDA cores.  PRD_OPT_PRECOND_SWEEPS: m_in as above. */
-enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2 };
+ * products), 0 on the CUDA cores.  PRD_OPT_PRECOND_SWEEPS: m_in as above.
+ * PRD_OPT_WAIT_POLLS: poll limit of the tensor-core contraction's pipeline
+ * waits (0: the default, 2^24 polls, about a second).  A wait that runs out
+ * makes its thread block stop, drain the copies and products it issued
+ * (those waits keep the default limit) and report PRD_E_TIMEOUT through
+ * prd_device_status; the output of that apply is invalid and the context
+ * stays usable.  A small limit is for testing that failure path.
+ * PRD_OPT_TEST_ZERO_OPERATOR: 1 makes prd_solve and prd_solve_adjoint iterate
+ * with the zero map instead of the operator (failure injection: the first
+ * Arnoldi step breaks down and an unconverged solve returns PRD_E_BREAKDOWN);
+ * 0 restores the operator.
+ * PRD_OPT_REFINE_FLOOR (FP32 mode): the floor of the relative tolerance of
+ * each inner FP32 GMRES solve of the mixed-precision refinement, in units of
+ * 1e-8 (default 3000: 3e-5); the inner tolerance is max(0.3 tol / res, floor)
+ * with res the current FP64 relative residual.  It trades outer FP64
+ * residuals against inner iterations, never the accuracy of the result. */
+enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2, PRD_OPT_WAIT_POLLS = 3, PRD_OPT_TEST_ZERO_OPERATOR = 4,
+       PRD_OPT_REFINE_FLOOR = 5 };
 int prd_set_option(prd_ctx* ctx, int option, int value);
 /* Synchronise the ctx stream and report device-side failures: a CUDA error,
  * or PRD_E_TIMEOUT if a bounded wait inside a kernel expired since the last
@@ -230,6 +246,20 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
 int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu,
                         const double* chi, void* out_dev);
 
+/* Wavelength-integrated narrow-band Stokes signals (Sect. 6.5, centre-to-limb
+ * variation): for each line of sight (mu in (0, 1], any chi) the emergent
+ * Stokes profiles of the solution x_dev (as prd_emergent_stokes) weighted by a
+ * Gaussian of full width at half maximum fwhm_A centred on lambda0_A and
+ * integrated over [lambda0_A - half_width_A, lambda0_A + half_width_A]
+ * (Angstrom, vacuum), normalised by 1/(sqrt(2 pi) sigma):
+ *     out[l][s] = 1/(sqrt(2 pi) sigma) int exp(-(lambda - lambda0)^2/(2 sigma^2)) X_s(mu_l, lambda) dlambda.
+ * X between the wavelength nodes is its natural cubic spline in lambda and
+ * beyond the grid its end value.  out: host array [nlos][4] (I, Q, U, V),
+ * FP64.  Synchronous.  PRD_E_ARG for fwhm or half width <= 0 or mu outside
+ * (0, 1]. */
+int prd_narrowband(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu, const double* chi,
+                   double lambda0_A, double fwhm_A, double half_width_A, double* out);
+
 /* Same result as prd_apply_sigma, for callers that must not allocate device
  * memory at call time: code that runs while another framework owns the
  * allocator, inside allocation-free real-time or replay loops, or in
@@ -238,12 +268,17 @@ int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double*
  * its intermediates (comoving field, spline second derivatives, comoving
  * emissivity, R_III moments) live in one static device array of 64 MiB that
  * every GPU which loads the library holds until the process exits.  A problem
- * whose intermediates need more than 64 MiB is rejected with PRD_E_ARG.  The
- * first call on a device looks up that array's device address (once per
- * device); make that first call before any stream capture.  Every call shares
- * the array and overwrites it, so calls that overlap on the GPU (other
- * streams, other contexts on the same device) race.  The paper has no
- * counterpart: this is a deployment variant of the Sigma apply. */
+ * whose intermediates need more than 64 MiB is rejected with PRD_E_ARG.  Each
+ * call looks up the array's device address in the current context (no
+ * allocation; it stays valid if the device is reset in between); the first
+ * call on a device may load the library's device code, so make it before any
+ * stream capture.  Every call shares the array and overwrites it, so calls
+ * that overlap on the GPU (other streams, other contexts on the same device)
+ * race.  PRD_OK means the work was queued: in FP32 mode the tensor-core
+ * contraction reports an expired bounded wait only through
+ * prd_device_status, which the caller checks after the stream completes, as
+ * for prd_apply_sigma.  The paper has no counterpart: this is a deployment
+ * variant of the Sigma apply. */
 int prd_apply_sigma_noalloc(prd_ctx* ctx, const void* x_dev, void* eps_dev);
 
 /* Stage timing (tracing).  When on, CUDA events recorded on the ctx stream

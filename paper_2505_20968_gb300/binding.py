@@ -40,7 +40,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
            "prd_device_status", "prd_contraction_work",
            "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch",
-           "prd_grad_B", "prd_set_allocator"]
+           "prd_grad_B", "prd_set_allocator", "prd_narrowband"]
 
 
 def lib():
@@ -80,6 +80,7 @@ def lib():
         L.prd_set_precond_sweeps.argtypes = [P, I]
         L.prd_solve.argtypes = [P, D, I, I, P, P, ctypes.POINTER(I), DP, DP]
         L.prd_emergent_stokes.argtypes = [P, P, I, DP, DP, P]
+        L.prd_narrowband.argtypes = [P, P, I, DP, DP, D, D, D, DP]
         L.prd_set_profiling.argtypes = [P, I]
         L.prd_set_option.argtypes = [P, I, I]
         L.prd_device_status.argtypes = [P]
@@ -99,8 +100,9 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 def _torch_allocator(device, stats):
     """prd_set_allocator callbacks backed by PyTorch's caching allocator;
-    stats counts the bytes handed out and the pointers still live."""
+    stats counts the calls, the bytes handed out and the pointers still live."""
     def alloc(nbytes, user, stream):
+        stats["n_alloc"] += 1
         try:
             p = torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=int(stream or 0))
         except Exception:   # out of memory: the library reports PRD_E_NOMEM
@@ -110,6 +112,7 @@ def _torch_allocator(device, stats):
         return p
 
     def free(ptr, user):
+        stats["n_free"] += 1
         stats["live"].pop(int(ptr), None)
         torch.cuda.caching_allocator_delete(int(ptr))
     return _ALLOC_FN(alloc), _FREE_FN(free)
@@ -143,7 +146,7 @@ class PRD:
         self._check(L.prd_set_quadrature(self.h, len(g), gp, q["grid_kind"], q["n_mu_half"], q["n_chi"],
                                          q.get("mu_rule", 0), q.get("mode", 0) if mode is None else mode))
         self._alloc = None
-        self.alloc_stats = {"bytes": 0, "live": {}}
+        self.alloc_stats = {"bytes": 0, "live": {}, "n_alloc": 0, "n_free": 0}
         if allocator == "torch":
             self._alloc = _torch_allocator(device, self.alloc_stats)   # kept alive as long as the ctx
             self._stream()
@@ -287,6 +290,17 @@ class PRD:
         chi, chip = _dp(chi)
         out = torch.empty((len(mu), self.nN, 4), dtype=self.dtype, device=self.device) if out is None else out
         self._check(lib().prd_emergent_stokes(self.h, self._vec(x), len(mu), mup, chip, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def narrowband(self, x, mu, chi, lambda0, fwhm, half_width):
+        """Gaussian-weighted wavelength integrals of the emergent Stokes
+        vectors along lines of sight (mu, chi): array [nlos][4] (Sect. 6.5)."""
+        self._stream()
+        mu, mup = _dp(mu)
+        chi, chip = _dp(chi)
+        out = np.zeros((len(mu), 4))
+        self._check(lib().prd_narrowband(self.h, self._vec(x), len(mu), mup, chip, lambda0, fwhm, half_width,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
     STAGES = ("S1_interp_in", "S5_R3", "S3_R2_contraction", "S6_interp_back", "S7_delo")

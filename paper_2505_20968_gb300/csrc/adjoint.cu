@@ -352,7 +352,7 @@ int apply_operator_t(Ctx* c, const void* x, void* y) {
   }
   const double* xd = (const double*)x;
   if (fp32) {
-    to_f64_kernel<<<608, 256, 0, c->stream>>>((const float*)x, (double*)x64.p, nv);
+    to_f64_kernel<<<c->grid_ew(), 256, 0, c->stream>>>((const float*)x, (double*)x64.p, nv);
     xd = (const double*)x64.p;
   }
   // Lambda^T
@@ -391,7 +391,7 @@ int apply_operator_t(Ctx* c, const void* x, void* y) {
                                                          (double*)ybr.p, (double*)mbr.p, nz, nO, N);
   rows_to_vec_kernel<<<cdiv((long long)nrows * N, 256), 256, 0, c->stream>>>((const double*)ybr.p, (double*)g1.p,
                                                                               nrows, N);
-  sub_out_kernel<<<608, 256, 0, c->stream>>>(xd, (const double*)g1.p, y, nv, fp32 ? 1 : 0);
+  sub_out_kernel<<<c->grid_ew(), 256, 0, c->stream>>>(xd, (const double*)g1.p, y, nv, fp32 ? 1 : 0);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cleanup();

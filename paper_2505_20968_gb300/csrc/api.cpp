@@ -65,7 +65,7 @@ static void free_all(Ctx* c) {
   DBuf* bufs[] = {&c->tiles, &c->Y, &c->r3w, &c->r3in, &c->r3out, &c->r3prof, &c->r3J, &c->r3ab, &c->kt,
                   &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk, &c->cls_dev, &c->dmu,
                   &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
-                  &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
+                  &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
                   &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64, &c->r3out64,
                   &c->r3prof64, &c->r3ab64};
   c->has64 = false;
@@ -189,6 +189,10 @@ int prd_create(prd_ctx** out, int device, int precision) {
   h->c.prec = precision;
   h->c.esz = precision == PRD_FP64 ? 8 : 4;
   h->c.use_tc = precision == PRD_FP32 ? 1 : 0;   // tcgen05 contraction by default in FP32
+  if (cudaDeviceGetAttribute(&h->c.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete h;
+    return PRD_E_CUDA;
+  }
   *out = h;
   return PRD_OK;
 }
@@ -330,7 +334,7 @@ int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
                              &c->kt, &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk,
                              &c->cls_dev, &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M,
                              &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t, &c->dmu, &c->pc_s1, &c->pc_s2,
-                             &c->pc_s3, &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64,
+                             &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64,
                              &c->r3out64, &c->r3prof64, &c->r3ab64};
   int64_t s = 0;
   for (auto* b : bufs) s += (int64_t)b->bytes;
@@ -516,6 +520,23 @@ int prd_emergent_stokes(prd_ctx* ctx, const void* x_dev, int nlos, const double*
   }
 }
 
+int prd_narrowband(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu, const double* chi, double lambda0_A,
+                   double fwhm_A, double half_width_A, double* out) {
+  CTX_OR_ARG(ctx);
+  NEED_READY();
+  if (!x_dev || !out || nlos < 1 || !mu || !chi) return fail(c, PRD_E_ARG, "bad narrowband arguments");
+  if (!(fwhm_A > 0) || !(half_width_A > 0) || !std::isfinite(lambda0_A))
+    return fail(c, PRD_E_ARG, "narrowband needs fwhm > 0, half width > 0 and a finite centre");
+  NEED_ALIGNED(x_dev);
+  for (int i = 0; i < nlos; ++i)
+    if (!(mu[i] > 0 && mu[i] <= 1)) return fail(c, PRD_E_ARG, "line-of-sight mu must be in (0, 1]");
+  try {
+    return prd::narrowband(c, x_dev, nlos, mu, chi, lambda0_A, fwhm_A, half_width_A, out);
+  } catch (const std::exception& e) {
+    return fail(c, PRD_E_NOMEM, std::string("host exception: ") + e.what());
+  }
+}
+
 int prd_set_option(prd_ctx* ctx, int option, int value) {
   CTX_OR_ARG(ctx);
   if (option == PRD_OPT_TENSOR_CORES) {
@@ -526,6 +547,20 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
   if (option == PRD_OPT_PRECOND_SWEEPS) {
     if (value < 0 || value > 64) return fail(c, PRD_E_ARG, "m_in must be in [0, 64]");
     c->m_in = value;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_WAIT_POLLS) {
+    if (value < 0) return fail(c, PRD_E_ARG, "poll limit must be >= 0");
+    c->tc_spin = value;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_REFINE_FLOOR) {
+    if (value < 1 || value > 1000000) return fail(c, PRD_E_ARG, "refinement floor must be in [1, 1e6] x 1e-8");
+    c->refine_floor = value * 1e-8;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_TEST_ZERO_OPERATOR) {
+    c->test_zero_op = value ? 1 : 0;
     return PRD_OK;
   }
   return fail(c, PRD_E_ARG, "unknown option");

@@ -65,7 +65,7 @@ static int residual_dot(Ctx* c, const std::vector<double>& B, const std::vector<
   if ((rc = dalloc(c, b, n * 8)) || (rc = dalloc(c, y, n * 8)) || (rc = dalloc(c, acc, 8))) return done(rc);
   if ((rc = prd_rhs(h, b.p)) || (rc = prd_apply_operator(h, x64, y.p))) return done(rc);
   if (cudaMemsetAsync(acc.p, 0, 8, c->stream) != cudaSuccess) return done(PRD_E_CUDA);
-  resdot_kernel<<<608, 256, 0, c->stream>>>(lam64, (const double*)b.p, (const double*)y.p, n, (double*)acc.p);
+  resdot_kernel<<<c->grid_ew(), 256, 0, c->stream>>>(lam64, (const double*)b.p, (const double*)y.p, n, (double*)acc.p);
   if (cudaMemcpyAsync(out, acc.p, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return done(PRD_E_CUDA);
@@ -89,8 +89,8 @@ int grad_b(Ctx* c, const void* x, const void* dJdI, double tol, double* dJdp) {
     PRD_CUDA_TRY(c, cudaMemcpyAsync(x64.p, x, n * 8, cudaMemcpyDeviceToDevice, c->stream));
     PRD_CUDA_TRY(c, cudaMemcpyAsync(lam64.p, lam.p, n * 8, cudaMemcpyDeviceToDevice, c->stream));
   } else {
-    f2d_kernel2<<<608, 256, 0, c->stream>>>((const float*)x, (double*)x64.p, n);
-    f2d_kernel2<<<608, 256, 0, c->stream>>>((const float*)lam.p, (double*)lam64.p, n);
+    f2d_kernel2<<<c->grid_ew(), 256, 0, c->stream>>>((const float*)x, (double*)x64.p, n);
+    f2d_kernel2<<<c->grid_ew(), 256, 0, c->stream>>>((const float*)lam.p, (double*)lam64.p, n);
   }
   PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   std::vector<double>* par[3] = {&c->B, &c->thB, &c->chB};

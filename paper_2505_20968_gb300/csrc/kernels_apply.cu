@@ -629,6 +629,21 @@ int spline_frame_change(Ctx* c, const void* in, void* out, bool to_comoving) {
   return PRD_OK;
 }
 
+// The same frame change for an FP64 vector in either mode (the preconditioner's
+// sweeps), with the caller's FP64 scratch for the spline second derivatives.
+int spline_frame_change_d(Ctx* c, const double* in, double* out, double* Mscratch, bool to_comoving) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  const long long npt = (long long)nz * nO * N;
+  const double* sp = (const double*)c->sp.p;
+  const int* kk = (const int*)(to_comoving ? c->iin.p : c->ibk.p);
+  const double* tt = (const double*)(to_comoving ? c->tin.p : c->tbk.p);
+  spline_M_kernel<double><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(in, Mscratch, sp, nz, nO, N);
+  spline_eval_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(in, Mscratch, kk, tt, sp, nullptr, out,
+                                                                               nz, nO, N);
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
+
 int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised) {
   if (c->prec == PRD_FP64) return sigma_T<double, double>(c, (const double*)x, (double*)eps, normalised);
   return sigma_T<float, float>(c, (const float*)x, (float*)eps, normalised);
@@ -887,25 +902,17 @@ int emergent(Ctx* c, const void* x, int nlos, const double* mu, const double* ch
 constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_sigma_scratch[kStaticScratchBytes];
 
-namespace {
-std::mutex g_scratch_mu;
-void* g_scratch_ptr[64] = {nullptr};   // device address of g_sigma_scratch per device
-}  // namespace
-
-// Device address of the static scratch on the current device, looked up once
-// per device (the host-side symbol is only a stand-in and must not be passed
-// to a kernel).
+// Device address of the static scratch in the current CUDA context.  The
+// host-side symbol is only a stand-in and must not be passed to a kernel.  The
+// address is looked up on every call (cudaGetSymbolAddress allocates nothing):
+// a cached address would dangle after the host framework resets the device or
+// re-creates its primary context, which reloads the library's device code.
 static int static_scratch(Ctx* c, void** out) {
-  if (c->device < 0 || c->device >= 64) return fail(c, PRD_E_ARG, "device index out of range for static scratch");
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[c->device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_sigma_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(c, PRD_E_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-    g_scratch_ptr[c->device] = p;
-  }
-  *out = g_scratch_ptr[c->device];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_sigma_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(c, PRD_E_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+  *out = p;
   return PRD_OK;
 }
 

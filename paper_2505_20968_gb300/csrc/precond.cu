@@ -20,53 +20,58 @@ namespace prd {
 int launch_pc_tiles(Ctx* c, const std::vector<double>& shift_g, std::vector<double>& aa_tiles,
                     std::vector<double>& r3g);
 
+// The sweeps run in FP64 in both modes: the residual y - P x of a later sweep
+// cancels almost completely, and the block inverse amplifies whatever rounding
+// it carries, so in FP32 it would leave P^-1 neither accurate nor linear.  The
+// vectors of P^-1 are Stokes I only and its tables small; the FP32 tables of
+// the ctx (K/DELO weights, Lambda_ii) enter as fixed coefficients.
+
 // J[z][m] = sum_o w_o X[z][o][m][0]
-template <typename T>
-__global__ void pc_angle_avg_kernel(const T* __restrict__ X, const double* __restrict__ w, T* __restrict__ J, int nz,
-                                    int nO, int N) {
+__global__ void pc_angle_avg_kernel(const double* __restrict__ X, const double* __restrict__ w, double* __restrict__ J,
+                                    int nz, int nO, int N) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nz * N) return;
   const int iz = idx / N, m = idx - iz * N;
   double s = 0.0;
-  for (int o = 0; o < nO; ++o) s += w[o] * (double)X[(((size_t)iz * nO + o) * N + m) * 4];
-  J[idx] = (T)s;
+  for (int o = 0; o < nO; ++o) s += w[o] * X[(((size_t)iz * nO + o) * N + m) * 4];
+  J[idx] = s;
 }
 
 // V[z][o][n][0] = sum_m A[z][n][m] J[z][m]  (broadcast over o; Q,U,V zero)
-template <typename T>
-__global__ void pc_matvec_bcast_kernel(const T* __restrict__ A, const T* __restrict__ J, T* __restrict__ V, int nz,
-                                       int nO, int N) {
+__global__ void pc_matvec_bcast_kernel(const double* __restrict__ A, const double* __restrict__ J, double* __restrict__ V,
+                                       int nz, int nO, int N) {
   const int iz = blockIdx.y;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  const T* a = A + ((size_t)iz * N + n) * N;
-  const T* j = J + (size_t)iz * N;
+  const double* a = A + ((size_t)iz * N + n) * N;
+  const double* j = J + (size_t)iz * N;
   double s = 0.0;
-  for (int m = 0; m < N; ++m) s += (double)a[m] * (double)j[m];
+  for (int m = 0; m < N; ++m) s += a[m] * j[m];
   for (int o = 0; o < nO; ++o) {
-    T* v = V + (((size_t)iz * nO + o) * N + n) * 4;
-    v[0] = (T)s;
-    v[1] = v[2] = v[3] = (T)0;
+    double* v = V + (((size_t)iz * nO + o) * N + n) * 4;
+    v[0] = s;
+    v[1] = v[2] = v[3] = 0.0;
   }
 }
 
 // Scalar DELO-linear sweep of Stokes I: out = Lambda* eps (zero boundary).
 template <typename T>
-__global__ void pc_delo_kernel(const T* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
-                               T* __restrict__ out, int nz, int nO, int N) {
+__global__ void pc_delo_kernel(const double* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
+                               double* __restrict__ out, int nz, int nO, int N) {
   const int ray = blockIdx.x * blockDim.x + threadIdx.x;
   if (ray >= nO * N) return;
   const int o = ray / N, n = ray - o * N;
   const bool up = mu[o] > 0.0;
-  T I = 0, Sp = 0;
+  double I = 0, Sp = 0;
   for (int p = 0; p < nz; ++p) {
     const int k = up ? p : nz - 1 - p;
     const size_t pt = ((size_t)k * nO + o) * N + n;
     const T* t = kt + pt * 10;
-    const T S = eps[pt * 4] * t[6];
+    const double S = eps[pt * 4] * (double)t[6];
+    const double e = (double)t[7], al = (double)t[8], be = (double)t[9];
     if (p == 0) I = 0;
-    else if (t[7] <= (T)0.5) I = S + t[7] * (I - S) + t[8] * (Sp - S);   // thick: photon-exact form
-    else I = t[7] * I + t[8] * Sp + t[9] * S;                              // thin: standard form
+    else if (e <= 0.5) I = S + e * (I - S) + al * (Sp - S);   // thick: photon-exact form
+    else I = e * I + al * Sp + be * S;                          // thin: standard form
     out[pt * 4] = I;
     Sp = S;
   }
@@ -74,34 +79,44 @@ __global__ void pc_delo_kernel(const T* __restrict__ eps, const T* __restrict__ 
 
 // x[.][0] += r[.][0] + lii * v[.][0]  (Richardson update with P_hat^-1)
 template <typename T>
-__global__ void pc_update_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict__ lii,
-                                 const T* __restrict__ v, long long npt) {
+__global__ void pc_update_kernel(double* __restrict__ x, const double* __restrict__ r, const T* __restrict__ lii,
+                                 const double* __restrict__ v, long long npt) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= npt) return;
-  x[pt * 4] += r[pt * 4] + lii[pt] * v[pt * 4];
+  x[pt * 4] += r[pt * 4] + (double)lii[pt] * v[pt * 4];
 }
 
 // r[.][0] = y[.][0] - x[.][0] + LS[.][0]   (residual of P x = y on Stokes I)
 template <typename T>
-__global__ void pc_resid_kernel(const T* __restrict__ y, const T* __restrict__ x, const T* __restrict__ ls,
-                                T* __restrict__ r, long long npt) {
+__global__ void pc_resid_kernel(const T* __restrict__ y, const double* __restrict__ x, const double* __restrict__ ls,
+                                double* __restrict__ r, long long npt) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= npt) return;
-  r[pt * 4] = y[pt * 4] - x[pt * 4] + ls[pt * 4];
+  r[pt * 4] = ((double)y[pt * 4] - x[pt * 4]) + ls[pt * 4];
 }
 
+// x = 0 on Stokes I; r = y on Stokes I (the first sweep's residual)
 template <typename T>
-__global__ void pc_init_kernel(const T* __restrict__ y, T* __restrict__ x, long long npt) {
+__global__ void pc_init_kernel(const T* __restrict__ y, double* __restrict__ x, double* __restrict__ r, long long npt) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= npt) return;
-  x[pt * 4] = 0;
-  x[pt * 4 + 1] = y[pt * 4 + 1];
-  x[pt * 4 + 2] = y[pt * 4 + 2];
-  x[pt * 4 + 3] = y[pt * 4 + 3];
+  x[pt * 4] = 0.0;
+  r[pt * 4] = (double)y[pt * 4];
 }
 
-// spline kernels from kernels_apply.cu
-int spline_frame_change(Ctx* c, const void* in, void* out, bool to_comoving);
+// out = (x on Stokes I, y on Q, U, V) in the ctx precision
+template <typename T>
+__global__ void pc_out_kernel(const T* __restrict__ y, const double* __restrict__ x, T* __restrict__ out, long long npt) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npt) return;
+  out[pt * 4] = (T)x[pt * 4];
+  out[pt * 4 + 1] = y[pt * 4 + 1];
+  out[pt * 4 + 2] = y[pt * 4 + 2];
+  out[pt * 4 + 3] = y[pt * 4 + 3];
+}
+
+// observer <-> comoving frame change of an FP64 vector (kernels_apply.cu)
+int spline_frame_change_d(Ctx* c, const double* in, double* out, double* Mscratch, bool to_comoving);
 
 static int lu_inverse(std::vector<double>& A, int n) {
   std::vector<int> piv(n);
@@ -192,19 +207,16 @@ int launch_precond_setup(Ctx* c) {
   }
   for (int iz = 0; iz < nz; ++iz)
     if (bad[iz]) return fail(c, PRD_E_ARG, "block-Jacobi matrix (Id - A_i) is singular at height " + std::to_string(iz));
-  auto up = [&](DBuf& b, const std::vector<double>& v) {
-    if (c->prec == PRD_FP64) return upload(c, b, v.data(), v.size() * 8);
-    std::vector<float> f(v.begin(), v.end());
-    return upload(c, b, f.data(), f.size() * 4);
-  };
-  if ((rc = up(c->pc_phi, phi)) || (rc = up(c->pc_M, Mm))) return rc;
+  if ((rc = upload(c, c->pc_phi, phi.data(), phi.size() * 8)) || (rc = upload(c, c->pc_M, Mm.data(), Mm.size() * 8)))
+    return rc;
   DBuf w;
   if ((rc = upload(c, w, c->wang.data(), nO * 8))) return rc;
   c->owned.push_back(w);     // angular weights (double), freed with the ctx
   c->pc_w = w.p;
-  const size_t vb = nvec(c) * c->esz;
+  const size_t vb = nvec(c) * sizeof(double);
   if ((rc = dalloc(c, c->pc_s1, vb)) || (rc = dalloc(c, c->pc_s2, vb)) || (rc = dalloc(c, c->pc_s3, vb)) ||
-      (rc = dalloc(c, c->gm_w, (size_t)nz * N * c->esz)))
+      (rc = dalloc(c, c->pc_s4, vb)) || (rc = dalloc(c, c->pc_s5, vb)) ||
+      (rc = dalloc(c, c->gm_w, (size_t)nz * N * sizeof(double))))
     return rc;
   return PRD_OK;
 }
@@ -213,32 +225,34 @@ template <typename T>
 static int precond_T(Ctx* c, const T* y, T* x) {
   const int nz = c->nz, nO = c->nO, N = c->nnu;
   const long long npt = (long long)nz * nO * N;
-  T* r = (T*)c->pc_s1.p;
-  T* t1 = (T*)c->pc_s2.p;
-  T* t2 = (T*)c->pc_s3.p;
-  T* J = (T*)c->gm_w.p;
+  double* r = (double*)c->pc_s1.p;
+  double* t1 = (double*)c->pc_s2.p;
+  double* t2 = (double*)c->pc_s3.p;
+  double* xd = (double*)c->pc_s4.p;
+  double* Ms = (double*)c->pc_s5.p;
+  double* J = (double*)c->gm_w.p;
   const double* w = (const double*)c->pc_w;
   const int g1 = ceil_div(npt, 256);
-  pc_init_kernel<T><<<g1, 256, 0, c->stream>>>(y, x, npt);
+  pc_init_kernel<T><<<g1, 256, 0, c->stream>>>(y, xd, r, npt);
   for (int sweep = 0; sweep < c->m_in; ++sweep) {
-    // r = y - P x on Stokes I (P x = x - Lambda* Sigma* x)
-    if (sweep == 0) {
-      PRD_CUDA_TRY(c, cudaMemcpyAsync(r, y, nvec(c) * c->esz, cudaMemcpyDeviceToDevice, c->stream));
-    } else {
-      int rc = spline_frame_change(c, x, t1, true);                       // comoving I~
+    // r = y - P x on Stokes I (P x = x - Lambda* Sigma* x); the first sweep starts from x = 0
+    if (sweep > 0) {
+      int rc = spline_frame_change_d(c, xd, t1, Ms, true);                  // comoving I~
       if (rc) return rc;
-      pc_angle_avg_kernel<T><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>(t1, w, J, nz, nO, N);
-      pc_matvec_bcast_kernel<T><<<dim3(ceil_div(N, 128), nz), 128, 0, c->stream>>>((const T*)c->pc_phi.p, J, t2, nz, nO, N);
-      if ((rc = spline_frame_change(c, t2, t1, false))) return rc;       // eps* (observer)
-      pc_delo_kernel<T><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>(t1, (const T*)c->kt.p, (const double*)c->dmu.p, t2,
-                                                                      nz, nO, N);
-      pc_resid_kernel<T><<<g1, 256, 0, c->stream>>>(y, x, t2, r, npt);
+      pc_angle_avg_kernel<<<ceil_div(nz * N, 128), 128, 0, c->stream>>>(t1, w, J, nz, nO, N);
+      pc_matvec_bcast_kernel<<<dim3(ceil_div(N, 128), nz), 128, 0, c->stream>>>((const double*)c->pc_phi.p, J, t2, nz,
+                                                                               nO, N);
+      if ((rc = spline_frame_change_d(c, t2, t1, Ms, false))) return rc;    // eps* (observer)
+      pc_delo_kernel<T><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>(t1, (const T*)c->kt.p, (const double*)c->dmu.p,
+                                                                      t2, nz, nO, N);
+      pc_resid_kernel<T><<<g1, 256, 0, c->stream>>>(y, xd, t2, r, npt);
     }
     // x += P_hat^-1 r
-    pc_angle_avg_kernel<T><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>(r, w, J, nz, nO, N);
-    pc_matvec_bcast_kernel<T><<<dim3(ceil_div(N, 128), nz), 128, 0, c->stream>>>((const T*)c->pc_M.p, J, t2, nz, nO, N);
-    pc_update_kernel<T><<<g1, 256, 0, c->stream>>>(x, r, (const T*)c->pc_lii.p, t2, npt);
+    pc_angle_avg_kernel<<<ceil_div(nz * N, 128), 128, 0, c->stream>>>(r, w, J, nz, nO, N);
+    pc_matvec_bcast_kernel<<<dim3(ceil_div(N, 128), nz), 128, 0, c->stream>>>((const double*)c->pc_M.p, J, t2, nz, nO, N);
+    pc_update_kernel<T><<<g1, 256, 0, c->stream>>>(xd, r, (const T*)c->pc_lii.p, t2, npt);
   }
+  pc_out_kernel<T><<<g1, 256, 0, c->stream>>>(y, xd, x, npt);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

@@ -1,8 +1,13 @@
 // Krylov solver (S10): left-preconditioned restarted GMRES with classical
 // Gram-Schmidt applied twice (CGS2), inner products accumulated in FP64 on the
-// device, Givens rotations and the least-squares update in FP64 on the host
-// (Sect. 5.1-5.2).  The stopping test is the unpreconditioned relative residual
-// ||b - A x|| / ||b|| of Sect. 5.1, recomputed in FP64 before returning.
+// device (Sect. 5.1-5.2).  The Arnoldi coefficients never leave the device:
+// the Gram-Schmidt projections read them from device memory, and one
+// single-thread kernel per iteration applies the Givens rotations to the new
+// Hessenberg column, forms the next rotation and the residual estimate (FP64).
+// The host reads back that estimate once per iteration (to stop), and the
+// least-squares back substitution runs on the device at the end of a cycle.
+// The stopping test is the unpreconditioned relative residual ||b - A x|| /
+// ||b|| of Sect. 5.1, recomputed in FP64 before returning.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -29,7 +34,7 @@ __global__ void multidot_kernel(const T* __restrict__ V, size_t ld, const T* __r
   if (threadIdx.x == 0) atomicAdd(&dots[k], red[0]);
 }
 
-// w -= sum_k h[k] V[k]
+// w -= sum_k h[k] V[k]   (h in device memory)
 template <typename T>
 __global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ld, const double* __restrict__ h, int nv, T* w,
                                  size_t n) {
@@ -40,13 +45,15 @@ __global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ld, const doubl
   }
 }
 
+// b = a * (*s)   (scale factor in device memory)
 template <typename T>
-__global__ void scale_copy_kernel(const T* __restrict__ a, double s, T* __restrict__ b, size_t n) {
+__global__ void scale_copy_kernel(const T* __restrict__ a, const double* __restrict__ s, T* __restrict__ b, size_t n) {
+  const double f = *s;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    b[i] = (T)((double)a[i] * s);
+    b[i] = (T)((double)a[i] * f);
 }
 
-// x += sum_k y[k] V[k]
+// x += sum_k y[k] V[k]   (y in device memory)
 template <typename T>
 __global__ void update_kernel(const T* __restrict__ V, size_t ld, const double* __restrict__ y, int nv, T* x, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -63,51 +70,122 @@ __global__ void rsub_kernel(const T* __restrict__ b, T* r, size_t n) {
     r[i] = b[i] - r[i];
 }
 
+// Device state of one GMRES(m) cycle, in one FP64 array:
+//   H[(m+1) x m] (row-major, the rotated Hessenberg matrix), cs[m], sn[m],
+//   g[m+1] (rotated right-hand side), y[m] (least-squares solution),
+//   h[m+1], h2[m+1] (projections of the two Gram-Schmidt passes), and
+//   scalars: kSS (sum of squares), kInv (1/norm for scaling), kEst (residual
+//   estimate), kNorm (norm), kBeta0.
+struct GState {
+  int m;
+  __host__ __device__ size_t H() const { return 0; }
+  __host__ __device__ size_t cs() const { return (size_t)(m + 1) * m; }
+  __host__ __device__ size_t sn() const { return cs() + m; }
+  __host__ __device__ size_t g() const { return sn() + m; }
+  __host__ __device__ size_t y() const { return g() + m + 1; }
+  __host__ __device__ size_t h() const { return y() + m; }
+  __host__ __device__ size_t h2() const { return h() + m + 1; }
+  __host__ __device__ size_t sc() const { return h2() + m + 1; }
+  __host__ __device__ size_t total() const { return sc() + 8; }
+};
+enum { kSS = 0, kInv = 1, kEst = 2, kNorm = 3, kBeta0 = 4 };
+
+// start of a cycle: beta = sqrt(ss); g = beta e_1; 1/beta for the first basis vector
+__global__ void gm_cycle_start_kernel(double* st, GState L) {
+  double* sc = st + L.sc();
+  const double beta = sqrt(sc[kSS]);
+  double* g = st + L.g();
+  for (int i = 0; i <= L.m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  sc[kBeta0] = beta;
+  sc[kNorm] = beta;
+  sc[kInv] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// Arnoldi step j: Hessenberg column from the two Gram-Schmidt passes and the
+// norm of the orthogonalised vector, earlier rotations applied, the new
+// rotation formed and applied to g; estimate tr |g[j+1]| / beta0.
+__global__ void gm_arnoldi_kernel(double* st, GState L, int j, double tr) {
+  const int m = L.m;
+  double* H = st + L.H();
+  double* cs = st + L.cs();
+  double* sn = st + L.sn();
+  double* g = st + L.g();
+  const double* h = st + L.h();
+  const double* h2 = st + L.h2();
+  double* sc = st + L.sc();
+  const double hn = sqrt(sc[kSS]);
+  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
+  H[(size_t)(j + 1) * m + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a0 = H[(size_t)i * m + j], a1 = H[(size_t)(i + 1) * m + j];
+    H[(size_t)i * m + j] = cs[i] * a0 + sn[i] * a1;
+    H[(size_t)(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
+  }
+  const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+  const double den = hypot(a0, a1);
+  cs[j] = den > 0 ? a0 / den : 1.0;
+  sn[j] = den > 0 ? a1 / den : 0.0;
+  H[(size_t)j * m + j] = den;
+  H[(size_t)(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  sc[kNorm] = hn;
+  sc[kInv] = hn > 0.0 ? 1.0 / hn : 0.0;
+  sc[kEst] = tr * fabs(g[j + 1]) / sc[kBeta0];
+}
+
+// y = H(0:j, 0:j)^-1 g(0:j)  (upper triangular after the rotations)
+__global__ void gm_backsolve_kernel(double* st, GState L, int j) {
+  const int m = L.m;
+  const double* H = st + L.H();
+  const double* g = st + L.g();
+  double* y = st + L.y();
+  for (int i = j - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
+    const double d = H[(size_t)i * m + i];
+    y[i] = d != 0.0 ? s / d : 0.0;   // an exact breakdown on the first step leaves a zero pivot
+  }
+}
+
 namespace {
 
 struct Vops {
   Ctx* c;
   size_t n;
-  int grid;
-  DBuf dots;
-  int cap = 0;   // capacity of `dots` in doubles
-  int init(int capacity) {
-    grid = 152 * 4;
-    cap = capacity;
-    return dalloc(c, dots, (size_t)capacity * sizeof(double));
+  int grid = 0;
+  int init() {
+    grid = c->grid_ew();
+    return PRD_OK;
   }
+  // out[k] = <V[k], w> for k < nv, in device memory
   int dot_many(const void* V, size_t ld, int nv, const void* w, double* out) {
-    if (nv > cap) return fail(c, PRD_E_ARG, "internal: dot buffer too small");
-    PRD_CUDA_TRY(c, cudaMemsetAsync(dots.p, 0, nv * sizeof(double), c->stream));
+    PRD_CUDA_TRY(c, cudaMemsetAsync(out, 0, nv * sizeof(double), c->stream));
     if (c->prec == PRD_FP64)
-      multidot_kernel<double><<<dim3(grid, nv), 256, 0, c->stream>>>((const double*)V, ld, (const double*)w, n, (double*)dots.p);
+      multidot_kernel<double><<<dim3(grid, nv), 256, 0, c->stream>>>((const double*)V, ld, (const double*)w, n, out);
     else
-      multidot_kernel<float><<<dim3(grid, nv), 256, 0, c->stream>>>((const float*)V, ld, (const float*)w, n, (double*)dots.p);
-    PRD_CUDA_TRY(c, cudaMemcpyAsync(out, dots.p, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      multidot_kernel<float><<<dim3(grid, nv), 256, 0, c->stream>>>((const float*)V, ld, (const float*)w, n, out);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
   int axpy_many(const void* V, size_t ld, const double* h, int nv, void* w) {
-    if (nv > cap) return fail(c, PRD_E_ARG, "internal: dot buffer too small");
-    PRD_CUDA_TRY(c, cudaMemcpyAsync(dots.p, h, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->prec == PRD_FP64)
-      multiaxpy_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, (const double*)dots.p, nv, (double*)w, n);
+      multiaxpy_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, h, nv, (double*)w, n);
     else
-      multiaxpy_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)V, ld, (const double*)dots.p, nv, (float*)w, n);
-    PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      multiaxpy_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)V, ld, h, nv, (float*)w, n);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
   int update(const void* V, size_t ld, const double* y, int nv, void* x) {
-    if (nv > cap) return fail(c, PRD_E_ARG, "internal: dot buffer too small");
-    PRD_CUDA_TRY(c, cudaMemcpyAsync(dots.p, y, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->prec == PRD_FP64)
-      update_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, (const double*)dots.p, nv, (double*)x, n);
+      update_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, y, nv, (double*)x, n);
     else
-      update_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)V, ld, (const double*)dots.p, nv, (float*)x, n);
-    PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      update_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)V, ld, y, nv, (float*)x, n);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
-  int scale(const void* a, double s, void* b) {
+  int scale(const void* a, const double* s, void* b) {
     if (c->prec == PRD_FP64)
       scale_copy_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)a, s, (double*)b, n);
     else
@@ -121,19 +199,33 @@ struct Vops {
     PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
-  int norm(const void* a, double* out) {
-    double d;
-    int rc = dot_many(a, 0, 1, a, &d);
-    *out = std::sqrt(d);
-    return rc;
+  // copy `cnt` doubles of device state to the host (synchronises the stream)
+  int read(const double* src, double* dst, int cnt) {
+    PRD_CUDA_TRY(c, cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PRD_OK;
+  }
+  // ||a|| on the host (sum of squares into *ss on the device)
+  int norm(const void* a, double* ss, double* out) {
+    int rc = dot_many(a, 0, 1, a, ss);
+    if (rc) return rc;
+    double h;
+    if ((rc = read(ss, &h, 1))) return rc;
+    *out = std::sqrt(h);
+    return PRD_OK;
   }
 };
 
 }  // namespace
 
 int apply_operator_t(Ctx* c, const void* x, void* y);
-// the operator GMRES iterates with: A, or A^T for the adjoint solve
+// the operator GMRES iterates with: A, or A^T for the adjoint solve (or the
+// zero map injected for testing the breakdown path, PRD_OPT_TEST_ZERO_OPERATOR)
 static int op_apply(Ctx* c, const void* x, void* y) {
+  if (c->test_zero_op) {
+    PRD_CUDA_TRY(c, cudaMemsetAsync(y, 0, nvec(c) * c->esz, c->stream));
+    return PRD_OK;
+  }
   return c->op_transpose ? apply_operator_t(c, x, y) : apply_operator(c, x, y);
 }
 
@@ -148,25 +240,29 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   const size_t vb = n * c->esz;
   const int m = std::max(1, std::min(restart, 200));
   Vops ops{c, n};
-  int rc = ops.init(m + 2);
+  int rc = ops.init();
   if (rc) return rc;
-  DBuf V, r, w;
+  const GState L{m};
+  DBuf V, r, w, S;
   struct { void* p; } b{const_cast<void*>(bvec)};
-  auto cleanup = [&]() { dfree(V); dfree(r); dfree(w); dfree(ops.dots); };
-  if ((rc = dalloc(c, V, vb * (m + 1))) || (rc = dalloc(c, r, vb)) || (rc = dalloc(c, w, vb))) {
+  auto cleanup = [&]() { dfree(V); dfree(r); dfree(w); dfree(S); };
+  if ((rc = dalloc(c, V, vb * (m + 1))) || (rc = dalloc(c, r, vb)) || (rc = dalloc(c, w, vb)) ||
+      (rc = dalloc(c, S, L.total() * sizeof(double)))) {
     cleanup();
     return rc;
   }
+  double* st = (double*)S.p;
+  double* ss = st + L.sc() + kSS;
   auto vec = [&](int k) { return (void*)((char*)V.p + (size_t)k * vb); };
   double bnorm;
-  if ((rc = ops.norm(b.p, &bnorm))) { cleanup(); return rc; }
+  if ((rc = ops.norm(b.p, ss, &bnorm))) { cleanup(); return rc; }
   if (!(bnorm > 0) || !std::isfinite(bnorm)) { cleanup(); return fail(c, PRD_E_NAN, "right-hand side norm is zero or not finite"); }
   int it = 0, nh = nh_io ? *nh_io : 0;
   double tol_in = tol;
   double tr = 1.0;
   int status = PRD_E_NOCONV;
   bool first = true;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+  double sc[8];
   while (it < max_iter) {
     // r = P^-1 (b - A x)
     if (inner && first) {
@@ -175,70 +271,56 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
     } else {
       if ((rc = op_apply(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
       double rn_true;
-      if ((rc = ops.norm(w.p, &rn_true))) break;
+      if ((rc = ops.norm(w.p, ss, &rn_true))) break;
       tr = rn_true / bnorm;
     }
     first = false;
     if (!std::isfinite(tr)) { rc = fail(c, PRD_E_NAN, "residual is not finite"); break; }
     if (tr < tol) { status = PRD_OK; break; }
     if ((rc = apply_precond(c, w.p, r.p))) break;
-    double beta;
-    if ((rc = ops.norm(r.p, &beta))) break;
-    if (!(beta > 0)) { status = PRD_OK; break; }
-    if ((rc = ops.scale(r.p, 1.0 / beta, vec(0)))) break;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    const double beta0 = beta;
+    if ((rc = ops.dot_many(r.p, 0, 1, r.p, ss))) break;
+    gm_cycle_start_kernel<<<1, 1, 0, c->stream>>>(st, L);
+    if ((rc = ops.read(st + L.sc(), sc, 8))) break;
+    const double beta0 = sc[kBeta0];
+    if (!(beta0 > 0)) { status = PRD_OK; break; }
+    if ((rc = ops.scale(r.p, st + L.sc() + kInv, vec(0)))) break;
     int j = 0;
     bool breakdown = false, est_ok = false;
     for (; j < m && it < max_iter; ++j) {
       if ((rc = op_apply(c, vec(j), w.p)) || (rc = apply_precond(c, w.p, r.p))) break;
       ++it;
-      // CGS2
-      if ((rc = ops.dot_many(V.p, n, j + 1, r.p, h.data())) || (rc = ops.axpy_many(V.p, n, h.data(), j + 1, r.p))) break;
-      if ((rc = ops.dot_many(V.p, n, j + 1, r.p, h2.data())) || (rc = ops.axpy_many(V.p, n, h2.data(), j + 1, r.p))) break;
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
-      double hn;
-      if ((rc = ops.norm(r.p, &hn))) break;
-      if (!std::isfinite(hn)) { rc = fail(c, PRD_E_NAN, "Arnoldi vector is not finite"); break; }
-      H[(size_t)(j + 1) * m + j] = hn;
-      // Givens
-      for (int i = 0; i < j; ++i) {
-        const double a0 = H[(size_t)i * m + j], a1 = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a0 + sn[i] * a1;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
-      }
-      const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
-      const double den = std::hypot(a0, a1);
-      cs[j] = den > 0 ? a0 / den : 1.0;
-      sn[j] = den > 0 ? a1 / den : 0.0;
-      H[(size_t)j * m + j] = den;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      const double est = tr * std::fabs(g[j + 1]) / beta0;   // estimate of the true relative residual
+      // CGS2, projections kept on the device
+      if ((rc = ops.dot_many(V.p, n, j + 1, r.p, st + L.h())) ||
+          (rc = ops.axpy_many(V.p, n, st + L.h(), j + 1, r.p)) ||
+          (rc = ops.dot_many(V.p, n, j + 1, r.p, st + L.h2())) ||
+          (rc = ops.axpy_many(V.p, n, st + L.h2(), j + 1, r.p)) ||
+          (rc = ops.dot_many(r.p, 0, 1, r.p, ss)))
+        break;
+      gm_arnoldi_kernel<<<1, 1, 0, c->stream>>>(st, L, j, tr);
+      // the next basis vector is scaled on the device before the host looks
+      if ((rc = ops.scale(r.p, st + L.sc() + kInv, vec(j + 1)))) break;
+      if ((rc = ops.read(st + L.sc(), sc, 8))) break;
+      const double hn = sc[kNorm], est = sc[kEst];
+      if (!std::isfinite(hn) || !std::isfinite(est)) { rc = fail(c, PRD_E_NAN, "Arnoldi vector is not finite"); break; }
       if (hist && nh <= max_iter) hist[nh++] = est * hist_scale;
       if (hn <= 1e-300 * std::max(1.0, beta0)) { breakdown = true; ++j; break; }
-      if ((rc = ops.scale(r.p, 1.0 / hn, vec(j + 1)))) break;
       if (est < 0.5 * tol_in) { ++j; est_ok = true; break; }
     }
     if (rc) break;
-    // back substitution H y = g, x += V y
-    for (int i = j - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
-      y[i] = s / H[(size_t)i * m + i];
-    }
-    if ((rc = ops.update(V.p, n, y.data(), j, x))) break;
+    // back substitution H y = g and x += V y, on the device
+    gm_backsolve_kernel<<<1, 1, 0, c->stream>>>(st, L, j);
+    if ((rc = ops.update(V.p, n, st + L.y(), j, x))) break;
     if (inner && (est_ok || breakdown)) {
+      double gj;
+      if ((rc = ops.read(st + L.g() + j, &gj, 1))) break;
       status = PRD_OK;
-      tr = std::fabs(g[j]) / beta0 * tr;
+      tr = std::fabs(gj) / beta0 * tr;
       break;
     }
     if (breakdown) {
       if ((rc = op_apply(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
       double rn;
-      if ((rc = ops.norm(w.p, &rn))) break;
+      if ((rc = ops.norm(w.p, ss, &rn))) break;
       tr = rn / bnorm;
       status = tr < tol ? PRD_OK : PRD_E_BREAKDOWN;
       break;
@@ -249,7 +331,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
     // final true residual
     if (!(rc = op_apply(c, x, w.p)) && !(rc = ops.rsub(b.p, w.p))) {
       double rn;
-      if (!(rc = ops.norm(w.p, &rn))) {
+      if (!(rc = ops.norm(w.p, ss, &rn))) {
         tr = rn / bnorm;
         if (tr < tol) status = PRD_OK;
       }
@@ -300,7 +382,7 @@ int rhs_acc(Ctx* c, double* b);
 
 static int dnorm(Ctx* c, const double* a, size_t n, double* dsum, double* out) {
   PRD_CUDA_TRY(c, cudaMemsetAsync(dsum, 0, 8, c->stream));
-  dnorm2_kernel<<<608, 256, 0, c->stream>>>(a, n, dsum);
+  dnorm2_kernel<<<c->grid_ew(), 256, 0, c->stream>>>(a, n, dsum);
   double h;
   PRD_CUDA_TRY(c, cudaMemcpyAsync(&h, dsum, 8, cudaMemcpyDeviceToHost, c->stream));
   PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -334,7 +416,7 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
     cleanup();
     return rc;
   }
-  const int G = 608;
+  const int G = c->grid_ew();
   if ((rc = rhs_acc(c, (double*)b64.p))) { cleanup(); return rc; }
   if (x0) f2d_kernel<<<G, 256, 0, c->stream>>>((const float*)x0, (double*)x64.p, n);
   else PRD_CUDA_TRY(c, cudaMemsetAsync(x64.p, 0, n * 8, c->stream));
@@ -359,7 +441,7 @@ int solve(Ctx* c, double tol, int max_iter, int restart, const void* x0, void* x
     if (res < tol) { status = PRD_OK; break; }
     d2f_kernel<<<G, 256, 0, c->stream>>>((const double*)r64.p, (float*)r32.p, n);
     PRD_CUDA_TRY(c, cudaMemsetAsync(d32.p, 0, vb, c->stream));
-    const double tin = std::max(0.3 * tol / res, 3e-5);
+    const double tin = std::max(0.3 * tol / res, c->refine_floor);
     int its = 0;
     double tr_in = 0;
     const int cap_in = std::min(max_iter - it_total, std::max(2 * restart, 40));

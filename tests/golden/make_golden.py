@@ -3,6 +3,8 @@
 Calls only oracle/ and the seeded input generator; never the CUDA library.
 Run from the repository root:  python tests/golden/make_golden.py [names...]
 Outputs tests/golden/<name>.npz (forward operator and solution),
+twolevel_full_sol.npz (the solution of the full two-level slab), <name>_nb.npz
+(narrow-band signals along lines of sight),
 <name>_adj.npz (transposed operator and adjoint solve), <name>_pc.npz (the
 preconditioner with 1 and 2 sweeps) and grad_mgii_small.npz
 (derivatives of an emergent-intensity functional by central differences of
@@ -133,6 +135,37 @@ def make_grad():
     np.savez_compressed(os.path.join(HERE, "grad_mgii_small.npz"), fd=fd, fd_half=fd_half, step=steps, J0=J[0])
 
 
+# narrow-band signals (Sect. 6.5) of the reduced cases' oracle solutions along
+# lines of sight at chi = 0: the H I cases with the paper's band (lambda_0 =
+# 1215.67 A, FWHM 35 A, +-30 A), the two-level slab with a band of its own width
+NB = {"hi": (1215.67, 35.0, 30.0), "hi_aa": (1215.67, 35.0, 30.0), "twolevel": (None, 0.08, 0.1)}
+NB_MU = np.array([0.1, 0.3, 0.5, 0.7, 0.9, 1.0])
+
+
+def make_narrowband(name):
+    from oracle.narrowband import narrowband, grid_wavelengths
+    P = Problem(CASES[name]())
+    sol = np.load(os.path.join(HERE, name + ".npz"))["sol"]
+    lam = grid_wavelengths(P)
+    lam0, fwhm, half = NB[name]
+    if lam0 is None:
+        lam0 = 0.5 * (lam[0] + lam[-1])
+    em = np.stack([P.emergent(sol, m, 0.0) for m in NB_MU])
+    np.savez_compressed(os.path.join(HERE, name + "_nb.npz"), mu=NB_MU, lam0=lam0, fwhm=fwhm, half=half, em=em,
+                        xbar=narrowband(lam, em, lam0, fwhm, half))
+
+
+# the full two-level slab (40 heights x 8 directions x 21 frequencies, FP64):
+# the solution to tol 1e-12 and its emergent Stokes vectors
+def make_full_solve():
+    P = Problem(inputs.twolevel_slab())
+    sol, hist = P.solve(tol=1e-12)
+    los = np.array([[0.1, 0.0], [1.0, 0.0], [0.55, 1.3]])
+    em = np.stack([P.emergent(sol, m, c) for m, c in los])
+    np.savez_compressed(os.path.join(HERE, "twolevel_full_sol.npz"), sol=sol, rhs=P.rhs(), res=hist[-1],
+                        iters=len(hist), los=los, emergent=em)
+
+
 def make_sample(name):
     mk, sig_pts, ray_pts = SAMPLES[name]
     cfg = mk()
@@ -150,7 +183,7 @@ def make_sample(name):
 
 if __name__ == "__main__":
     names = sys.argv[1:] or (list(CASES) + list(SAMPLES) + [a + "_adj" for a in ADJOINT] + ["grad"]
-                             + [a + "_pc" for a in PRECOND])
+                             + [a + "_pc" for a in PRECOND] + ["twolevel_full_sol"] + [a + "_nb" for a in NB])
     for nm in names:
         t0 = time.time()
         if nm in CASES:
@@ -163,6 +196,10 @@ if __name__ == "__main__":
             make_precond(nm[:-3])
         elif nm == "grad":
             make_grad()
+        elif nm == "twolevel_full_sol":
+            make_full_solve()
+        elif nm.endswith("_nb"):
+            make_narrowband(nm[:-3])
         else:
             raise SystemExit(f"unknown golden set {nm}")
         print(f"{nm}: {time.time() - t0:.1f} s", flush=True)

@@ -683,3 +683,31 @@ def test_r3_incident_bracket_matches_r2_under_flat_emission():
     finally:
         OP.voigt_faraday = vf
     assert np.max(np.abs(a2 - a3)) < 1e-12 * np.max(np.abs(a2))
+
+
+# ---------------------------------------------------------------- narrow-band CLV signals
+def test_narrowband_closed_forms():
+    """Sect. 6.5's Gaussian-weighted wavelength integral (FWHM 35 A, limits
+    +-30 A around 1215.67 A) on ascending wavelength nodes: a constant profile
+    c gives c erf(Delta / (sqrt(2) sigma)) (the constant continuation covers
+    the limits beyond the grid); an odd profile about lambda_0 on a symmetric
+    grid covering the limits gives 0; a Gaussian profile of width tau gives
+    (rho / sigma) erf(Delta / (sqrt(2) rho)), 1/rho^2 = 1/sigma^2 + 1/tau^2
+    (to the spline's interpolation error, 1e-6 on a 0.2 A grid)."""
+    from oracle.narrowband import narrowband, sigma_of_fwhm
+    from scipy.special import erf
+    lam0, fwhm, dl = 1215.67, 35.0, 30.0
+    s = sigma_of_fwhm(fwhm)
+    assert abs(2 * np.sqrt(2 * np.log(2)) * s - fwhm) < 1e-12
+    lam = lam0 + np.concatenate([-np.geomspace(20, 1.5, 8), np.linspace(-1.4, 1.4, 9), np.geomspace(1.5, 20, 8)])
+    X = np.full((lam.size, 4), 0.7)
+    np.testing.assert_allclose(narrowband(lam, X, lam0, fwhm, dl), 0.7 * erf(dl / (np.sqrt(2) * s)), rtol=1e-10)
+    lam = lam0 + np.linspace(-40.0, 40.0, 161)
+    X = np.stack([lam - lam0, (lam - lam0) ** 3] * 2, axis=1)
+    assert np.max(np.abs(narrowband(lam, X, lam0, fwhm, dl))) < 1e-9 * np.max(np.abs(X))
+    lam = lam0 + np.arange(-40.0, 40.0 + 1e-9, 0.2)
+    tau = 3.0
+    X = np.exp(-0.5 * ((lam - lam0) / tau) ** 2)[:, None] * np.ones(4)
+    rho = 1.0 / np.sqrt(1.0 / s ** 2 + 1.0 / tau ** 2)
+    np.testing.assert_allclose(narrowband(lam, X, lam0, fwhm, dl), rho / s * erf(dl / (np.sqrt(2) * rho)),
+                               rtol=1e-6)

@@ -1,8 +1,13 @@
-"""Fault paths of the C ABI on a set-up context (two-level slab, FP64), none
-of which launches a kernel on invalid memory: arguments rejected on the host
-(NULL, non-positive tolerance, zero iterations, calls before prd_setup), a
-start vector holding NaN (the solve stops with PRD_E_NAN), and an iteration
-cap below what the tolerance needs (PRD_E_NOCONV, with the iterate kept)."""
+"""Fault paths of the C ABI on a set-up context (two-level slab, FP64, and a
+reduced H I case in FP32), none of which launches a kernel on invalid memory:
+arguments rejected on the host (NULL, non-positive tolerance, zero
+iterations, calls before prd_setup), a start vector holding NaN (the solve
+stops with PRD_E_NAN), an iteration cap below what the tolerance needs
+(PRD_E_NOCONV, with the iterate kept), an Arnoldi breakdown on an injected
+zero operator (PRD_E_BREAKDOWN), and the bounded waits of the tensor-core
+contraction running out (PRD_E_TIMEOUT from prd_device_status; the waits are
+given a few polls, every thread block drains what it issued, and the context
+applies correctly afterwards)."""
 import ctypes
 
 import numpy as np
@@ -13,7 +18,8 @@ from paper_2505_20968_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-E_ARG, E_STATE, E_NOCONV, E_NAN = -1, -2, -5, -7
+E_ARG, E_STATE, E_NOCONV, E_BREAKDOWN, E_NAN, E_TIMEOUT = -1, -2, -5, -6, -7, -8
+OPT_WAIT_POLLS, OPT_TEST_ZERO_OPERATOR = 3, 4
 
 
 def _case():
@@ -59,4 +65,45 @@ def test_iteration_cap_reports_no_convergence():
     assert info["rc"] == E_NOCONV and info["iters"] == 1, info
     assert bool(torch.isfinite(x).all()) and float(x.abs().max()) > 0   # the iterate is kept
     assert info["true_rel_res"] > 1e-14
+    P.close()
+
+
+def test_breakdown_on_injected_zero_operator():
+    """With the operator replaced by the zero map, the first Arnoldi vector
+    is annihilated (h_10 = 0): GMRES stops at the breakdown with the residual
+    still ||b||, returns PRD_E_BREAKDOWN and keeps a finite iterate; with the
+    operator restored the same context solves."""
+    from paper_2505_20968_gb300.binding import PRD, lib
+    P = PRD(_case(), precision="fp64", device=0)
+    assert lib().prd_set_option(P.h, OPT_TEST_ZERO_OPERATOR, 1) == 0
+    x, info = P.solve(tol=1e-10, max_iter=50, restart=20, check=False)
+    assert info["rc"] == E_BREAKDOWN, info
+    assert info["true_rel_res"] > 0.5 and bool(torch.isfinite(x).all())
+    assert lib().prd_set_option(P.h, OPT_TEST_ZERO_OPERATOR, 0) == 0
+    x, info = P.solve(tol=1e-10, max_iter=200, restart=40)
+    assert info["rc"] == 0 and info["true_rel_res"] < 1e-10
+    P.close()
+
+
+def test_contraction_wait_expiry_reports_timeout():
+    """The tensor-core contraction with its pipeline waits limited to 4 polls:
+    the first waits run out before the first bulk copies land, so thread
+    blocks stop, drain the copies and products they issued (those waits keep
+    the default limit) and record the failure: prd_device_status returns
+    PRD_E_TIMEOUT.  With the default limit restored the same context gives
+    the emissivity of a fresh apply again (to FP32 summation order)."""
+    from paper_2505_20968_gb300.binding import PRD, lib
+    cfg = inputs.hi_lya(n_z=4, n_core=13, n_wing=8, n_mu_half=2, n_chi=4, seed=31)
+    P = PRD(cfg, device=0)
+    x = torch.from_numpy(inputs.seeded_vector(P.shape, 3, 0.1, 1.0)).to(P.device, P.dtype)
+    ref = P.apply_sigma(x).clone()
+    P.device_status()
+    assert lib().prd_set_option(P.h, OPT_WAIT_POLLS, 4) == 0
+    P.apply_sigma(x)
+    assert lib().prd_device_status(P.h) == E_TIMEOUT
+    assert lib().prd_device_status(P.h) == 0                      # reported once
+    assert lib().prd_set_option(P.h, OPT_WAIT_POLLS, 0) == 0
+    out = P.apply_sigma(x)
+    P.device_status()
+    assert torch.max(torch.abs(out - ref)).item() <= 1e-6 * torch.max(torch.abs(ref)).item()
     P.close()
