@@ -260,7 +260,7 @@ def main():
                     help="GMRES tol; 1e-10 is the largest meeting 1e-5 on emergent I in the Mg II parity case")
     ap.add_argument("--workload", default="mgii", choices=["mgii", "mgii_small", "lambda_wide"],
                     help="mgii_small (8 heights) is only for ncu captures of single kernels; lambda_wide "
-                         "(two-level, angle-averaged, 300 heights x 128 directions x 256 frequencies) sizes "
+                         "(two-level, angle-averaged, 300 heights x 128 directions x 200 frequencies) sizes "
                          "the formal-solution sweep beyond L2 for its HBM capture")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -270,7 +270,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload == "lambda_wide":
-        cfg = inputs.twolevel_slab(n_z=300, n_x=256, n_mu_half=8, n_chi=8, seed=2 + rank)
+        cfg = inputs.twolevel_slab(n_z=300, n_x=200, n_mu_half=8, n_chi=8, seed=2 + rank)
         cfg["quad"]["mode"] = inputs.MODE_AA
         cfg["precision"] = "fp32"
     else:

@@ -117,6 +117,19 @@ int prd_set_atmosphere(prd_ctx* ctx, int nz, const double* z_km, const double* T
                        const double* B_G, const double* thetaB, const double* chiB,
                        const double* v_kms);
 
+/* Continuum processes (App. A), optional: per height and frequency, arrays
+ * [nz][nnu] of the continuum absorption kappa_c and scattering sigma_c
+ * coefficients (km^-1, as k_line) and the thermal continuum emissivity.
+ * kappa_c + sigma_c adds to the diagonal of K (no continuum dichroism or
+ * dispersion), the thermal emissivity to Stokes I, and sigma_c scatters
+ * coherently in the observer frame with the dipole phase matrix:
+ *     eps_c(Omega, nu) = sigma_c(nu) oint P(Omega, Omega') I(Omega', nu) dOmega'/4pi.
+ * The Kirchhoff factor f normalises the line emissivity alone.  Call after
+ * prd_set_atmosphere and prd_set_quadrature and before prd_setup; three
+ * NULLs remove the continuum.  The transposed operator, the adjoint solve and
+ * prd_grad_B are built without continuum and return PRD_E_STATE with it. */
+int prd_set_continuum(prd_ctx* ctx, const double* kappa_c, const double* sigma_c, const double* eps_c_th);
+
 /* Frequency and angular quadrature (Sects. 2.6, 4.2, 4.3).  grid: nnu ascending
  * values, vacuum wavelengths in Angstrom (PRD_GRID_LAMBDA) or reduced
  * frequencies x with nu = nu0 - x dnu_D(z_0) (PRD_GRID_X).  mu_rule
@@ -220,9 +233,18 @@ int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
  * each inner FP32 GMRES solve of the mixed-precision refinement, in units of
  * 1e-8 (default 3000: 3e-5); the inner tolerance is max(0.3 tol / res, floor)
  * with res the current FP64 relative residual.  It trades outer FP64
- * residuals against inner iterations, never the accuracy of the result. */
+ * residuals against inner iterations, never the accuracy of the result.
+ * PRD_OPT_FORMAL_SOLVER: PRD_DELO_LINEAR (default; the source vector and the
+ * K'I term linear over a step) or PRD_DELOPAR (Sect. 3: the source vector
+ * parabolic through the upwind, current and downwind points, K'I linear;
+ * linear on the last step of a ray).  Both are linear in the emissivity, so
+ * GMRES applies to either; every formal solution (Lambda, the right-hand
+ * side, emergent Stokes vectors, the refinement residuals) uses the choice.
+ * The transposed operator, the adjoint solve and prd_grad_B are built for
+ * DELO-linear and return PRD_E_STATE under PRD_DELOPAR. */
 enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2, PRD_OPT_WAIT_POLLS = 3, PRD_OPT_TEST_ZERO_OPERATOR = 4,
-       PRD_OPT_REFINE_FLOOR = 5 };
+       PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6 };
+enum { PRD_DELO_LINEAR = 0, PRD_DELOPAR = 1 };
 int prd_set_option(prd_ctx* ctx, int option, int value);
 /* Synchronise the ctx stream and report device-side failures: a CUDA error,
  * or PRD_E_TIMEOUT if a bounded wait inside a kernel expired since the last

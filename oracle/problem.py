@@ -34,6 +34,16 @@ Propagation matrix from the forward-scattering amplitude (LL04 Ch. 7, cited in
 Sect. 2.2): kappa = k/(2 sqrt(pi)(2S+1)) sum_{k_u k_l} (a_l^*)(a_l)^T W(x)^*,
 K_ij = 1/2 Tr(sigma_i kappa sigma_j + sigma_i sigma_j kappa^+); then
 eps_th = eps W_T (K_11, K_21, K_31, K_41) (Sect. 2.3).
+
+Continuum (App. A, optional atmosphere arrays kappa_c, sigma_c, eps_c_th of
+shape [z, nu], km^-1 like k_line): eta_c = kappa_c + sigma_c is added to the
+diagonal of K; the thermal continuum emissivity to Stokes I of eps_th; and
+coherent scattering in the observer frame,
+    eps_c(Omega, nu) = sigma_c(nu) oint P(Omega, Omega') I(Omega', nu) dOmega'/4pi,
+with P the dipole (Rayleigh) phase matrix P_ij = 3/4 Tr(sigma_i J sigma_j J^T),
+J_ab = e_a(Omega) . e_b(Omega') (the sum over K <= 2 of (-1)^Q T^K_Q T^K_-Q of
+App. A with every W_K = 1).  The Kirchhoff factor f normalises the line part
+only, with the line's eta_I.
 """
 import numpy as np
 from . import constants as C
@@ -77,9 +87,36 @@ def delo_coeffs(d):
     return e, alpha, beta
 
 
+def delopar_coeffs(dM, dP):
+    """Weights (psi_M, psi_O, psi_P) of the upwind, current and downwind source
+    values for one step of DELOPAR: the source vector is the parabola through
+    the three points and its contribution int_0^dM e^{-t} S(t) dt is taken
+    exactly, t measured from the current point back towards the upwind one
+    (upwind at t = dM, downwind at t = -dP).  From the moments
+    I_n = int_0^dM t^n e^{-t} dt = n! P(n + 1, dM) (regularised incomplete
+    gamma) and the Lagrange basis through t = dM, 0, -dP."""
+    from scipy.special import gammainc
+    dM = np.asarray(dM, dtype=np.float64)
+    dP = np.asarray(dP, dtype=np.float64)
+    I0 = gammainc(1.0, dM)
+    I1 = gammainc(2.0, dM)
+    I2 = 2.0 * gammainc(3.0, dM)
+    psiM = (I2 + dP * I1) / (dM * (dM + dP))
+    psiO = -(I2 + (dP - dM) * I1 - dM * dP * I0) / (dM * dP)
+    psiP = (I2 - dM * I1) / (dP * (dM + dP))
+    return psiM, psiO, psiP
+
+
 class Problem:
-    def __init__(self, cfg, mode=None, normalise=True):
+    # formal solvers: DELO-linear (source vector and K'I linear over a step) and
+    # DELOPAR (source vector parabolic through the upwind, current and downwind
+    # points, K'I linear; linear at the last point of a ray)
+    FORMAL_SOLVERS = ("delo_linear", "delopar")
+
+    def __init__(self, cfg, mode=None, normalise=True, formal_solver="delo_linear"):
         self.cfg = cfg
+        assert formal_solver in self.FORMAL_SOLVERS
+        self.formal_solver = formal_solver
         atom, atm, quad = cfg["atom"], cfg["atm"], cfg["quad"]
         self.atom = atom
         self.mode = quad.get("mode", 0) if mode is None else mode
@@ -110,6 +147,10 @@ class Problem:
         self.rE = np.asarray(atm["r_el"], float)
         self.k = np.asarray(atm["k_line"], float)
         self.WT = np.asarray(atm["W_T"], float)
+        zn = (nz, self.nN)
+        self.kap_c = np.asarray(atm.get("kappa_c", np.zeros(zn)), float).reshape(zn)
+        self.sig_c = np.asarray(atm.get("sigma_c", np.zeros(zn)), float).reshape(zn)
+        self.epsc_th = np.asarray(atm.get("eps_c_th", np.zeros(zn)), float).reshape(zn)
         v = np.asarray(atm["v_kms"], float)
         self.ub = (v @ self.nvec.T) / self.vD_kms[:, None]           # [z, Omega]
         # atom per height
@@ -174,8 +215,12 @@ class Problem:
             for o in range(nO):
                 self.K[iz, o] = self.K_from_kappa(self.kappa(iz, self.amp[iz][o], self.ub[iz, o],
                                                              self.u[iz]))
-        self.eta1 = self.K[..., 0, 0]
+        self.eta1_line = self.K[..., 0, 0].copy()
         self.eps_th = (self.eps * self.WT)[:, None, None, None] * self.K[..., :, 0]
+        for s_ in range(4):
+            self.K[..., s_, s_] += (self.kap_c + self.sig_c)[:, None, :]
+        self.eta1 = self.K[..., 0, 0]
+        self.eps_th[..., 0] += self.epsc_th[:, None, :]
 
     # ------------------------------------------------------------------ Lambda
     def _build_delo(self):
@@ -190,7 +235,11 @@ class Problem:
                 self.dtau[k1, o] = 0.5 * (self.eta1[k0, o] + self.eta1[k1, o]) * abs(z[k1] - z[k0]) / abs(mu)
 
     def formal_solution(self, eps, boundary=False, K=None, eta1=None, dtau=None, mu=None):
-        """I = Lambda eps (+ t if boundary): DELO-linear along every ray (Sect. 3)."""
+        """I = Lambda eps (+ t if boundary) along every ray (Sect. 3), with the
+        problem's formal solver: DELO-linear,
+            (Id + b K'_k) I_k = (e Id - a K'_{k-1}) I_{k-1} + a S_{k-1} + b S_k,
+        or DELOPAR, whose source terms are psi_M S_{k-1} + psi_O S_k + psi_P S_{k+1}
+        (delopar_coeffs; DELO-linear's a, b at the last point of the ray)."""
         K = self.K if K is None else K
         eta1 = self.eta1 if eta1 is None else eta1
         dtau = self.dtau if dtau is None else dtau
@@ -215,8 +264,14 @@ class Problem:
                 S0 = eps[k0, o] / eta1[k0, o][:, None]
                 S1 = eps[k1, o] / eta1[k1, o][:, None]
                 lhs = Id[None] + be[:, None, None] * Kp1
-                rhs = np.einsum("nij,nj->ni", e[:, None, None] * Id[None] - al[:, None, None] * Kp0, I) \
-                    + al[:, None] * S0 + be[:, None] * S1
+                rhs = np.einsum("nij,nj->ni", e[:, None, None] * Id[None] - al[:, None, None] * Kp0, I)
+                if self.formal_solver == "delopar" and p + 1 < nz:
+                    k2 = order[p + 1]
+                    pM, pO, pP = delopar_coeffs(dtau[k1, o], dtau[k2, o])
+                    S2 = eps[k2, o] / eta1[k2, o][:, None]
+                    rhs = rhs + pM[:, None] * S0 + pO[:, None] * S1 + pP[:, None] * S2
+                else:
+                    rhs = rhs + al[:, None] * S0 + be[:, None] * S1
                 I = np.linalg.solve(lhs, rhs[..., None])[..., 0]
                 out[k1, o] = I
                 k0 = k1
@@ -298,7 +353,23 @@ class Problem:
     def interp_back(self, iz, o):
         return self.spl[iz].basis(self.u[iz] + self.ub[iz, o])
 
-    def sigma_matrix(self, iz, normalised=True):
+    @staticmethod
+    def rayleigh(mu_o, chi_o, mu_p, chi_p):
+        """Dipole phase matrix P[i, j] from direction Omega' (mu_p, chi_p) into
+        Omega (mu_o, chi_o), normalised to oint P_00 dOmega'/4pi = 1."""
+        eo, ep = pol_basis(mu_o, chi_o), pol_basis(mu_p, chi_p)
+        J = np.array([[eo[a] @ ep[b] for b in range(2)] for a in range(2)])
+        P = 0.75 * np.einsum("iab,bc,jcd,ad->ij", SIG, J, SIG, J)    # Tr(sigma_i J sigma_j J^T)
+        assert np.max(np.abs(P.imag)) < 1e-13
+        return P.real
+
+    def continuum_block(self, iz, mu_o, chi_o):
+        """sigma_c-weighted continuum scattering into one direction:
+        C[n, i, o', j] with eps_c(n, i) = sum C[n, i, o', j] I(o', n, j)."""
+        P = np.stack([self.rayleigh(mu_o, chi_o, self.mu[p], self.chi[p]) * self.wang[p] for p in range(self.nO)])
+        return self.sig_c[iz][:, None, None, None] * P.transpose(1, 0, 2)[None]
+
+    def sigma_matrix(self, iz, normalised=True, continuum=True):
         nO, N = self.nO, self.nN
         Sb = self.sigma_bar(iz).reshape(nO, N, 4, nO, N, 4)
         Uin = np.stack([self.interp_in(iz, o) for o in range(nO)])      # [o', m, n']
@@ -307,6 +378,11 @@ class Problem:
         S = S.reshape(nO, N, 4, nO, N, 4)
         if normalised:
             S[:, :, 0] *= self.f[iz][:, :, None, None, None]
+        if continuum and np.any(self.sig_c[iz]):
+            for o in range(nO):
+                C = self.continuum_block(iz, self.mu[o], self.chi[o])           # [n, i, o', j]
+                for n in range(N):
+                    S[o, n, :, :, n, :] += C[n]
         return S.reshape(nO * N * 4, nO * N * 4)
 
     def sigma_sample(self, x, iz, o):
@@ -325,8 +401,9 @@ class Problem:
         Ub = self.interp_back(iz, o)
         eps = Ub @ sb
         num = (Ub @ sw)[:, 0]
-        f = (1.0 - self.eps[iz]) * self.WT[iz] * self.eta1[iz, o] / num
+        f = (1.0 - self.eps[iz]) * self.WT[iz] * self.eta1_line[iz, o] / num
         eps[:, 0] *= f
+        eps += np.einsum("nipj,pnj->ni", self.continuum_block(iz, self.mu[o], self.chi[o]), x[iz])
         return eps, f
 
     def lambda_ray(self, eps, o, n):
@@ -350,6 +427,7 @@ class Problem:
             amp = self.amplitudes(iz, mu, chi)
             ub = (v[iz] @ n_l) / self.vD_kms[iz]
             K[iz, 0] = self.K_from_kappa(self.kappa(iz, amp, ub, self.u[iz]))
+            eta_line = K[iz, 0, :, 0, 0].copy()
             sb = np.zeros((N, 4))
             sw = np.zeros((N, 4))
             Il = np.zeros((N, 4))
@@ -363,9 +441,13 @@ class Problem:
                 sw += (blk @ (Uin @ Il).ravel()).reshape(N, 4)
             Ub = self.spl[iz].basis(self.u[iz] + ub)
             e = Ub @ sb
-            f = (1.0 - self.eps[iz]) * self.WT[iz] * K[iz, 0, :, 0, 0] / (Ub @ sw)[:, 0]
+            f = (1.0 - self.eps[iz]) * self.WT[iz] * eta_line / (Ub @ sw)[:, 0]
             e[:, 0] *= f
             eps[iz, 0] = e + (self.eps[iz] * self.WT[iz]) * K[iz, 0, :, :, 0]
+            eps[iz, 0, :, 0] += self.epsc_th[iz]
+            eps[iz, 0] += np.einsum("nipj,pnj->ni", self.continuum_block(iz, mu, chi), x[iz])
+            for s_ in range(4):
+                K[iz, 0, :, s_, s_] += self.kap_c[iz] + self.sig_c[iz]
         eta1 = K[..., 0, 0]
         dtau = np.zeros((nz, 1, N))
         for k in range(1, nz):
@@ -378,8 +460,8 @@ class Problem:
         for iz in range(self.nz):
             Il = np.zeros((self.nO, self.nN, 4))
             Il[..., 0] = self.WT[iz]
-            num = (self.sigma_matrix(iz, normalised=False) @ Il.ravel()).reshape(self.nO, self.nN, 4)
-            ref = (1.0 - self.eps[iz]) * self.WT[iz] * self.eta1[iz]
+            num = (self.sigma_matrix(iz, normalised=False, continuum=False) @ Il.ravel()).reshape(self.nO, self.nN, 4)
+            ref = (1.0 - self.eps[iz]) * self.WT[iz] * self.eta1_line[iz]
             f[iz] = ref / num[..., 0]
         return f
 

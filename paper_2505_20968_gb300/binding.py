@@ -40,7 +40,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
            "prd_device_status", "prd_contraction_work",
            "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch",
-           "prd_grad_B", "prd_set_allocator", "prd_narrowband"]
+           "prd_grad_B", "prd_set_allocator", "prd_narrowband", "prd_set_continuum"]
 
 
 def lib():
@@ -61,6 +61,7 @@ def lib():
         L.prd_set_atom.argtypes = [P, ctypes.POINTER(_Atom)]
         L.prd_set_atmosphere.argtypes = [P, I] + [DP] * 12
         L.prd_set_quadrature.argtypes = [P, I, DP, I, I, I, I, I]
+        L.prd_set_continuum.argtypes = [P, DP, DP, DP]
         L.prd_setup.argtypes = [P]
         L.prd_sizes.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                 ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]
@@ -145,6 +146,9 @@ class PRD:
         g, gp = _dp(q["grid"])
         self._check(L.prd_set_quadrature(self.h, len(g), gp, q["grid_kind"], q["n_mu_half"], q["n_chi"],
                                          q.get("mu_rule", 0), q.get("mode", 0) if mode is None else mode))
+        if "sigma_c" in atm:
+            cont = [_dp(atm[k]) for k in ("kappa_c", "sigma_c", "eps_c_th")]
+            self._check(L.prd_set_continuum(self.h, *[p for _, p in cont]))
         self._alloc = None
         self.alloc_stats = {"bytes": 0, "live": {}, "n_alloc": 0, "n_free": 0}
         if allocator == "torch":

@@ -67,7 +67,7 @@ static void free_all(Ctx* c) {
                   &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
                   &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
                   &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64, &c->r3out64,
-                  &c->r3prof64, &c->r3ab64};
+                  &c->r3prof64, &c->r3ab64, &c->par, &c->eta_line, &c->cont_pw, &c->cont_sig};
   c->has64 = false;
   c->tc_ready = false;
   for (DBuf* b : bufs) dfree(*b);
@@ -291,11 +291,35 @@ int prd_set_quadrature(prd_ctx* ctx, int nnu, const double* grid, int grid_kind,
   return PRD_OK;
 }
 
+int prd_set_continuum(prd_ctx* ctx, const double* kappa_c, const double* sigma_c, const double* eps_c_th) {
+  CTX_OR_ARG(ctx);
+  if (!kappa_c && !sigma_c && !eps_c_th) {
+    c->kapc.clear(); c->sigc.clear(); c->epsc.clear();
+    c->ready = false;
+    return PRD_OK;
+  }
+  if (!kappa_c || !sigma_c || !eps_c_th) return fail(c, PRD_E_ARG, "continuum: give all three arrays or none");
+  if (!c->have_atm || !c->have_quad) return fail(c, PRD_E_STATE, "continuum: set the atmosphere and quadrature first");
+  const size_t n = (size_t)c->nz * c->nnu;
+  for (size_t i = 0; i < n; ++i)
+    if (!(kappa_c[i] >= 0) || !(sigma_c[i] >= 0) || !(eps_c_th[i] >= 0))
+      return fail(c, PRD_E_ARG, "continuum coefficients must be finite and non-negative");
+  c->kapc.assign(kappa_c, kappa_c + n);
+  c->sigc.assign(sigma_c, sigma_c + n);
+  c->epsc.assign(eps_c_th, eps_c_th + n);
+  c->cont_nz = c->nz;
+  c->cont_nnu = c->nnu;
+  c->ready = false;
+  return PRD_OK;
+}
+
 int prd_setup(prd_ctx* ctx) {
   CTX_OR_ARG(ctx);
   if (!c->have_atom || !c->have_atm || !c->have_quad)
     return fail(c, PRD_E_STATE, "set_atom, set_atmosphere and set_quadrature must precede setup");
   if (c->grid_kind == PRD_GRID_LAMBDA && !(c->grid[0] > 0)) return fail(c, PRD_E_ARG, "wavelengths must be positive");
+  if (c->has_cont() && (c->cont_nz != c->nz || c->cont_nnu != c->nnu))
+    return fail(c, PRD_E_STATE, "continuum arrays were set for another atmosphere or frequency grid");
   try {
     return prd::setup(c);
   } catch (const std::exception& e) {
@@ -335,7 +359,8 @@ int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
                              &c->cls_dev, &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M,
                              &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t, &c->dmu, &c->pc_s1, &c->pc_s2,
                              &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64,
-                             &c->r3out64, &c->r3prof64, &c->r3ab64};
+                             &c->r3out64, &c->r3prof64, &c->r3ab64, &c->par, &c->eta_line, &c->cont_pw,
+                             &c->cont_sig};
   int64_t s = 0;
   for (auto* b : bufs) s += (int64_t)b->bytes;
   *bytes = s;
@@ -427,6 +452,9 @@ int prd_solve(prd_ctx* ctx, double tol, int max_iter, int restart, const void* x
 int prd_grad_B(prd_ctx* ctx, const void* x_dev, const void* dJdI_dev, double* dJ_dp) {
   CTX_OR_ARG(ctx);
   NEED_READY();
+  if (c->formal != PRD_DELO_LINEAR)
+    return fail(c, PRD_E_STATE, "the transposed operator is built for the DELO-linear formal solver");
+  if (c->has_cont()) return fail(c, PRD_E_STATE, "the transposed operator is built without continuum");
   if (!x_dev || !dJdI_dev || !dJ_dp) return fail(c, PRD_E_ARG, "NULL argument");
   NEED_ALIGNED(x_dev);
   NEED_ALIGNED(dJdI_dev);
@@ -478,6 +506,9 @@ int prd_solve_batch(prd_ctx* const* ctxs, int n, double tol, int max_iter, int r
 int prd_apply_operator_T(prd_ctx* ctx, const void* x_dev, void* y_dev) {
   CTX_OR_ARG(ctx);
   NEED_READY();
+  if (c->formal != PRD_DELO_LINEAR)
+    return fail(c, PRD_E_STATE, "the transposed operator is built for the DELO-linear formal solver");
+  if (c->has_cont()) return fail(c, PRD_E_STATE, "the transposed operator is built without continuum");
   if (!x_dev || !y_dev) return fail(c, PRD_E_ARG, "NULL vector");
   NEED_ALIGNED(x_dev);
   NEED_ALIGNED(y_dev);
@@ -492,6 +523,9 @@ int prd_solve_adjoint(prd_ctx* ctx, const void* g_dev, double tol, int max_iter,
                       int* iters, double* true_rel_res, double* res_history) {
   CTX_OR_ARG(ctx);
   NEED_READY();
+  if (c->formal != PRD_DELO_LINEAR)
+    return fail(c, PRD_E_STATE, "the transposed operator is built for the DELO-linear formal solver");
+  if (c->has_cont()) return fail(c, PRD_E_STATE, "the transposed operator is built without continuum");
   if (!g_dev || !lam_dev || !(tol > 0) || max_iter < 1 || restart < 1)
     return fail(c, PRD_E_ARG, "bad adjoint solve arguments");
   NEED_ALIGNED(g_dev);
@@ -557,6 +591,11 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
   if (option == PRD_OPT_REFINE_FLOOR) {
     if (value < 1 || value > 1000000) return fail(c, PRD_E_ARG, "refinement floor must be in [1, 1e6] x 1e-8");
     c->refine_floor = value * 1e-8;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_FORMAL_SOLVER) {
+    if (value != PRD_DELO_LINEAR && value != PRD_DELOPAR) return fail(c, PRD_E_ARG, "unknown formal solver");
+    c->formal = value;
     return PRD_OK;
   }
   if (option == PRD_OPT_TEST_ZERO_OPERATOR) {

@@ -50,6 +50,61 @@ void delo(double d, double* e, double* al, double* be) {
 
 }  // namespace
 
+// DELOPAR source weights for a step of optical thickness dM (upwind point at
+// t = dM, current point at t = 0) and the next step downwind of thickness dP
+// (downwind point at t = -dP): psi_j = int_0^dM e^{-t} L_j(t) dt with L_j the
+// quadratic Lagrange basis through the three points.  The moments
+// J_n = int_0^dM t^n e^{-t} dt come from their power series for small dM
+// (alternating, terms dM^(n+1+k) / (k! (n+1+k))) and in closed form otherwise.
+void delopar_weights(double dM, double dP, double* psi) {
+  double J0, J1, J2;
+  if (dM < 0.5) {
+    J0 = J1 = J2 = 0.0;
+    double term = 1.0;                     // (-1)^k dM^k / k!
+    for (int k = 0; k < 30; ++k) {
+      J0 += term * std::pow(dM, 1) / (1 + k);
+      J1 += term * std::pow(dM, 2) / (2 + k);
+      J2 += term * std::pow(dM, 3) / (3 + k);
+      term *= -dM / (k + 1);
+    }
+  } else {
+    const double e = std::exp(-dM);
+    J0 = 1.0 - e;
+    J1 = 1.0 - e * (1.0 + dM);
+    J2 = 2.0 - e * (dM * dM + 2.0 * dM + 2.0);
+  }
+  psi[0] = (J2 + dP * J1) / (dM * (dM + dP));
+  psi[1] = (dM * dP * J0 - J2 - (dP - dM) * J1) / (dM * dP);
+  psi[2] = (J2 - dM * J1) / (dP * (dM + dP));
+}
+
+// Dipole phase matrix of coherent continuum scattering (App. A: the sum over
+// K <= 2 of (-1)^Q T^K_Q(o) T^K_-Q(o') with every W_K = 1): the field scattered
+// into o is the projection of the incident one, J_ab = e_a(o) . e_b(o') in the
+// polarisation bases of the two directions (e_a parallel to the limb), and
+// P_ij = 3/4 Tr(sig_i J sig_j J^T), normalised to oint P_00 dOmega'/4pi = 1.
+void dipole_phase(double mu_o, double chi_o, double mu_p, double chi_p, double* P) {
+  auto basis = [](double mu, double chi, double e[2][3]) {
+    const double s = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+    e[0][0] = -std::sin(chi); e[0][1] = std::cos(chi); e[0][2] = 0.0;
+    e[1][0] = mu * std::cos(chi); e[1][1] = mu * std::sin(chi); e[1][2] = -s;
+  };
+  double eo[2][3], ep[2][3], J[2][2];
+  basis(mu_o, chi_o, eo);
+  basis(mu_p, chi_p, ep);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) J[a][b] = eo[a][0] * ep[b][0] + eo[a][1] * ep[b][1] + eo[a][2] * ep[b][2];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cplx tr = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          for (int cc = 0; cc < 2; ++cc)
+            for (int d = 0; d < 2; ++d) tr += sig(i, a, b) * J[b][cc] * sig(j, cc, d) * J[a][d];
+      P[i * 4 + j] = 0.75 * tr.real();
+    }
+}
+
 // Outgoing factor O_i(o; ku, kv, kl') = sum_ab a_b(kv,kl') sig_i[b][a] conj(a_a(ku,kl'))
 // Incoming factor I_j(o'; ku, kv, kl) = sum_gd conj(a_d(kv,kl)) sig_j[g][d] a_g(ku,kl)
 static void phase_factors_amp(const Ctx* c, const cplx* A, std::vector<cplx>& O, std::vector<cplx>& I) {
@@ -130,6 +185,13 @@ void los_tables(const Ctx* c, double mu, double chi, LosTables& L) {
   L.epsth.assign((size_t)nz * N * 4, 0.0);
   L.kidx.assign((size_t)nz * N, 0);
   L.tt.assign((size_t)nz * N, 0.0);
+  L.eta_line.assign((size_t)nz * N, 0.0);
+  L.cont_pw.assign((size_t)nO * 16, 0.0);
+  if (c->has_cont())
+    for (int op = 0; op < nO; ++op) {
+      dipole_phase(mu, chi, c->mu[op], c->chi[op], &L.cont_pw[(size_t)op * 16]);
+      for (int e = 0; e < 16; ++e) L.cont_pw[(size_t)op * 16 + e] *= c->wang[op];
+    }
   std::vector<double> eta((size_t)nz * N);
   for (int iz = 0; iz < nz; ++iz) {
     std::vector<cplx> A((size_t)2 * nu_ * nl);
@@ -168,13 +230,19 @@ void los_tables(const Ctx* c, double mu, double chi, LosTables& L) {
     for (int n = 0; n < N; ++n) {
       double K[4][4];
       kmatrix(c, iz, A.data(), ub, u[n], K);
+      L.eta_line[(size_t)iz * N + n] = K[0][0];
+      for (int s = 0; s < 4; ++s) L.epsth[((size_t)iz * N + n) * 4 + s] = c->eps[iz] * c->WT[iz] * K[s][0];
+      if (c->has_cont()) {
+        const size_t q = (size_t)iz * N + n;
+        for (int s = 0; s < 4; ++s) K[s][s] += c->kapc[q] + c->sigc[q];
+        L.epsth[q * 4] += c->epsc[q];
+      }
       const double e1 = K[0][0];
       double* t = &L.kt[((size_t)iz * N + n) * 10];
       t[0] = K[0][1] / e1; t[1] = K[0][2] / e1; t[2] = K[0][3] / e1;
       t[3] = K[1][2] / e1; t[4] = K[1][3] / e1; t[5] = K[2][3] / e1;
       t[6] = 1.0 / e1;
       eta[(size_t)iz * N + n] = e1;
-      for (int s = 0; s < 4; ++s) L.epsth[((size_t)iz * N + n) * 4 + s] = c->eps[iz] * c->WT[iz] * K[s][0];
       const double x = u[n] + ub;
       int kk;
       double tv = 0.0;
@@ -190,15 +258,22 @@ void los_tables(const Ctx* c, double mu, double chi, LosTables& L) {
       L.tt[(size_t)iz * N + n] = tv;
     }
   }
-  // DELO weights along the line of sight (upward, mu > 0)
+  // DELO weights along the line of sight (upward, mu > 0), and DELOPAR's
+  L.par.assign((size_t)nz * N * 3, 0.0);
+  auto dtau = [&](int n, int p) {
+    return 0.5 * (eta[(size_t)(p - 1) * N + n] + eta[(size_t)p * N + n]) * std::fabs(c->z[p] - c->z[p - 1]) / mu;
+  };
   for (int n = 0; n < N; ++n)
     for (int p = 1; p < nz; ++p) {
-      const double d = 0.5 * (eta[(size_t)(p - 1) * N + n] + eta[(size_t)p * N + n]) * std::fabs(c->z[p] - c->z[p - 1]) / mu;
+      const double d = dtau(n, p);
       double e, a, b;
       delo(d, &e, &a, &b);
       L.kt[((size_t)p * N + n) * 10 + 7] = e;
       L.kt[((size_t)p * N + n) * 10 + 8] = a;
       L.kt[((size_t)p * N + n) * 10 + 9] = b;
+      double* ps = &L.par[((size_t)p * N + n) * 3];
+      if (p + 1 < nz) delopar_weights(d, dtau(n, p + 1), ps);
+      else { ps[0] = a; ps[1] = b; ps[2] = 0.0; }
     }
 }
 
@@ -206,7 +281,7 @@ int build_device_tables(Ctx* c) {
   const int nz = c->nz, nO = c->nO, N = c->nnu, nu_ = c->nu_st, nl = c->nl_st;
   const double S2 = (c->atom.twoS == 1) ? 2.0 : 1.0;
   const size_t npt = (size_t)nz * nO * N;
-  std::vector<double> kt(npt * 10), epsth(npt * 4), eta(npt);
+  std::vector<double> kt(npt * 10), epsth(npt * 4), eta(npt), etal(npt);
   // ---- propagation matrix from the forward-scattering amplitude
 #pragma omp parallel for schedule(dynamic)
   for (int iz = 0; iz < nz; ++iz) {
@@ -242,29 +317,45 @@ int build_device_tables(Ctx* c) {
             K[i][j] = 0.5 * tr.real();
           }
         const size_t pt = ((size_t)iz * nO + o) * N + n;
+        etal[pt] = K[0][0];
+        for (int s = 0; s < 4; ++s) epsth[pt * 4 + s] = c->eps[iz] * c->WT[iz] * K[s][0];
+        if (c->has_cont()) {
+          // continuum (App. A): extinction on the diagonal, thermal emission in Stokes I
+          const size_t q = (size_t)iz * N + n;
+          for (int s = 0; s < 4; ++s) K[s][s] += c->kapc[q] + c->sigc[q];
+          epsth[pt * 4] += c->epsc[q];
+        }
         const double e1 = K[0][0];
         eta[pt] = e1;
         double* t = &kt[pt * 10];
         t[0] = K[0][1] / e1; t[1] = K[0][2] / e1; t[2] = K[0][3] / e1;
         t[3] = K[1][2] / e1; t[4] = K[1][3] / e1; t[5] = K[2][3] / e1;
         t[6] = 1.0 / e1;
-        for (int s = 0; s < 4; ++s) epsth[pt * 4 + s] = c->eps[iz] * c->WT[iz] * K[s][0];
       }
     }
   }
-  // ---- DELO-linear weights of the step arriving at each point (Sect. 3)
+  // ---- DELO-linear weights of the step arriving at each point (Sect. 3), and the
+  // DELOPAR source weights of the same step (linear at the last point of a ray)
+  std::vector<double> par(npt * 3, 0.0);
   for (int o = 0; o < nO; ++o) {
     const bool up = c->mu[o] > 0;
+    // optical thickness of the step arriving at the p-th point along the ray
+    auto dtau = [&](int n, int p) {
+      const int k1 = up ? p : nz - 1 - p, k0 = up ? p - 1 : nz - p;
+      const size_t pt1 = ((size_t)k1 * nO + o) * N + n, pt0 = ((size_t)k0 * nO + o) * N + n;
+      return 0.5 * (eta[pt0] + eta[pt1]) * std::fabs(c->z[k1] - c->z[k0]) / std::fabs(c->mu[o]);
+    };
     for (int n = 0; n < N; ++n)
       for (int p = 0; p < nz; ++p) {
         const int k1 = up ? p : nz - 1 - p;
         const size_t pt1 = ((size_t)k1 * nO + o) * N + n;
         double e = 0, al = 0, be = 0;
         if (p > 0) {
-          const int k0 = up ? p - 1 : nz - p;
-          const size_t pt0 = ((size_t)k0 * nO + o) * N + n;
-          const double d = 0.5 * (eta[pt0] + eta[pt1]) * std::fabs(c->z[k1] - c->z[k0]) / std::fabs(c->mu[o]);
+          const double d = dtau(n, p);
           delo(d, &e, &al, &be);
+          double* ps = &par[pt1 * 3];
+          if (p + 1 < nz) delopar_weights(d, dtau(n, p + 1), ps);
+          else { ps[0] = al; ps[1] = be; ps[2] = 0.0; }
         }
         kt[pt1 * 10 + 7] = e;
         kt[pt1 * 10 + 8] = al;
@@ -272,7 +363,21 @@ int build_device_tables(Ctx* c) {
       }
   }
   int rc;
-  if ((rc = upload_T(c, c->kt, kt)) || (rc = upload_T(c, c->epsth, epsth))) return rc;
+  if ((rc = upload_T(c, c->kt, kt)) || (rc = upload_T(c, c->epsth, epsth)) || (rc = upload_T(c, c->par, par)) ||
+      (rc = upload(c, c->eta_line, etal.data(), npt * 8)))
+    return rc;
+  if (c->has_cont()) {
+    std::vector<double> pw((size_t)nO * nO * 16);
+    for (int o = 0; o < nO; ++o)
+      for (int op = 0; op < nO; ++op) {
+        double* P = &pw[((size_t)o * nO + op) * 16];
+        dipole_phase(c->mu[o], c->chi[o], c->mu[op], c->chi[op], P);
+        for (int e = 0; e < 16; ++e) P[e] *= c->wang[op];
+      }
+    if ((rc = upload(c, c->cont_pw, pw.data(), pw.size() * 8)) ||
+        (rc = upload(c, c->cont_sig, c->sigc.data(), c->sigc.size() * 8)))
+      return rc;
+  }
   {
     std::vector<double> ones(npt, 1.0);
     if ((rc = upload(c, c->f, ones.data(), npt * 8))) return rc;   // FP64 in both modes

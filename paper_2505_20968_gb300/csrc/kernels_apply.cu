@@ -452,10 +452,15 @@ __device__ __forceinline__ void kprime(const T* t, A K[4][4]) {
   K[2][3] = t[5]; K[3][2] = -t[5];
 }
 
+// Formal solution along every ray (Sect. 3): DELO-linear, or DELOPAR when
+// `par` holds the parabolic source weights (psi_M, psi_O, psi_P) of the step
+// arriving at each point (the source vector parabolic through the upwind,
+// current and downwind points; the K'I term stays linear, with DELO-linear's
+// a, b; the last point of a ray has psi = (a, b, 0)).
 template <typename T, typename A>
-__global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ mu,
-                            const A* __restrict__ x_sub, A* __restrict__ out, int nz, int nO, int N, int boundary,
-                            double WT0) {
+__global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt, const T* __restrict__ par,
+                            const double* __restrict__ mu, const A* __restrict__ x_sub, A* __restrict__ out, int nz,
+                            int nO, int N, int boundary, double WT0) {
   const int ray = blockIdx.x * blockDim.x + threadIdx.x;
   if (ray >= nO * N) return;
   const int o = ray / N, n = ray - o * N;
@@ -484,9 +489,24 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
       // cancellation I_{k-1} - S_k when I << S.
       const A e = t[7], al = t[8], be = t[9];
       const bool thick = e <= (A)0.5;
+      // source weights: DELO-linear (a, b, 0) or DELOPAR's parabolic ones, with the
+      // downwind source S_P; psi_M + psi_O + psi_P = 1 - e in both
+      A pM = al, pO = be, pP = (A)0;
+      A SP[4] = {0, 0, 0, 0};
+      if (par) {
+        pM = (A)par[pt * 3];
+        pO = (A)par[pt * 3 + 1];
+        pP = (A)par[pt * 3 + 2];
+        if (p + 1 < nz) {
+          const size_t pt2 = ((size_t)(up ? p + 1 : nz - 2 - p) * nO + o) * N + n;
+          const A ie2 = kt[pt2 * 10 + 6];
+          for (int s = 0; s < 4; ++s) SP[s] = eps[pt2 * 4 + s] * ie2;
+        }
+      }
       A rhs[4];
       for (int i = 0; i < 4; ++i) {
-        A v = thick ? e * (I[i] - S[i]) + al * (Sp[i] - S[i]) : e * I[i] + al * Sp[i] + be * S[i];
+        A v = thick ? e * (I[i] - S[i]) + pM * (Sp[i] - S[i]) + pP * (SP[i] - S[i])
+                    : e * I[i] + pM * Sp[i] + pO * S[i] + pP * SP[i];
         for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + (thick ? be * Kk[i][j] * S[j] : (A)0);
         rhs[i] = v;
       }
@@ -519,14 +539,38 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
   }
 }
 
-template <typename A, typename T>
-__global__ void normalise_kernel(const A* __restrict__ num, const T* __restrict__ kt, const double* __restrict__ fac,
-                                 double* __restrict__ f, int nz, int nO, int N) {
+// f = (1 - eps) W_T eta_I / [Sigma (W_T, 0, 0, 0)]_I with the line's eta_I (App. E)
+template <typename A>
+__global__ void normalise_kernel(const A* __restrict__ num, const double* __restrict__ eta_line,
+                                 const double* __restrict__ fac, double* __restrict__ f, int nz, int nO, int N) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= (long long)nz * nO * N) return;
   const int iz = (int)(pt / ((long long)nO * N));
-  const double eta1 = 1.0 / (double)kt[pt * 10 + 6];
-  f[pt] = fac[iz] * eta1 / (double)num[pt * 4];
+  f[pt] = fac[iz] * eta_line[pt] / (double)num[pt * 4];
+}
+
+// Coherent continuum scattering in the observer frame (App. A):
+//   eps[z][o][n][i] += sigma_c[z][n] sum_{o', j} PW[o][o'][i][j] x[z][o'][n][j]
+// PW = w_o' P(o, o') (dipole phase matrix); nOut output directions (the grid,
+// or one line of sight), the input x on the grid's nO directions.
+template <typename A>
+__global__ void continuum_kernel(const A* __restrict__ x, const double* __restrict__ pw,
+                                 const double* __restrict__ sig, A* __restrict__ eps, int nz, int nOut, int nO, int N) {
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (z, o, n), n fastest
+  if (pt >= (long long)nz * nOut * N) return;
+  const int n = (int)(pt % N);
+  const int o = (int)((pt / N) % nOut);
+  const int iz = (int)(pt / ((long long)N * nOut));
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int op = 0; op < nO; ++op) {
+    const A* xv = x + (((size_t)iz * nO + op) * N + n) * 4;
+    const double* P = pw + ((size_t)o * nO + op) * 16;
+    const double x0 = xv[0], x1 = xv[1], x2 = xv[2], x3 = xv[3];
+    for (int i = 0; i < 4; ++i) acc[i] += P[i * 4] * x0 + P[i * 4 + 1] * x1 + P[i * 4 + 2] * x2 + P[i * 4 + 3] * x3;
+  }
+  const double sc = sig[(size_t)iz * N + n];
+  A* e = eps + pt * 4;
+  for (int i = 0; i < 4; ++i) e[i] = (A)((double)e[i] + sc * acc[i]);
 }
 
 template <typename T>
@@ -603,6 +647,11 @@ s6:
                                                                      (const double*)c->tbk.p, sp,
                                                                      normalised ? (const double*)c->f.p : nullptr, eps, nz,
                                                                      nO, N);
+  // continuum scattering (App. A) joins the normalised emissivity; the
+  // Kirchhoff factor is computed from the line alone (normalised = false)
+  if (normalised && c->has_cont())
+    continuum_kernel<A><<<ceil_div(npt, 256), 256, 0, c->stream>>>(x, (const double*)c->cont_pw.p,
+                                                                 (const double*)c->cont_sig.p, eps, nz, nO, nO, N);
   stage_end(c, ST_S6, e0);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
@@ -655,11 +704,13 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
   cudaEvent_t e0;
   stage_begin(c, ST_S7, &e0);
   if (c->prec == PRD_FP64)
-    delo_kernel<double, double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p, dmu,
+    delo_kernel<double, double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p,
+                                                                       (const double*)c->par_active(), dmu,
                                                                        (const double*)sub_from, (double*)out, nz, nO,
                                                                        N, boundary ? 1 : 0, c->WT[0]);
   else
-    delo_kernel<float, float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p, dmu,
+    delo_kernel<float, float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p,
+                                                                      (const float*)c->par_active(), dmu,
                                                                       (const float*)sub_from, (float*)out, nz, nO, N,
                                                                       boundary ? 1 : 0, c->WT[0]);
   stage_end(c, ST_S7, e0);
@@ -691,8 +742,8 @@ int compute_normalisation(Ctx* c) {
     fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
     rc = sigma_T<double, double>(c, (const double*)xin.p, (double*)num.p, false);
     if (!rc)
-      normalise_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
-          (const double*)num.p, (const double*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
+      normalise_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const double*)c->eta_line.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
   } else {
     fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
     rc = c->has64 ? sigma_T<double, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p,
@@ -700,8 +751,8 @@ int compute_normalisation(Ctx* c) {
                   : sigma_T<float, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p,
                                            (double*)Ic.p);
     if (!rc)
-      normalise_kernel<double, float><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
-          (const double*)num.p, (const float*)c->kt.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
+      normalise_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const double*)c->eta_line.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cleanup();
@@ -728,7 +779,8 @@ int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws /* 4 x nve
                      : sigma_T<float, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv);
   if (rc) return rc;
   delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
-      eps, (const float*)c->kt.p, (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu, 0, c->WT[0]);
+      eps, (const float*)c->kt.p, (const float*)c->par_active(), (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu,
+      0, c->WT[0]);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
@@ -743,8 +795,8 @@ int rhs_acc(Ctx* c, double* b) {
   std::vector<double> hd(h.begin(), h.end());
   cudaMemcpy(e64.p, hd.data(), nv * 8, cudaMemcpyHostToDevice);
   delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
-      (const double*)e64.p, (const float*)c->kt.p, (const double*)c->dmu.p, nullptr, b, c->nz, c->nO, c->nnu, 1,
-      c->WT[0]);
+      (const double*)e64.p, (const float*)c->kt.p, (const float*)c->par_active(), (const double*)c->dmu.p, nullptr, b,
+      c->nz, c->nO, c->nnu, 1, c->WT[0]);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   dfree(e64);
   if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("rhs_acc: ") + cudaGetErrorString(e));
@@ -768,13 +820,13 @@ __global__ void planck_comoving_kernel(T* __restrict__ Ic, const double* __restr
 
 // eps(z, n) = (eps_sc with f) + eps_th;  f = (1-eps) W_T eta_I / num_I
 template <typename T, typename A>
-__global__ void los_combine_kernel(const A* __restrict__ es, const A* __restrict__ ew, const T* __restrict__ kt,
+__global__ void los_combine_kernel(const A* __restrict__ es, const A* __restrict__ ew, const double* __restrict__ eta_line,
                                    const T* __restrict__ eth, const double* __restrict__ fac, A* __restrict__ out,
                                    int nz, int N) {
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= nz * N) return;
   const int iz = pt / N;
-  const double f = fac[iz] / ((double)kt[pt * 10 + 6] * (double)ew[pt * 4]);
+  const double f = fac[iz] * eta_line[pt] / (double)ew[pt * 4];
   out[pt * 4] = (A)((double)es[pt * 4] * f + (double)eth[pt * 4]);
   for (int s = 1; s < 4; ++s) out[pt * 4 + s] = es[pt * 4 + s] + (A)eth[pt * 4 + s];
 }
@@ -796,10 +848,10 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
   const long long npt = (long long)nz * nO * N;
   const size_t tz = (size_t)nO * nti * N * c->ld() * sizeof(T);   // tiles of one height, all LOS classes
   DBuf Icx, Icw, Jx, Jw, tiles, Yd, rout, ktd, ethd, kidx, ttd, es_bar, ew_bar, es, ew, M, eps, lam, fac, dmu, clsd,
-      xa, Mx;
+      xa, Mx, pard, etald, cpwd;
   auto cleanup = [&]() {
     DBuf* bs[] = {&Icx, &Icw, &Jx, &Jw, &tiles, &Yd, &rout, &ktd, &ethd, &kidx, &ttd, &es_bar, &ew_bar, &es, &ew,
-                  &M, &eps, &lam, &fac, &dmu, &clsd, &xa, &Mx};
+                  &M, &eps, &lam, &fac, &dmu, &clsd, &xa, &Mx, &pard, &etald, &cpwd};
     for (DBuf* b : bs) dfree(*b);
   };
   const size_t vb = nvec(c) * sizeof(A), lb = (size_t)nz * N * 4 * sizeof(A);
@@ -845,6 +897,8 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       return upload(c, b, h.data(), h.size() * sizeof(T));
     };
     if ((rc = up(Yd, L.Y)) || (rc = up(rout, L.rout)) || (rc = up(ktd, L.kt)) || (rc = up(ethd, L.epsth)) ||
+        (rc = up(pard, L.par)) || (rc = upload(c, etald, L.eta_line.data(), L.eta_line.size() * 8)) ||
+        (rc = upload(c, cpwd, L.cont_pw.data(), L.cont_pw.size() * 8)) ||
         (rc = upload(c, kidx, L.kidx.data(), L.kidx.size() * 4)) || (rc = upload(c, ttd, L.tt.data(), L.tt.size() * 8)) ||
         (rc = upload(c, dmu, &mus[l], 8)))
       break;
@@ -878,10 +932,16 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
         (const A*)ew_bar.p, (const A*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
         (A*)ew.p, nz, 1, N);
     los_combine_kernel<T, A><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const A*)es.p, (const A*)ew.p,
-                                                                          (const T*)ktd.p, (const T*)ethd.p,
+                                                                          (const double*)etald.p, (const T*)ethd.p,
                                                                           (const double*)fac.p, (A*)eps.p, nz, N);
-    delo_kernel<T, A><<<ceil_div(N, 128), 128, 0, c->stream>>>((const A*)eps.p, (const T*)ktd.p, (const double*)dmu.p,
-                                                             nullptr, (A*)lam.p, nz, 1, N, 1, c->WT[0]);
+    if (c->has_cont())
+      continuum_kernel<A><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const A*)xa.p, (const double*)cpwd.p,
+                                                                       (const double*)c->cont_sig.p, (A*)eps.p, nz,
+                                                                       1, nO, N);
+    delo_kernel<T, A><<<ceil_div(N, 128), 128, 0, c->stream>>>((const A*)eps.p, (const T*)ktd.p,
+                                                             c->formal ? (const T*)pard.p : nullptr,
+                                                             (const double*)dmu.p, nullptr, (A*)lam.p, nz, 1, N, 1,
+                                                             c->WT[0]);
     cast_kernel<A, T><<<ceil_div(N * 4, 128), 128, 0, c->stream>>>((const A*)lam.p + (size_t)(nz - 1) * N * 4,
                                                                   out + (size_t)l * N * 4, (long long)N * 4);
     PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));

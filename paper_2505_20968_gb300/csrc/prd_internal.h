@@ -51,6 +51,10 @@ struct Ctx {
   prd_atom atom{};
   int nz = 0;
   std::vector<double> z, T, xi, a, eps, rE, k, WT, B, thB, chB, v;
+  // continuum (App. A), [z][nu] each, empty if none: absorption, scattering, thermal emissivity
+  std::vector<double> kapc, sigc, epsc;
+  bool has_cont() const { return !sigc.empty(); }
+  int cont_nz = 0, cont_nnu = 0;      // sizes the continuum arrays were given for
   int nnu = 0;
   std::vector<double> grid;
   int grid_kind = 0, n_mu_half = 0, n_chi = 0, mu_rule = 0, mode = 0;
@@ -114,6 +118,12 @@ struct Ctx {
   DBuf r3J;          // [z][uv] complex scratch
   DBuf r3ab;         // [z][uv] complex (beta-alpha) * k * c3
   DBuf kt;           // [z][o][n][10] K'/eta1 (6), 1/eta1, exp(-d), alpha, beta
+  DBuf par;          // [z][o][n][3] DELOPAR source weights psi_M, psi_O, psi_P of the step arriving there
+  DBuf eta_line;     // [z][o][n] the line's eta_I (double): the Kirchhoff factor normalises the line only
+  DBuf cont_pw;      // [o][o'][4][4] w_o' P(o, o') dipole phase matrix of continuum scattering (double)
+  DBuf cont_sig;     // [z][n] sigma_c (double)
+  int formal = 0;    // formal solver: 0 DELO-linear, 1 DELOPAR (PRD_OPT_FORMAL_SOLVER)
+  const void* par_active() const { return formal ? par.p : nullptr; }
   DBuf epsth;        // [z][o][n][4]
   DBuf f;            // [z][o][n]
   DBuf sp;           // spline tables: per z  h[N-1], cp[N], den[N]  (T) -> [z][3][N]
@@ -192,12 +202,21 @@ struct LosTables {
   std::vector<double> theta;   // [z? no: nO]  scattering angle LOS-o'
   std::vector<double> rout;    // [z][nuv][nl][4][2]
   std::vector<double> kt;      // [z][N][10]
+  std::vector<double> par;     // [z][N][3]  DELOPAR source weights
+  std::vector<double> eta_line;   // [z][N]  the line's eta_I
+  std::vector<double> cont_pw;    // [nO][4][4]  w_o' P(LOS, o') (continuum scattering)
   std::vector<double> epsth;   // [z][N][4]
   std::vector<int> kidx;       // [z][N]   back-interpolation intervals
   std::vector<double> tt;      // [z][N]
 };
 void los_tables(const Ctx* c, double mu, double chi, LosTables& L);
 int gen_tiles_z(Ctx* c, int iz, const std::vector<double>& thetas, void* outT);
+// DELOPAR source weights of a step of optical thickness dM followed downwind by dP
+void delopar_weights(double dM, double dP, double* psi);
+// dipole (Rayleigh) phase matrix P[4][4] from direction (mu_p, chi_p) into (mu_o, chi_o)
+void dipole_phase(double mu_o, double chi_o, double mu_p, double chi_p, double* P);
+// eps[z][o][n] += sigma_c sum_o' w_o' P(o, o') x[z][o'][n] (continuum scattering, App. A)
+int add_continuum_scattering(Ctx* c, const void* x, void* eps, bool fp64_vectors);
 
 // ---- device launchers (kernels_*.cu)
 int launch_tiles(Ctx* c);

@@ -15,9 +15,9 @@
 // Roles (320 threads): warp 0 streams the tile into a 5-stage ring with one
 // bulk asynchronous copy per K step (the FP32 tiles are stored pre-swizzled, K
 // step by K step, so a step is one contiguous N x 64-byte block), stages the
-// step's I~ of every incident direction of the CTA beside it (its 32 lanes
-// load and store; the ring depth hides the load latency) and owns the TMEM
-// allocation; warp 1 issues tcgen05.mma; warps 2-9 build B in shared memory
+// step's I~ of every incident direction of the CTA beside it (one or two bulk
+// copies per direction, issued by its 32 lanes, completing on the same stage
+// barrier) and owns the TMEM allocation; warp 1 issues tcgen05.mma; warps 2-9 build B in shared memory
 // from Y (staged per tile, prefetched into registers a tile ahead) and the
 // staged I~, split both operands into TF32 hi/lo parts
 // (3 products: hi*hi + hi*lo + lo*hi, FP32-level accuracy) in a 2-buffer ring
@@ -35,29 +35,39 @@ namespace prd {
 
 namespace tc {
 
-constexpr int kStages = 5;                    // tile + I~ ring
+constexpr int kStagesMax = 5;                 // tile ring depth: 2..5, the most that fit beside the rest
 constexpr int kCBufs = 2;                     // builder ring: A_lo, B_hi, B_lo
 constexpr int kKC = 16;                       // fp32 per stage along K (64-byte rows)
 constexpr int kMaxE = 32;                     // output directions per CTA
 constexpr int kNCPMax = 4 * kMaxE;            // MMA N (Stokes columns)
-constexpr int kABytes = 256 * kKC * 4;        // one K step of up to 256 tile rows
 constexpr int kBBytes = kNCPMax * kKC * 4;
-constexpr int kCBytes = kABytes + 2 * kBBytes;
-constexpr int kGen = 256;                     // builder threads (warps 2-9)
+// Builder warps: the B build and the TF32 splits are chains of dependent
+// shared-memory loads and FMAs, so the builders are latency-bound; more warps
+// hide more of that latency (16 warps, one B item each, fit 576 threads x 112
+// registers).
+constexpr int kGenWarps = 16;
+constexpr int kGen = 32 * kGenWarps;          // builder threads (warps 2 .. 2 + kGenWarps - 1)
 constexpr int kThreads = 64 + kGen;
-constexpr int kYPairs = 64;                   // pairs whose Y is staged in shared memory
+constexpr int kItems = 16 / kGenWarps;        // B items per builder warp (16 items of 32 rows x 4 k)
+constexpr int kYPairsC = 64;
+constexpr int kYR = (kYPairsC * 8 + kGen - 1) / kGen;   // Y prefetch float4 per builder thread
+constexpr int kAR = (1024 + kGen - 1) / kGen;           // A_lo float4 per builder thread (N <= 256)
+constexpr int kYPairs = kYPairsC;             // pairs whose Y is staged in shared memory
 constexpr int kYBytes = kYPairs * 32 * 4;     // one tile's Y (two buffers)
-constexpr int kISlots = 32;                   // incident directions staged per K step
-// I~ of one K step: slot sl, column kl at float4 sl * kIStride + kl; the odd stride
-// puts the slots of a warp's 8 outputs in 8 distinct bank groups
-constexpr int kIStride = kKC + 1;
-constexpr int kIBytes = kISlots * kIStride * 16;
-constexpr int kAuxBytes = (kMaxE + 3 + kYPairs + kISlots) * 4 + 256;
-constexpr int kSmemBytes = kStages * (kABytes + kIBytes) + kCBufs * kCBytes + 2 * kYBytes + kAuxBytes + 1024;
-static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
-static_assert(kYPairs * 8 <= 2 * kGen, "Y prefetch registers");
-static_assert(kNCPMax == 128 && kGen == 256, "B items: 8 builder warps x 2 (32-row group, 4-k chunk)");
-constexpr long long kSpin = 1ll << 24;        // bounded waits
+constexpr int kISlots = 32;                   // incident directions whose I~ is resident per CTA
+constexpr int kAuxBytes = 1024;               // work-item tables, barriers, TMEM slot, abort flag
+constexpr int kSmemMax = 227 * 1024;          // shared memory per CTA
+static_assert(kNCPMax == 128 && (kGenWarps == 8 || kGenWarps == 16), "B items: 16 (32-row group, 4-k chunk) over the builder warps");
+// Shared memory of one CTA for N tile rows with `st` tile stages: the tile ring
+// (NM x 64 bytes per K step), the builder ring (A_lo of NM rows, B_hi, B_lo),
+// two Y buffers, the resident I~ of kISlots incident directions (stride N + 1
+// float4, odd modulo 8 so that different slots fall in different bank groups)
+// and the auxiliary tables, plus 1 KB to align the base.
+__host__ __device__ constexpr int smem_bytes(int N, int st) {
+  return st * ((N + 15) / 16 * 16) * 64 + kCBufs * (((N + 15) / 16 * 16) * 64 + 2 * kBBytes) + 2 * kYBytes +
+         kISlots * (N + 1) * 16 + kAuxBytes + 1024;
+}
+constexpr long long kSpin = 1ll << 24;        // bounded waits (default limit of the pipeline waits; drains)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -81,9 +91,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; returns false (and raises the CTA abort flag) on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-  for (long long i = 0; i < kSpin; ++i) {
+// bounded pipeline wait of at most `limit` polls; returns false (and raises the
+// CTA abort flag) on expiry or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
   }
@@ -157,6 +168,8 @@ struct Params {
   float* eb;            // [z][o][N][4]
   int* err;
   int ncls, ntile, nO, N, npairs, ld;
+  int nst;              // tile stages (2..kStagesMax)
+  long long spin;       // poll limit of the pipeline waits (the drains keep kSpin)
 };
 
 // barrier over the builder warps only (named barrier 1)
@@ -178,16 +191,22 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   // 1024-byte aligned base, derived by offset so that the compiler keeps the
   // shared address space on every pointer below (plain LDS/STS, no generic access)
   unsigned char* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
-  unsigned char* cbuf = sm + kStages * kABytes;                    // [buffer] A_lo, B_hi, B_lo
-  float* Ys = (float*)(cbuf + kCBufs * kCBytes);                   // [buffer][pair][16][2]
-  float4* Is = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [stage][slot][kIStride]
-  int* eptr = (int*)((unsigned char*)Is + kStages * kIBytes);      // local pair range of each output
+  const int N = p.N;
+  const int NM = (N + 15) / 16 * 16;             // MMA N: the tile rows n (<= 256)
+  const int SA = NM * kKC * 4;                   // one K step of the tile (multiple of 1024 bytes)
+  const int nst = p.nst;
+  const int IS = N + 1;                          // float4 stride of a resident I~ slot
+  unsigned char* cbuf = sm + nst * SA;                             // [buffer] A_lo, B_hi, B_lo
+  const int CB = SA + 2 * kBBytes;
+  float* Ys = (float*)(cbuf + kCBufs * CB);                        // [buffer][pair][16][2]
+  float4* Ir = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [slot][k < N], resident
+  int* eptr = (int*)((unsigned char*)Ir + (size_t)kISlots * IS * 16);   // local pair range of each output
   int* fast_p = eptr + kMaxE + 1;                                  // fast-path flag, staged slots
   int* pslot = fast_p + 2;                                         // slot of each local pair
   int* slot_dir = pslot + kYPairs;                                 // direction held in each slot
   uint64_t* full = (uint64_t*)(((uintptr_t)(slot_dir + kISlots) + 7) & ~(uintptr_t)7);
-  uint64_t* empty = full + kStages;
-  uint64_t* ready = empty + kStages;
+  uint64_t* empty = full + kStagesMax;
+  uint64_t* ready = empty + kStagesMax;
   uint64_t* cfree = ready + kCBufs;
   uint64_t* done = cfree + kCBufs;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -202,7 +221,6 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int* pair_in = pair_ptr + ne_tot + 1;
   const int E = min(kMaxE, cout_ptr[c + 1] - e0);
   const int NCP = ((4 * E + 15) / 16) * 16;      // MMA N (multiple of 16, <= 128)
-  const int N = p.N;
   const int KCH = (2 * N + kKC - 1) / kKC;
   const int iters = p.ntile * KCH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -212,8 +230,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const bool y_in_smem = npl <= kYPairs;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1 + 32);   // tile copy armed by lane 0, I~ staged by the 32 producer lanes
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&full[s], 1);        // armed by the producer with the bytes of the tile copy
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < kCBufs; ++b) {
@@ -255,53 +273,32 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const bool fast = fast_p[0] != 0;
   const int ns = fast_p[1];
   const long long slab0 = ((long long)iz * p.ncls + c) * p.ntile;
-  const int NM = (N + 15) / 16 * 16;             // MMA N: the tile rows n (<= 256)
   const float* Icz = p.Ic + (size_t)iz * p.nO * N * 4;
 
   if (warp == 0) {
-    // ---------------- producer warp: lane 0 waits for a free stage and copies the tile
-    // K step (one bulk copy); all 32 lanes stage the step's I~ of every slot (loads
-    // issued together, latency hidden by the ring) and arrive on the stage barrier
-    int it = 0;
-    const uint64_t pol_t = policy_evict_first();
-    const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
-    for (; it < iters; ++it) {
-      const int s = it % kStages;
-      int ok = 1;
-      if (lane == 0 && it >= kStages) ok = mbar_wait(&empty[s], ((it / kStages) - 1) & 1, abort_flag) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      const int ti = it / KCH, kc = it - ti * KCH;
-      if (lane == 0) {
-        const uint32_t abytes = (uint32_t)N * kKC * 4;
+    // ---------------- producer: lane 0 waits for a free stage, arms its barrier with the
+    // bytes of the step and copies the tile K step (one bulk copy), up to nst steps
+    // ahead of the MMAs.  I~ is resident (staged once by the builders).
+    if (lane == 0) {
+      int it = 0;
+      const uint64_t pol_t = policy_evict_first();
+      const uint32_t abytes = (uint32_t)N * kKC * 4;
+      for (; it < iters; ++it) {
+        const int s = it % nst;
+        if (it >= nst && !mbar_wait(&empty[s], ((it / nst) - 1) & 1, abort_flag, p.spin)) break;
+        const int ti = it / KCH, kc = it - ti * KCH;
         // rows n >= N of the stage keep stale data: they only reach output rows
         // that the epilogue never reads
         const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
         mbar_expect_tx(&full[s], abytes);
-        bulk_load(sm + s * kABytes, src, abytes, &full[s], pol_t);
+        bulk_load(sm + s * SA, src, abytes, &full[s], pol_t);
       }
-      float4* Isb = Is + (size_t)s * (kISlots * kIStride);
-      float4 v[kISlots * kKC / 32];
-#pragma unroll
-      for (int r = 0; r < kISlots * kKC / 32; ++r) {
-        const int q = lane + 32 * r;
-        const int sl = q / kKC, k = kc * kKC + (q - sl * kKC);
-        v[r] = (q < ns * kKC && k < 2 * N) ? Icz4[(size_t)slot_dir[sl] * N + (k < N ? k : k - N)]
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int r = 0; r < kISlots * kKC / 32; ++r) {
-        const int q = lane + 32 * r;
-        const int sl = q / kKC;
-        if (q < ns * kKC) Isb[sl * kIStride + (q - sl * kKC)] = v[r];
-      }
-      mbar_arrive(&full[s]);
-    }
-    if (lane == 0 && *abort_flag) {
-      // drain copies that were issued and may not have been consumed
-      for (int j = max(0, it - kStages); j < it; ++j) {
-        const int s = j % kStages;
-        for (long long i = 0; i < kSpin && !mbar_try(&full[s], (j / kStages) & 1); ++i) {
+      if (*abort_flag) {
+        // drain copies that were issued and may not have been consumed
+        for (int j = max(0, it - nst); j < it; ++j) {
+          const int s = j % nst;
+          for (long long i = 0; i < kSpin && !mbar_try(&full[s], (j / nst) & 1); ++i) {
+          }
         }
       }
     }
@@ -313,12 +310,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NM >> 3) << 17) | ((128u >> 4) << 24);
       int issued = 0;
       for (int it = 0; it < iters; ++it) {
-        const int s = it % kStages, cb = it % kCBufs;
-        if (!mbar_wait(&ready[cb], (it / kCBufs) & 1, abort_flag)) break;
+        const int s = it % nst, cb = it % kCBufs;
+        if (!mbar_wait(&ready[cb], (it / kCBufs) & 1, abort_flag, p.spin)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* A = sm + s * kABytes;
-        unsigned char* Alo = cbuf + cb * kCBytes;
-        unsigned char* Bhi = Alo + kABytes;
+        unsigned char* A = sm + s * SA;
+        unsigned char* Alo = cbuf + cb * CB;
+        unsigned char* Bhi = Alo + SA;
         unsigned char* Blo = Bhi + kBBytes;
         for (int ks = 0; ks < 2; ++ks) {
           const int o = ks * 32;                   // 8 fp32 of K per MMA
@@ -349,10 +346,10 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     // lane takes row rg*32 + lane (output el = row / 4, Stokes i = row % 4), and
     // the swizzle spreads each 8 lanes' stores over all banks
     const int nrg = (NCP + 31) / 32;
-    int it_row[2], it_kq[2], it_pa[2], it_pb[2];
+    int it_row[kItems], it_kq[kItems], it_pa[kItems], it_pb[kItems];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int item = bw + 8 * r;
+    for (int r = 0; r < kItems; ++r) {
+      const int item = bw + kGenWarps * r;
       const bool vi = item < nrg * 4;
       const int rg = vi ? item % nrg : 0;
       it_row[r] = vi ? rg * 32 + lane : NCP;      // NCP: no item
@@ -363,39 +360,50 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       it_pb[r] = v ? eptr[el + 1] : 0;
     }
     const size_t ybase = (size_t)iz * p.npairs + pp0;
-    float4 ypre[2];
+    float4 ypre[kYR];
     auto load_y = [&](int ti) {
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < kYR; ++r) {
         const int q = gt + r * kGen;
         if (y_in_smem && q < npl * 8)
           ypre[r] = *((const float4*)(p.Y + ((ybase + (q >> 3)) * p.ntile + ti) * 32) + (q & 7));
       }
     };
     // fast path: each lane keeps its items' Y rows and I~ slot offsets for the tile
-    // in registers; the I~ of every K step is staged in shared memory by the producer
-    float4 yreg[2][2][2];
-    int soff[2][2];
+    // in registers.  I~ does not depend on the tile: column k of the Re half and
+    // column N + k of the Im half both read I~(k).  So the I~ of the CTA's staged
+    // incident directions is loaded into shared memory once, here, while the
+    // producer already streams the first tile steps.
+    float4 yreg[kItems][2][2];
+    int soff[kItems][2];
     load_y(0);
+    {
+      const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
+      for (int idx = gt; idx < ns * N; idx += kGen) {
+        const int sl = idx / N, k = idx - sl * N;
+        Ir[sl * IS + k] = Icz4[(size_t)slot_dir[sl] * N + k];
+      }
+      gen_sync();
+    }
     bool aborted = false;
     for (int it = 0; it < iters; ++it) {
-      const int s = it % kStages, cb = it % kCBufs;
+      const int s = it % nst, cb = it % kCBufs;
       const int ti = it / KCH, kc = it - ti * KCH;
-      bool got = !aborted && mbar_wait(&full[s], (it / kStages) & 1, abort_flag);
-      if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag);
+      bool got = !aborted && mbar_wait(&full[s], (it / nst) & 1, abort_flag, p.spin);
+      if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag, p.spin);
       float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
       if (kc == 0) {
         // a new tile: stage its Y, then all builders agree to go on (every builder
         // reaches this barrier, aborted or not, so none waits for one that left)
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < kYR; ++r) {
           const int q = gt + r * kGen;
           if (y_in_smem && q < npl * 8) ((float4*)Ysb)[q] = ypre[r];
         }
         got = gen_all(got);
         if (got && fast) {
 #pragma unroll
-          for (int r = 0; r < 2; ++r) {
+          for (int r = 0; r < kItems; ++r) {
             const int npr = it_pb[r] - it_pa[r], i = it_row[r] & 3;
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) {
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
                 const float4* y4 = reinterpret_cast<const float4*>(Ysb) + (it_pa[r] + pp) * 8 + i * 2;
                 yreg[r][pp][0] = y4[0];
                 yreg[r][pp][1] = y4[1];
-                soff[r][pp] = pslot[it_pa[r] + pp] * kIStride + it_kq[r] * 4;
+                soff[r][pp] = pslot[it_pa[r] + pp] * IS;
               }
             }
           }
@@ -414,21 +422,20 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         aborted = true;
         continue;
       }
-      unsigned char* A = sm + s * kABytes;
-      unsigned char* Alo = cbuf + cb * kCBytes;
-      unsigned char* Bhi = Alo + kABytes;
+      unsigned char* A = sm + s * SA;
+      unsigned char* Alo = cbuf + cb * CB;
+      unsigned char* Bhi = Alo + SA;
       unsigned char* Blo = Bhi + kBBytes;
-      const float4* Isb = Is + (size_t)s * (kISlots * kIStride);
       {
         const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
-        const int nq4 = N * (kKC / 4);             // <= 4 kGen
-        float4 v[4];
+        const int nq4 = N * (kKC / 4);             // <= kAR kGen
+        float4 v[kAR];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < kAR; ++r)
           if (gt + r * kGen < nq4) v[r] = a4[gt + r * kGen];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < kAR; ++r)
           if (gt + r * kGen < nq4) {
             float4 l;
             l.x = tf32_hi(v[r].x - tf32_trunc(v[r].x));
@@ -439,26 +446,53 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           }
       }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < kItems; ++r) {
         const int row = it_row[r], kq = it_kq[r], i = row & 3;
         if (row >= NCP) continue;
         const int kb = kc * kKC + kq * 4;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (fast) {
           const int npr = it_pb[r] - it_pa[r];
-          bool re[4];
+          // a 4-column chunk lies in the Re half (k < N), the Im half, or across
+          // k = N; the first two are uniform over the warp (same chunk kq)
+          if (kb + 3 < N) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) re[q] = kb + q < N;   // I~ past 2N was loaded as zero
+            for (int pp = 0; pp < 2; ++pp) {
+              if (pp < npr) {
+                const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
 #pragma unroll
-          for (int pp = 0; pp < 2; ++pp) {
-            if (pp < npr) {
-              const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
+                for (int q = 0; q < 4; ++q) {
+                  const float4 iv = Ir[soff[r][pp] + kb + q];
+                  z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
+                }
+              }
+            }
+          } else if (kb >= N) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float4 iv = Isb[soff[r][pp] + q];
-                const float sr = ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
-                const float si = ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
-                z[q] += re[q] ? sr : -si;
+            for (int pp = 0; pp < 2; ++pp) {
+              if (pp < npr) {
+                const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  // past 2N (last chunk of a ragged tile) the read is clamped into the
+                  // slot and the column zeroed below
+                  const float4 iv = Ir[soff[r][pp] + min(kb + q - N, N - 1)];
+                  z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+              if (pp < npr) {
+                const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const int k = kb + q;
+                  const float4 iv = Ir[soff[r][pp] + (k < N ? k : min(k - N, N - 1))];
+                  if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
+                  else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
+                }
               }
             }
           }
@@ -472,12 +506,16 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
             for (int q = 0; q < 4; ++q) {
               const int k = kb + q;
               if (k >= 2 * N) continue;
-              const float4 iv = sl >= 0 ? Isb[sl * kIStride + kq * 4 + q] : ir[k < N ? k : k - N];
+              const int km = k < N ? k : k - N;
+              const float4 iv = sl >= 0 ? Ir[sl * IS + km] : ir[km];
               if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
               else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
             }
           }
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (kb + q >= 2 * N) z[q] = 0.f;                  // columns past 2N (zero tile columns)
         float4 hi, lo;
         hi.x = tf32_hi(z[0]); lo.x = tf32_hi(z[0] - hi.x);
         hi.y = tf32_hi(z[1]); lo.y = tf32_hi(z[1] - hi.y);
@@ -490,16 +528,16 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       mbar_arrive(&ready[cb]);
     }
     // ---------------- epilogue: TMEM -> registers -> eps_bar
-    const bool ok = mbar_wait(done, 0, abort_flag);
+    const bool ok = mbar_wait(done, 0, abort_flag, p.spin);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       const int q = warp & 3;                    // TMEM lane quarter of this warp
-      const int par = (warp - 2) >> 2;           // two warps per quarter split the 16-column groups
+      const int par = (warp - 2) >> 2;           // kGenWarps / 4 warps per quarter split the 16-column groups
       const int r = q * 32 + lane;               // D row: Stokes column (output el = r / 4, i = r % 4)
       const bool live = r < 4 * E;
       const int o = live ? cout_dir[e0 + (r >> 2)] : 0;
       float* dst = p.eb + (((size_t)iz * p.nO + o) * N) * 4 + (r & 3);
-      for (int c0 = par * 16; c0 < NM; c0 += 32) {
+      for (int c0 = par * 16; c0 < NM; c0 += 16 * (kGenWarps / 4)) {
         uint32_t v[16];
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
         asm volatile(
@@ -529,10 +567,19 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 
 }  // namespace tc
 
+// Tile stages for N rows: the most (<= kStagesMax) whose shared memory fits.
+static int r2_tc_stages(int N) {
+  for (int st = tc::kStagesMax; st >= 2; --st)
+    if (tc::smem_bytes(N, st) <= tc::kSmemMax) return st;
+  return 0;
+}
+
 // Work list and error flag of the tensor-core contraction.
 int r2_tc_prepare(Ctx* c) {
   if (c->prec != PRD_FP32) return PRD_OK;
-  if (c->nnu > 256 || !c->tiled()) return fail(c, PRD_E_ARG, "tensor-core contraction needs N <= 256 and FP32 tiles");
+  if (!c->tiled() || r2_tc_stages(c->nnu) < 2)
+    return fail(c, PRD_E_ARG, "tensor-core contraction needs FP32 tiles and N small enough for two tile stages "
+                              "beside the resident I~ (N <= 232)");
   if (!c->tc_err.p) {
     int rc = dalloc(c, c->tc_err, sizeof(int));
     if (rc) return rc;
@@ -557,11 +604,13 @@ int r2_tc_prepare(Ctx* c) {
 }
 
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
+  const int nst = r2_tc_stages(c->nnu);
   tc::Params p{(const float*)c->tiles.p, (const float*)c->Y.p, Ic, (const int2*)c->tc_work.p,
                (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p, c->ncls, c->ntile(), c->nO, c->nnu, c->npairs,
-               c->ld()};
-  PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
-  tc::r2_tc_kernel<<<dim3(c->tc_nwork, c->nz), tc::kThreads, tc::kSmemBytes, c->stream>>>(p);
+               c->ld(), nst, c->tc_spin > 0 ? c->tc_spin : tc::kSpin};
+  const int smem = tc::smem_bytes(c->nnu, nst);
+  PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  tc::r2_tc_kernel<<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

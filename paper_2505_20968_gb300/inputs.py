@@ -191,6 +191,24 @@ def hi_lya(n_z=90, n_core=90, n_wing=60, n_mu_half=6, n_chi=8, Bmax=50.0, vmax=5
                 gmres_tol=1e-6, seed=seed)
 
 
+def with_continuum(cfg, opacity=1e-4, albedo=0.3, seed=7):
+    """The workload with continuum arrays added (App. A): per height a
+    continuum extinction opacity * k_line (10 % smooth seeded modulation),
+    flat over the line's narrow frequency range, of which the share `albedo`
+    is scattering (sigma_c) and the rest absorption (kappa_c), and the LTE
+    thermal continuum emissivity kappa_c W_T.  Arrays [z][nu], km^-1."""
+    rng = np.random.default_rng(seed)
+    atm = dict(cfg["atm"])
+    z = np.asarray(atm["z_km"], float)
+    nnu = len(cfg["quad"]["grid"])
+    ext = opacity * np.asarray(atm["k_line"], float) * _smooth(rng, z, 0.1)
+    kap = (1.0 - albedo) * ext
+    atm["kappa_c"] = np.repeat(kap[:, None], nnu, axis=1)
+    atm["sigma_c"] = np.repeat((albedo * ext)[:, None], nnu, axis=1)
+    atm["eps_c_th"] = np.repeat((kap * np.asarray(atm["W_T"], float))[:, None], nnu, axis=1)
+    return dict(cfg, atm=atm)
+
+
 def mgii_batch(n_inst=256, base_seed=400, n_mu_half=4, n_chi=8, nz_range=(50, 130),
                nnu_range=(120, 220)):
     """Ragged batch of Mg II-like instances (config-2 physics)."""

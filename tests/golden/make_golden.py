@@ -4,7 +4,8 @@ Calls only oracle/ and the seeded input generator; never the CUDA library.
 Run from the repository root:  python tests/golden/make_golden.py [names...]
 Outputs tests/golden/<name>.npz (forward operator and solution),
 twolevel_full_sol.npz (the solution of the full two-level slab), <name>_nb.npz
-(narrow-band signals along lines of sight),
+(narrow-band signals along lines of sight), <name>_par.npz (the DELOPAR
+formal solver),
 <name>_adj.npz (transposed operator and adjoint solve), <name>_pc.npz (the
 preconditioner with 1 and 2 sweeps) and grad_mgii_small.npz
 (derivatives of an emergent-intensity functional by central differences of
@@ -33,6 +34,11 @@ CASES = {
     "hi": lambda: inputs.hi_lya(n_z=10, n_core=13, n_wing=8, n_mu_half=2, n_chi=4, seed=31),
     "hi_aa": lambda: inputs.hi_lya(n_z=8, n_core=11, n_wing=6, n_mu_half=2, n_chi=4, seed=32,
                                    mode=inputs.MODE_AA),
+    # with continuum absorption, emission and coherent scattering (App. A)
+    "twolevel_cont": lambda: inputs.with_continuum(
+        inputs.twolevel_slab(n_z=8, n_x=11, n_mu_half=2, n_chi=4, eps=1e-2), 1e-3, 0.4),
+    "mgii_cont": lambda: inputs.with_continuum(
+        inputs.mgii(n_z=10, n_core_each=9, n_wing=8, n_mu_half=2, n_chi=4, seed=21), 1e-5, 0.3),
 }
 # full-size workloads: sampled outputs the oracle can compute one by one
 SAMPLES = {
@@ -155,6 +161,19 @@ def make_narrowband(name):
                         xbar=narrowband(lam, em, lam0, fwhm, half))
 
 
+# the DELOPAR formal solver (Sect. 3) on reduced cases: Lambda of the stored
+# emissivity, the right-hand side and the solution to 1e-13
+PAR = ("twolevel", "hi")
+
+
+def make_delopar(name):
+    P = Problem(CASES[name](), formal_solver="delopar")
+    G = np.load(os.path.join(HERE, name + ".npz"))
+    sol, hist = P.solve(tol=1e-13)
+    np.savez_compressed(os.path.join(HERE, name + "_par.npz"), lam=P.formal_solution(G["sigma"]), rhs=P.rhs(),
+                        sol=sol, res=hist[-1])
+
+
 # the full two-level slab (40 heights x 8 directions x 21 frequencies, FP64):
 # the solution to tol 1e-12 and its emergent Stokes vectors
 def make_full_solve():
@@ -183,7 +202,8 @@ def make_sample(name):
 
 if __name__ == "__main__":
     names = sys.argv[1:] or (list(CASES) + list(SAMPLES) + [a + "_adj" for a in ADJOINT] + ["grad"]
-                             + [a + "_pc" for a in PRECOND] + ["twolevel_full_sol"] + [a + "_nb" for a in NB])
+                             + [a + "_pc" for a in PRECOND] + ["twolevel_full_sol"] + [a + "_nb" for a in NB]
+                             + [a + "_par" for a in PAR])
     for nm in names:
         t0 = time.time()
         if nm in CASES:
@@ -200,6 +220,8 @@ if __name__ == "__main__":
             make_full_solve()
         elif nm.endswith("_nb"):
             make_narrowband(nm[:-3])
+        elif nm.endswith("_par"):
+            make_delopar(nm[:-4])
         else:
             raise SystemExit(f"unknown golden set {nm}")
         print(f"{nm}: {time.time() - t0:.1f} s", flush=True)

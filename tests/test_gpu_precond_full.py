@@ -160,3 +160,103 @@ def test_narrowband_signals_match_oracle(name):
     print(f"narrow-band {name}: I {dI:.2e}, Q/I U/I {dP:.2e}")
     assert dI < tol and dP < tol
     P.close()
+
+
+PAR_CASES = {
+    "twolevel": lambda: inputs.twolevel_slab(n_z=8, n_x=11, n_mu_half=2, n_chi=4, eps=1e-2),
+    "hi": lambda: inputs.hi_lya(n_z=10, n_core=13, n_wing=8, n_mu_half=2, n_chi=4, seed=31),
+}
+OPT_FORMAL_SOLVER, DELOPAR = 6, 1
+
+
+@pytest.mark.parametrize("name", list(PAR_CASES))
+def test_delopar_formal_solver_matches_oracle(name):
+    """The DELOPAR formal solver (Sect. 3; the paper's solver for H I Ly-alpha)
+    selected with PRD_OPT_FORMAL_SOLVER: Lambda of the oracle's emissivity,
+    the right-hand side (FP64 1e-9, FP32 2e-5 of the maximum, the DELO-linear
+    bounds), and the solution of the whole problem: FP64 within 1e-8; FP32
+    (refined solve) emergent I within 1e-5 relative and Q/I, U/I, V/I within
+    1e-4 absolute of the oracle's DELOPAR solution.  The transposed operator
+    is refused under DELOPAR."""
+    from paper_2505_20968_gb300.binding import PRD, PrdError, lib
+    G = np.load(os.path.join(GOLD, name + ".npz"))
+    R = np.load(os.path.join(GOLD, name + "_par.npz"))
+    P = PRD(PAR_CASES[name](), device=0)
+    assert lib().prd_set_option(P.h, OPT_FORMAL_SOLVER, DELOPAR) == 0
+    fp64 = P.prec == 0
+    tol = 1e-9 if fp64 else 2e-5
+    lam = P.apply_lambda(_t(G["sigma"], P)).cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(lam - R["lam"])) / np.max(np.abs(R["lam"])) < tol
+    b = P.rhs().cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(b - R["rhs"])) / np.max(np.abs(R["rhs"])) < tol
+    x, info = P.solve(tol=1e-11 if fp64 else 1e-10, max_iter=600, restart=80)
+    x = x.cpu().numpy().astype(np.float64)
+    if fp64:
+        assert np.max(np.abs(x - R["sol"])) / np.max(np.abs(R["sol"])) < 1e-8
+    else:
+        top = P.mu > 0
+        Ig, Io = x[-1, top], R["sol"][-1, top]
+        assert np.max(np.abs(Ig[..., 0] - Io[..., 0]) / Io[..., 0]) < 1e-5
+        for s in (1, 2, 3):
+            assert np.max(np.abs(Ig[..., s] / Ig[..., 0] - Io[..., s] / Io[..., 0])) < 1e-4
+    with pytest.raises(PrdError):
+        P.apply_operator_T(P.empty().zero_())
+    P.close()
+
+
+CONT_CASES = {
+    "twolevel_cont": lambda: inputs.with_continuum(
+        inputs.twolevel_slab(n_z=8, n_x=11, n_mu_half=2, n_chi=4, eps=1e-2), 1e-3, 0.4),
+    "mgii_cont": lambda: inputs.with_continuum(
+        inputs.mgii(n_z=10, n_core_each=9, n_wing=8, n_mu_half=2, n_chi=4, seed=21), 1e-5, 0.3),
+}
+
+
+@pytest.mark.parametrize("name", list(CONT_CASES))
+def test_continuum_matches_oracle(name):
+    """Continuum processes (App. A, prd_set_continuum): extinction on K's
+    diagonal, thermal emission in Stokes I, coherent dipole scattering in the
+    observer frame.  Against the oracle: Sigma x (FP64 1e-9 relative; FP32
+    4e-6 of each height's largest emissivity, the tcgen05 bound), Lambda and
+    the right-hand side (FP64 1e-9, FP32 2e-5), the operator in FP64 (1e-9),
+    the solution (FP64 1e-8; FP32 emergent I 1e-5 relative, Q/I, U/I, V/I
+    1e-4 absolute) and the emergent Stokes vectors off the grid from the
+    oracle's solution (FP64 1e-9; FP32 1e-5)."""
+    from paper_2505_20968_gb300.binding import PRD
+    G = np.load(os.path.join(GOLD, name + ".npz"))
+    P = PRD(CONT_CASES[name](), device=0)
+    fp64 = P.prec == 0
+    x = G["x"]
+    eg = P.apply_sigma(_t(x, P)).cpu().numpy().astype(np.float64)
+    if fp64:
+        assert np.max(np.abs(eg - G["sigma"])) / np.max(np.abs(G["sigma"])) < 1e-9
+    else:
+        for iz in range(P.nz):
+            scale = np.max(np.abs(G["sigma"][iz, ..., 0]))
+            assert np.max(np.abs(eg[iz] - G["sigma"][iz])) / scale < 4e-6, iz
+    tol = 1e-9 if fp64 else 2e-5
+    lam = P.apply_lambda(_t(G["sigma"], P)).cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(lam - G["lam"])) / np.max(np.abs(G["lam"])) < tol
+    b = P.rhs().cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(b - G["rhs"])) / np.max(np.abs(G["rhs"])) < tol
+    if fp64:
+        y = P.apply_operator(_t(x, P)).cpu().numpy()
+        assert np.max(np.abs(y - G["Ax"])) / np.max(np.abs(G["Ax"])) < 1e-9
+    xs, info = P.solve(tol=1e-11 if fp64 else 1e-10, max_iter=600, restart=80)
+    xs = xs.cpu().numpy().astype(np.float64)
+    if fp64:
+        assert np.max(np.abs(xs - G["sol"])) / np.max(np.abs(G["sol"])) < 1e-8
+    else:
+        top = P.mu > 0
+        Ig, Io = xs[-1, top], G["sol"][-1, top]
+        assert np.max(np.abs(Ig[..., 0] - Io[..., 0]) / Io[..., 0]) < 1e-5
+        for s in (1, 2, 3):
+            assert np.max(np.abs(Ig[..., s] / Ig[..., 0] - Io[..., s] / Io[..., 0])) < 1e-4
+    los = G["los"]
+    out = P.emergent_stokes(_t(G["sol"], P), los[:, 0], los[:, 1]).cpu().numpy().astype(np.float64)
+    ref = G["emergent"]
+    t2 = 1e-9 if fp64 else 1e-5
+    assert np.max(np.abs(out[..., 0] - ref[..., 0]) / ref[..., 0]) < t2
+    for s in (1, 2, 3):
+        assert np.max(np.abs(out[..., s] / out[..., 0] - ref[..., s] / ref[..., 0])) < t2
+    P.close()

@@ -431,3 +431,38 @@ def test_rii_coefficients_rebuild_the_oracle_block(tmp_path):
                 G = P.tile(iz, th, P.shift[iz][ku, l], P.shift[iz][ku, lp])
                 rebuilt += np.einsum("ij,nm->nimj", Y[iz, op, ng + t], G).real
             assert np.max(np.abs(rebuilt - ref)) < 1e-10 * np.max(np.abs(ref)), (iz, op)
+
+
+PAR = r'''
+#include <cstdio>
+#include <cstdlib>
+namespace prd { void delopar_weights(double dM, double dP, double* psi); }
+int main(int argc, char** argv) {
+  for (int i = 1; i + 1 < argc; i += 2) {
+    double psi[3];
+    prd::delopar_weights(std::atof(argv[i]), std::atof(argv[i + 1]), psi);
+    std::printf("%.17g %.17g %.17g\n", psi[0], psi[1], psi[2]);
+  }
+  return 0;
+}
+'''
+
+
+def test_host_delopar_weights_match_the_oracle(tmp_path):
+    """DELOPAR's source weights (Sect. 3) of the library (power series of the
+    moments int_0^d t^n e^{-t} dt below d = 0.5, closed forms above) against
+    the oracle's (regularised incomplete gamma), from optically thin to thick
+    steps and for downwind steps thinner and thicker than the current one:
+    1e-12 of the largest weight."""
+    import numpy as np
+    from oracle.problem import delopar_coeffs
+    exe = _build_exe(tmp_path, "par", PAR)
+    pts = [(dM, dP) for dM in (1e-6, 3e-4, 0.02, 0.3, 0.49, 0.51, 1.7, 12.0, 300.0)
+           for dP in (1e-5, 0.01, 0.5, 2.0, 50.0)]
+    args = [repr(x) for dM, dP in pts for x in (dM, dP)]
+    r = subprocess.run([str(exe)] + args, capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0
+    got = np.array([[float(s) for s in line.split()] for line in r.stdout.strip().splitlines()])
+    for (dM, dP), g in zip(pts, got):
+        want = np.array(delopar_coeffs(dM, dP), dtype=float)
+        assert np.max(np.abs(g - want)) <= 1e-12 * np.max(np.abs(want)), (dM, dP, g, want)

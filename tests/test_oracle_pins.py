@@ -499,7 +499,7 @@ def test_gradient_reference_differences_converged():
 
 
 # ---------------------------------------------------------------- polarised formal solution
-def _magnetised_homogeneous_slab(n_z):
+def _magnetised_homogeneous_slab(n_z, formal_solver="delo_linear"):
     """Two-level slab with every height alike (T, a, k, B): K is constant
     along each ray, so the transfer equation has a closed-form solution."""
     cfg = inputs.twolevel_slab(n_z=n_z, n_x=9, n_mu_half=2, n_chi=4, a=2e-2)
@@ -508,14 +508,14 @@ def _magnetised_homogeneous_slab(n_z):
     atm["B_G"][:] = 900.0
     atm["thetaB"][:] = 0.6
     atm["chiB"][:] = 0.9
-    return Problem(cfg, normalise=False)
+    return Problem(cfg, normalise=False, formal_solver=formal_solver)
 
 
-def _delo_error_vs_matrix_exponential(n_z):
+def _delo_error_vs_matrix_exponential(n_z, formal_solver="delo_linear"):
     """Max error of the emergent Stokes vectors of formal_solution for a
     constant emissivity e against I = exp(-K l) I0 + (Id - exp(-K l)) K^-1 e."""
     from scipy.linalg import expm
-    P = _magnetised_homogeneous_slab(n_z)
+    P = _magnetised_homogeneous_slab(n_z, formal_solver)
     e = np.array([1.0, 0.3, -0.2, 0.15])
     out = P.formal_solution(np.broadcast_to(e, P.shape()).copy(), boundary=True)
     err = scale = 0.0
@@ -711,3 +711,86 @@ def test_narrowband_closed_forms():
     rho = 1.0 / np.sqrt(1.0 / s ** 2 + 1.0 / tau ** 2)
     np.testing.assert_allclose(narrowband(lam, X, lam0, fwhm, dl), rho / s * erf(dl / (np.sqrt(2) * rho)),
                                rtol=1e-6)
+
+
+def test_delopar_parabolic_source_exact_and_linear_limit():
+    """DELOPAR (Sect. 3; the source vector parabolic through the upwind,
+    current and downwind points, K'I linear): in an unmagnetised homogeneous
+    slab (K' = 0) a source quadratic in height, hence in optical depth along
+    every ray, is integrated exactly at every point whose step has a
+    downwind neighbour (the last step of a ray is linear):
+        I(T) = I0 e^{-T} + int_0^T e^{-(T - t)} S(t) dt  in closed form;
+    a linear source gives DELO-linear's solution at every point."""
+    from oracle.problem import delo_coeffs
+    cfg = inputs.twolevel_slab(n_z=9, n_x=7, n_mu_half=2, n_chi=4, a=2e-2)
+    cfg["atm"]["z_km"] = np.linspace(0.0, 3.0, 9) + np.array([0, .1, -.05, .2, 0, -.1, .05, 0, 0])
+    par = Problem(cfg, normalise=False, formal_solver="delopar")
+    lin = Problem(cfg, normalise=False)
+    z = par.z
+    S = 0.3 + 0.8 * (z - z[0]) - 0.15 * (z - z[0]) ** 2
+    eps = np.zeros(par.shape())
+    eps[..., 0] = (S[:, None, None] * par.eta1[:, :, :])
+    out = par.formal_solution(eps, boundary=True)
+    for o in range(par.nO):
+        mu = par.mu[o]
+        for n in range(par.nN):
+            eta = par.eta1[0, o, n]
+            # along the ray: tau = eta (z - z_start) / |mu| from the entry point
+            if mu > 0:
+                zs, k = z[0], par.nz - 2
+                I0 = par.WT[0]
+                Sf = lambda t: 0.3 + 0.8 * (mu * t / eta) - 0.15 * (mu * t / eta) ** 2
+            else:
+                zs, k = z[-1], 1
+                I0 = 0.0
+                Sf = lambda t: 0.3 + 0.8 * (z[-1] - z[0] + mu * t / eta) - 0.15 * (z[-1] - z[0] + mu * t / eta) ** 2
+            T = eta * abs(z[k] - zs) / abs(mu)
+            exact = I0 * np.exp(-T) + quad(lambda t: np.exp(-(T - t)) * Sf(t), 0, T, epsabs=1e-14, epsrel=1e-13)[0]
+            assert abs(out[k, o, n, 0] - exact) < 1e-11 * max(1.0, abs(exact)), (o, n)
+    S = 0.3 + 0.8 * (z - z[0])
+    eps[..., 0] = S[:, None, None] * par.eta1
+    np.testing.assert_allclose(par.formal_solution(eps, boundary=True), lin.formal_solution(eps, boundary=True),
+                               rtol=1e-12, atol=1e-13)
+
+
+def test_delopar_polarised_slab_converges_to_matrix_exponential():
+    """DELOPAR in the magnetised homogeneous slab of the DELO-linear pin: the
+    K'I term is linear over a step, so the error falls at second order too
+    (the source there is constant, which both schemes integrate exactly, so
+    the errors equal DELO-linear's: 5.2e-5, 1.3e-5, 3.3e-6 at 21, 41, 81
+    heights).  Swapping psi_M and psi_P fails the parabolic-source pin."""
+    e21, _ = _delo_error_vs_matrix_exponential(21, "delopar")
+    e41, _ = _delo_error_vs_matrix_exponential(41, "delopar")
+    assert e41 < 2e-5
+    assert 3.5 < e21 / e41 < 4.5
+
+
+# ---------------------------------------------------------------- continuum (App. A)
+def test_continuum_phase_matrix_and_photon_budget():
+    """App. A's coherent continuum scattering uses the dipole phase matrix
+    (sum over K <= 2 of (-1)^Q T^K_Q T^K_-Q, every W_K = 1).  The oracle builds
+    it from the polarisation bases (3/4 Tr(sigma_i J sigma_j J^T)); it must
+    equal the frequency-integrated R_II phase matrix of the J 0 -> 1 atom at
+    B = 0 (W_1 = W_2 = 1), built from the atom's scattering amplitudes, for
+    every direction pair; integrate to one over incident directions; obey
+    reciprocity; and under an isotropic unpolarised field W return sigma_c W
+    on Stokes I and nothing on Q, U, V."""
+    cfg = inputs.with_continuum(inputs.twolevel_slab(n_z=3, n_x=7, n_mu_half=2, n_chi=4, eps=1e-2), 1e-3, 0.4)
+    P = Problem(cfg, normalise=False)
+    for o in range(P.nO):
+        tot = np.zeros((4, 4))
+        for op in range(P.nO):
+            R = P.rayleigh(P.mu[o], P.chi[o], P.mu[op], P.chi[op])
+            A = _integrated_phase(P, 0, P.amplitudes(0, P.mu[o], P.chi[o]), P.amplitudes(0, P.mu[op], P.chi[op]))
+            assert np.max(np.abs(R - A)) < 1e-12
+            assert np.max(np.abs(R - P.rayleigh(P.mu[op], P.chi[op], P.mu[o], P.chi[o]).T)) < 1e-13
+            tot += P.wang[op] * R
+        assert abs(tot[0, 0] - 1.0) < 1e-12 and np.max(np.abs(tot[1:, 0])) < 1e-12
+    W = np.zeros(P.shape())
+    W[..., 0] = 0.8
+    full = Problem(cfg, normalise=False)
+    for iz in range(P.nz):
+        C = np.stack([full.continuum_block(iz, P.mu[o], P.chi[o]) for o in range(P.nO)])  # [o, n, i, o', j]
+        e = np.einsum("onipj,pnj->oni", C, W[iz])
+        np.testing.assert_allclose(e[..., 0], 0.8 * P.sig_c[iz][None, :] * np.ones((P.nO, 1)), rtol=1e-12)
+        assert np.max(np.abs(e[..., 1:])) < 1e-12 * 0.8 * np.max(P.sig_c[iz])
