@@ -33,7 +33,7 @@ UNIT = "applies/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # layout tag of the contraction whose DRAM traffic profiles/traffic.json records;
 # the traffic figure is reported only while it matches the kernel that runs
-KERNEL_LAYOUT = "bulk-v3"
+KERNEL_LAYOUT = "resident-ir-v4"
 
 
 def _peaks():
@@ -258,6 +258,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-tol", type=float, default=1e-10,
                     help="GMRES tol; 1e-10 is the largest meeting 1e-5 on emergent I in the Mg II parity case")
+    ap.add_argument("--contraction", default="tf32x3", choices=["tf32x3", "bf16x3"],
+                    help="split products of the timed R_II contraction (tf32x3: FP32-level accuracy)")
     ap.add_argument("--workload", default="mgii", choices=["mgii", "mgii_small", "lambda_wide"],
                     help="mgii_small (8 heights) is only for ncu captures of single kernels; lambda_wide "
                          "(two-level, angle-averaged, 300 heights x 128 directions x 200 frequencies) sizes "
@@ -302,10 +304,18 @@ def main():
     P = PRD(cfg, device=local)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
+    if P.prec == 1:
+        P.set_contraction(args.contraction)
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     x = torch.rand(P.shape, device="cuda", dtype=P.dtype, generator=g)
     x[..., 1:] *= 0.05
     y = P.empty()
+    autotune = None
+    if P.prec == 1:
+        # the contraction's tile-ring depth, measured (tune.py)
+        from paper_2505_20968_gb300.tune import tune_tile_stages
+        best, res = tune_tile_stages(P)
+        autotune = {"tile_stages": best, "ms_per_apply": res}
     for _ in range(args.warmup):
         P.apply_operator(x, y)
     torch.cuda.synchronize()
@@ -377,7 +387,7 @@ def main():
             traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
-    roofline = {"bound": "tensor", "kernel": "r2_tc_kernel (S3+S4 R_II contraction, tcgen05 3xTF32)",
+    roofline = {"bound": "tensor", "kernel": f"r2_tc_kernel (S3+S4 R_II contraction, tcgen05 {args.contraction})",
                 "achieved": achieved_tf, "peak": tf32_peak, "unit": "TFLOP/s", "frac": achieved_tf / tf32_peak,
                 "useful_frac": achieved_tf / tf32_peak, "issued_frac": issued_tf / tf32_peak,
                 "issued": issued_tf,
@@ -399,11 +409,35 @@ def main():
                                  "frac": delo_bytes / (delo_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                  "l2_resident": delo_bytes < 129e6}
 
+    # the split-BF16 contraction (BF16x3) on the same context: contraction time and
+    # the refined solve at the same tolerance (the FP64 residuals fix the accuracy)
+    modes = {}
+    if cfg.get("precision", "fp32") == "fp32" and not args.no_solve and args.contraction == "tf32x3":
+        P.set_contraction("bf16x3")
+        for _ in range(2):
+            P.apply_operator(x, y)
+        P.set_profiling(True)
+        for _ in range(3):
+            P.apply_operator(x, y)
+        st16 = P.stage_times()
+        P.set_profiling(False)
+        b16_ms = st16["S3_R2_contraction"][0] / max(st16["S3_R2_contraction"][1], 1)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        sol16, info16 = P.solve(tol=args.solve_tol, max_iter=900, restart=200, check=False)
+        torch.cuda.synchronize()
+        modes["bf16x3"] = {"contraction_ms": b16_ms, "useful_tflops": useful / (b16_ms * 1e-3) / 1e12,
+                           "issued_frac_of_bf16_peak": 3.0 * flops / (b16_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                           "solve_seconds": time.time() - t0, "solve_applies": info16["iters"],
+                           "solve_true_rel_res": info16["true_rel_res"], "rc": info16["rc"]}
+        P.set_contraction("tf32x3")
+        modes["tf32x3"] = {"contraction_ms": r2_ms, "useful_tflops": achieved_tf}
+
     solve = None
     if not args.no_solve:
         torch.cuda.synchronize()
         t0 = time.time()
-        sol, info = P.solve(tol=args.solve_tol, max_iter=600, restart=60, check=False)
+        sol, info = P.solve(tol=args.solve_tol, max_iter=600, restart=200, check=False)
         torch.cuda.synchronize()
         solve = {"seconds": time.time() - t0, "tol": args.solve_tol, "applies": info["iters"],
                  "true_rel_res": info["true_rel_res"], "rc": info["rc"], "setup_seconds": setup_s}
@@ -422,7 +456,8 @@ def main():
                 "clocks": clk,
                 "e2e": {"value": job_value(world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes},
-                "gpu_launches": 8 * args.steps, "roofline": roofline, "cpu_baseline": cpu, "solve": solve}
+                "gpu_launches": 8 * args.steps, "roofline": roofline, "cpu_baseline": cpu, "solve": solve,
+                "contraction_modes": modes, "autotune": autotune}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -51,7 +51,15 @@ enum {
   PRD_E_TIMEOUT = -8     /* a bounded device wait expired                   */
 };
 
-enum { PRD_FP64 = 0, PRD_FP32 = 1 };
+/* Precision of a context.  PRD_FP64: every table, vector and product in
+ * FP64.  PRD_FP32: FP32 tables and vectors with FP64 reductions and an FP64
+ * residual refinement in prd_solve; the R_II contraction runs on the tcgen05
+ * tensor cores as 3xTF32 split products (<= 3 * 2^-22 per product).
+ * PRD_FP32_BF16X3: the same, with split-BF16 products (hi*hi + hi*lo + lo*hi
+ * of bf16 halves, <= 3 * 2^-18 per product, twice the TF32 tensor rate); the
+ * context is a PRD_FP32 context (vectors are float) whose contraction is
+ * BF16x3, see PRD_OPT_CONTRACTION. */
+enum { PRD_FP64 = 0, PRD_FP32 = 1, PRD_FP32_BF16X3 = 2 };
 enum { PRD_TWO_LEVEL = 0, PRD_TWO_TERM = 1 };
 enum { PRD_GRID_LAMBDA = 0, PRD_GRID_X = 1 };
 enum { PRD_MU_GL_HEMISPHERES = 0, PRD_MU_GL_FULL = 1 };
@@ -75,7 +83,8 @@ typedef struct {
 } prd_atom;
 
 /* Create a context on CUDA device `device` with arithmetic `precision`
- * (PRD_FP64 or PRD_FP32).  *out receives the handle (NULL on failure). */
+ * (PRD_FP64, PRD_FP32 or PRD_FP32_BF16X3).  *out receives the handle (NULL
+ * on failure). */
 int prd_create(prd_ctx** out, int device, int precision);
 /* Free the context and all library-owned device memory.  NULL is a no-op. */
 int prd_destroy(prd_ctx* ctx);
@@ -213,7 +222,7 @@ int prd_solve_adjoint(prd_ctx* ctx, const void* g_dev, double tol, int max_iter,
  * Sigma* unpolarised, unmagnetised PRD-AA; m_in block-Jacobi-preconditioned
  * Richardson sweeps from zero (Sect. 5.2, App. F). */
 int prd_apply_preconditioner(prd_ctx* ctx, const void* y_dev, void* x_dev);
-/* Set the number of inner sweeps m_in (>= 1, default 2) of the preconditioner. */
+/* Set the number of inner sweeps m_in (>= 1, default 3) of the preconditioner. */
 int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
 
 /* Options.  PRD_OPT_TENSOR_CORES (FP32 only): 1 runs the R_II contraction on
@@ -241,9 +250,18 @@ int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
  * GMRES applies to either; every formal solution (Lambda, the right-hand
  * side, emergent Stokes vectors, the refinement residuals) uses the choice.
  * The transposed operator, the adjoint solve and prd_grad_B are built for
- * DELO-linear and return PRD_E_STATE under PRD_DELOPAR. */
+ * DELO-linear and return PRD_E_STATE under PRD_DELOPAR.
+ * PRD_OPT_CONTRACTION (FP32 contexts): the split products of the tensor-core
+ * R_II contraction, PRD_CONTRACTION_TF32X3 (the PRD_FP32 default) or
+ * PRD_CONTRACTION_BF16X3 (the PRD_FP32_BF16X3 default).  prd_solve's FP64
+ * residuals do not use the contraction, so the solution's accuracy is the
+ * same with either; the inner iterations count changes.
+ * PRD_OPT_TILE_STAGES: depth of the contraction's tile ring, 2..5 (capped at
+ * the deepest that fits in shared memory beside the resident I~) or 0 for
+ * that deepest ring (default); a schedule parameter for measured tuning. */
 enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2, PRD_OPT_WAIT_POLLS = 3, PRD_OPT_TEST_ZERO_OPERATOR = 4,
-       PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6 };
+       PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6, PRD_OPT_CONTRACTION = 7, PRD_OPT_TILE_STAGES = 8 };
+enum { PRD_CONTRACTION_TF32X3 = 0, PRD_CONTRACTION_BF16X3 = 1 };
 enum { PRD_DELO_LINEAR = 0, PRD_DELOPAR = 1 };
 int prd_set_option(prd_ctx* ctx, int option, int value);
 /* Synchronise the ctx stream and report device-side failures: a CUDA error,

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libprd.so")
 PRD_OK = 0
 ERRORS = {-1: "PRD_E_ARG", -2: "PRD_E_STATE", -3: "PRD_E_CUDA", -4: "PRD_E_NOMEM", -5: "PRD_E_NOCONV",
           -6: "PRD_E_BREAKDOWN", -7: "PRD_E_NAN", -8: "PRD_E_TIMEOUT"}
-PRD_FP64, PRD_FP32 = 0, 1
+PRD_FP64, PRD_FP32, PRD_FP32_BF16X3 = 0, 1, 2
 
 
 class PrdError(RuntimeError):
@@ -129,10 +129,11 @@ class PRD:
         L = lib()
         prec = cfg.get("precision", "fp32") if precision is None else precision
         self.prec = PRD_FP64 if prec in ("fp64", PRD_FP64) else PRD_FP32
+        create = PRD_FP32_BF16X3 if prec == "fp32_bf16x3" else self.prec
         self.dtype = torch.float64 if self.prec == PRD_FP64 else torch.float32
         self.device = torch.device("cuda", device)
         h = ctypes.c_void_p()
-        self._check(L.prd_create(ctypes.byref(h), device, self.prec), None)
+        self._check(L.prd_create(ctypes.byref(h), device, create), None)
         self.h = h
         atom = cfg["atom"]
         A = _Atom(atom["kind"], atom["twoS"], (ctypes.c_double * 2)(*atom["E_u_cm"]), atom["mass_amu"],
@@ -267,6 +268,14 @@ class PRD:
 
     def set_tensor_cores(self, on=True):
         self._check(lib().prd_set_option(self.h, 1, 1 if on else 0))
+
+    def set_tile_stages(self, n):
+        """Depth of the contraction's tile ring (0: the deepest that fits)."""
+        self._check(lib().prd_set_option(self.h, 8, int(n)))
+
+    def set_contraction(self, kind):
+        """Split products of the tensor-core contraction: "tf32x3" or "bf16x3"."""
+        self._check(lib().prd_set_option(self.h, 7, {"tf32x3": 0, "bf16x3": 1}[kind]))
 
     def device_status(self):
         self._check(lib().prd_device_status(self.h))

@@ -176,7 +176,9 @@ extern "C" {
 int prd_create(prd_ctx** out, int device, int precision) {
   if (!out) return PRD_E_ARG;
   *out = nullptr;
-  if (precision != PRD_FP64 && precision != PRD_FP32) return PRD_E_ARG;
+  if (precision != PRD_FP64 && precision != PRD_FP32 && precision != PRD_FP32_BF16X3) return PRD_E_ARG;
+  const bool bf16x3 = precision == PRD_FP32_BF16X3;
+  if (bf16x3) precision = PRD_FP32;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -189,6 +191,7 @@ int prd_create(prd_ctx** out, int device, int precision) {
   h->c.prec = precision;
   h->c.esz = precision == PRD_FP64 ? 8 : 4;
   h->c.use_tc = precision == PRD_FP32 ? 1 : 0;   // tcgen05 contraction by default in FP32
+  h->c.tc_bf16 = bf16x3 ? 1 : 0;
   if (cudaDeviceGetAttribute(&h->c.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete h;
     return PRD_E_CUDA;
@@ -596,6 +599,18 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
   if (option == PRD_OPT_FORMAL_SOLVER) {
     if (value != PRD_DELO_LINEAR && value != PRD_DELOPAR) return fail(c, PRD_E_ARG, "unknown formal solver");
     c->formal = value;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_CONTRACTION) {
+    if (value != PRD_CONTRACTION_TF32X3 && value != PRD_CONTRACTION_BF16X3)
+      return fail(c, PRD_E_ARG, "unknown contraction product");
+    if (c->prec != PRD_FP32) return fail(c, PRD_E_ARG, "the split products are for PRD_FP32 contexts");
+    c->tc_bf16 = value == PRD_CONTRACTION_BF16X3 ? 1 : 0;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_TILE_STAGES) {
+    if (value != 0 && (value < 2 || value > 5)) return fail(c, PRD_E_ARG, "tile stages must be 0 or in [2, 5]");
+    c->tc_stages = value;
     return PRD_OK;
   }
   if (option == PRD_OPT_TEST_ZERO_OPERATOR) {

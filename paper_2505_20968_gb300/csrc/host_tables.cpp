@@ -238,6 +238,7 @@ void los_tables(const Ctx* c, double mu, double chi, LosTables& L) {
         L.epsth[q * 4] += c->epsc[q];
       }
       const double e1 = K[0][0];
+      L.eta_line[(size_t)iz * N + n] /= e1;   // the line's share of eta_I
       double* t = &L.kt[((size_t)iz * N + n) * 10];
       t[0] = K[0][1] / e1; t[1] = K[0][2] / e1; t[2] = K[0][3] / e1;
       t[3] = K[1][2] / e1; t[4] = K[1][3] / e1; t[5] = K[2][3] / e1;
@@ -327,6 +328,7 @@ int build_device_tables(Ctx* c) {
         }
         const double e1 = K[0][0];
         eta[pt] = e1;
+        etal[pt] /= e1;   // the line's share of eta_I
         double* t = &kt[pt * 10];
         t[0] = K[0][1] / e1; t[1] = K[0][2] / e1; t[2] = K[0][3] / e1;
         t[3] = K[1][2] / e1; t[4] = K[1][3] / e1; t[5] = K[2][3] / e1;
@@ -363,7 +365,10 @@ int build_device_tables(Ctx* c) {
       }
   }
   int rc;
-  if ((rc = upload_T(c, c->kt, kt)) || (rc = upload_T(c, c->epsth, epsth)) || (rc = upload_T(c, c->par, par)) ||
+  // the DELOPAR weights stay FP64 in both modes: with uneven steps they are large and of
+  // opposite sign, and their FP32 rounding would reach the FP64 residuals of the refinement
+  if ((rc = upload_T(c, c->kt, kt)) || (rc = upload_T(c, c->epsth, epsth)) ||
+      (rc = upload(c, c->par, par.data(), par.size() * 8)) ||
       (rc = upload(c, c->eta_line, etal.data(), npt * 8)))
     return rc;
   if (c->has_cont()) {

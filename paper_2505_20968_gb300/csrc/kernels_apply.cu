@@ -457,26 +457,57 @@ __device__ __forceinline__ void kprime(const T* t, A K[4][4]) {
 // arriving at each point (the source vector parabolic through the upwind,
 // current and downwind points; the K'I term stays linear, with DELO-linear's
 // a, b; the last point of a ray has psi = (a, b, 0)).
+// Per-point inputs of one step of the formal solution.
 template <typename T, typename A>
-__global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt, const T* __restrict__ par,
+struct DeloPoint {
+  T t[10];          // K'/eta1 (6), 1/eta1, exp(-dtau), alpha, beta
+  A e[4];           // emissivity
+  A xs[4];          // x of y = x - Lambda eps (zero if unused)
+  double ps[3];     // DELOPAR source weights
+};
+
+template <typename T, typename A>
+__device__ __forceinline__ void delo_load(DeloPoint<T, A>& d, const A* __restrict__ eps, const T* __restrict__ kt,
+                                          const double* __restrict__ par, const A* __restrict__ x_sub, size_t pt) {
+  for (int i = 0; i < 10; ++i) d.t[i] = kt[pt * 10 + i];
+  for (int s = 0; s < 4; ++s) d.e[s] = eps[pt * 4 + s];
+  for (int s = 0; s < 4; ++s) d.xs[s] = x_sub ? x_sub[pt * 4 + s] : (A)0;
+  if (par)
+    for (int i = 0; i < 3; ++i) d.ps[i] = par[pt * 3 + i];
+}
+
+// Formal solution along every ray (Sect. 3): DELO-linear, or DELOPAR when
+// `par` holds the parabolic source weights (psi_M, psi_O, psi_P) of the step
+// arriving at each point (the source vector parabolic through the upwind,
+// current and downwind points; the K'I term stays linear, with DELO-linear's
+// a, b; the last point of a ray has psi = (a, b, 0)).  One thread per ray
+// (Omega, nu); the sweep is sequential in height, so the inputs of the next
+// two points are loaded while a point is solved (few rays per SM, so the
+// memory parallelism has to come from within each ray).
+template <typename T, typename A>
+__global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ par,
                             const double* __restrict__ mu, const A* __restrict__ x_sub, A* __restrict__ out, int nz,
                             int nO, int N, int boundary, double WT0) {
   const int ray = blockIdx.x * blockDim.x + threadIdx.x;
   if (ray >= nO * N) return;
   const int o = ray / N, n = ray - o * N;
   const bool up = mu[o] > 0.0;
+  auto point = [&](int p) { return ((size_t)(up ? p : nz - 1 - p) * nO + o) * N + n; };
   A I[4] = {0, 0, 0, 0};
   A Sp[4] = {0, 0, 0, 0};
   A Kp[4][4];
+  DeloPoint<T, A> cur, nx1, nx2;
+  delo_load(cur, eps, kt, par, x_sub, point(0));
+  if (nz > 1) delo_load(nx1, eps, kt, par, x_sub, point(1));
   for (int p = 0; p < nz; ++p) {
-    const int k = up ? p : nz - 1 - p;
-    const size_t pt = ((size_t)k * nO + o) * N + n;
-    const T* t = kt + pt * 10;
+    const size_t pt = point(p);
+    if (p + 2 < nz) delo_load(nx2, eps, kt, par, x_sub, point(p + 2));
+    const T* t = cur.t;
     A Kk[4][4];
     kprime(t, Kk);
     const A ie = t[6];
     A S[4];
-    for (int s = 0; s < 4; ++s) S[s] = eps[pt * 4 + s] * ie;
+    for (int s = 0; s < 4; ++s) S[s] = cur.e[s] * ie;
     if (p == 0) {
       I[0] = (boundary && up) ? (A)WT0 : (A)0;
       I[1] = I[2] = I[3] = (A)0;
@@ -494,13 +525,12 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
       A pM = al, pO = be, pP = (A)0;
       A SP[4] = {0, 0, 0, 0};
       if (par) {
-        pM = (A)par[pt * 3];
-        pO = (A)par[pt * 3 + 1];
-        pP = (A)par[pt * 3 + 2];
+        pM = (A)cur.ps[0];
+        pO = (A)cur.ps[1];
+        pP = (A)cur.ps[2];
         if (p + 1 < nz) {
-          const size_t pt2 = ((size_t)(up ? p + 1 : nz - 2 - p) * nO + o) * N + n;
-          const A ie2 = kt[pt2 * 10 + 6];
-          for (int s = 0; s < 4; ++s) SP[s] = eps[pt2 * 4 + s] * ie2;
+          const A ie2 = nx1.t[6];
+          for (int s = 0; s < 4; ++s) SP[s] = nx1.e[s] * ie2;
         }
       }
       A rhs[4];
@@ -529,24 +559,29 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
       }
       for (int i = 0; i < 4; ++i) I[i] = thick ? S[i] + D[i] : D[i];
     }
-    for (int s = 0; s < 4; ++s) {
-      out[pt * 4 + s] = x_sub ? x_sub[pt * 4 + s] - I[s] : I[s];
-    }
+    for (int s = 0; s < 4; ++s) out[pt * 4 + s] = x_sub ? cur.xs[s] - I[s] : I[s];
     for (int i = 0; i < 4; ++i) {
       Sp[i] = S[i];
       for (int j = 0; j < 4; ++j) Kp[i][j] = Kk[i][j];
     }
+    cur = nx1;
+    nx1 = nx2;
   }
 }
 
-// f = (1 - eps) W_T eta_I / [Sigma (W_T, 0, 0, 0)]_I with the line's eta_I (App. E)
-template <typename A>
-__global__ void normalise_kernel(const A* __restrict__ num, const double* __restrict__ eta_line,
+// f = (1 - eps) W_T eta_I / [Sigma (W_T, 0, 0, 0)]_I with the line's eta_I (App. E),
+// written as (1 - eps) W_T rho / (kt6 num) with rho = eta_line / eta_total (FP64)
+// and kt6 the stored 1/eta_total of the formal solver's tables: the source
+// f num kt6 then holds the photon budget exactly whatever the rounding of kt6
+// (an FP32 1/eta against an FP64 eta would break it at 1e-7, which the
+// scattering amplifies by ~1/eps).
+template <typename T, typename A>
+__global__ void normalise_kernel(const A* __restrict__ num, const T* __restrict__ kt, const double* __restrict__ rho,
                                  const double* __restrict__ fac, double* __restrict__ f, int nz, int nO, int N) {
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= (long long)nz * nO * N) return;
   const int iz = (int)(pt / ((long long)nO * N));
-  f[pt] = fac[iz] * eta_line[pt] / (double)num[pt * 4];
+  f[pt] = fac[iz] * rho[pt] / ((double)kt[pt * 10 + 6] * (double)num[pt * 4]);
 }
 
 // Coherent continuum scattering in the observer frame (App. A):
@@ -710,7 +745,7 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
                                                                        N, boundary ? 1 : 0, c->WT[0]);
   else
     delo_kernel<float, float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p,
-                                                                      (const float*)c->par_active(), dmu,
+                                                                      (const double*)c->par_active(), dmu,
                                                                       (const float*)sub_from, (float*)out, nz, nO, N,
                                                                       boundary ? 1 : 0, c->WT[0]);
   stage_end(c, ST_S7, e0);
@@ -742,8 +777,9 @@ int compute_normalisation(Ctx* c) {
     fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
     rc = sigma_T<double, double>(c, (const double*)xin.p, (double*)num.p, false);
     if (!rc)
-      normalise_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
-          (const double*)num.p, (const double*)c->eta_line.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
+      normalise_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const double*)c->kt.p, (const double*)c->eta_line.p, (const double*)fac.p,
+          (double*)c->f.p, nz, nO, N);
   } else {
     fill_planck_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>((double*)xin.p, (const double*)wt.p, nz, nO, N);
     rc = c->has64 ? sigma_T<double, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p,
@@ -751,8 +787,9 @@ int compute_normalisation(Ctx* c) {
                   : sigma_T<float, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p,
                                            (double*)Ic.p);
     if (!rc)
-      normalise_kernel<double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
-          (const double*)num.p, (const double*)c->eta_line.p, (const double*)fac.p, (double*)c->f.p, nz, nO, N);
+      normalise_kernel<float, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const float*)c->kt.p, (const double*)c->eta_line.p, (const double*)fac.p,
+          (double*)c->f.p, nz, nO, N);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cleanup();
@@ -779,7 +816,7 @@ int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws /* 4 x nve
                      : sigma_T<float, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv);
   if (rc) return rc;
   delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
-      eps, (const float*)c->kt.p, (const float*)c->par_active(), (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu,
+      eps, (const float*)c->kt.p, (const double*)c->par_active(), (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu,
       0, c->WT[0]);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
@@ -795,7 +832,7 @@ int rhs_acc(Ctx* c, double* b) {
   std::vector<double> hd(h.begin(), h.end());
   cudaMemcpy(e64.p, hd.data(), nv * 8, cudaMemcpyHostToDevice);
   delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
-      (const double*)e64.p, (const float*)c->kt.p, (const float*)c->par_active(), (const double*)c->dmu.p, nullptr, b,
+      (const double*)e64.p, (const float*)c->kt.p, (const double*)c->par_active(), (const double*)c->dmu.p, nullptr, b,
       c->nz, c->nO, c->nnu, 1, c->WT[0]);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   dfree(e64);
@@ -818,15 +855,16 @@ __global__ void planck_comoving_kernel(T* __restrict__ Ic, const double* __restr
   Ic[pt * 4 + 1] = Ic[pt * 4 + 2] = Ic[pt * 4 + 3] = (T)0;
 }
 
-// eps(z, n) = (eps_sc with f) + eps_th;  f = (1-eps) W_T eta_I / num_I
+// eps(z, n) = (eps_sc with f) + eps_th;  f = (1-eps) W_T eta_I / num_I, formed
+// as in normalise_kernel from rho = eta_line / eta_total and the stored 1/eta_total
 template <typename T, typename A>
-__global__ void los_combine_kernel(const A* __restrict__ es, const A* __restrict__ ew, const double* __restrict__ eta_line,
-                                   const T* __restrict__ eth, const double* __restrict__ fac, A* __restrict__ out,
-                                   int nz, int N) {
+__global__ void los_combine_kernel(const A* __restrict__ es, const A* __restrict__ ew, const T* __restrict__ kt,
+                                   const double* __restrict__ rho, const T* __restrict__ eth,
+                                   const double* __restrict__ fac, A* __restrict__ out, int nz, int N) {
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= nz * N) return;
   const int iz = pt / N;
-  const double f = fac[iz] * eta_line[pt] / (double)ew[pt * 4];
+  const double f = fac[iz] * rho[pt] / ((double)kt[pt * 10 + 6] * (double)ew[pt * 4]);
   out[pt * 4] = (A)((double)es[pt * 4] * f + (double)eth[pt * 4]);
   for (int s = 1; s < 4; ++s) out[pt * 4 + s] = es[pt * 4 + s] + (A)eth[pt * 4 + s];
 }
@@ -897,7 +935,8 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
       return upload(c, b, h.data(), h.size() * sizeof(T));
     };
     if ((rc = up(Yd, L.Y)) || (rc = up(rout, L.rout)) || (rc = up(ktd, L.kt)) || (rc = up(ethd, L.epsth)) ||
-        (rc = up(pard, L.par)) || (rc = upload(c, etald, L.eta_line.data(), L.eta_line.size() * 8)) ||
+        (rc = upload(c, pard, L.par.data(), L.par.size() * 8)) ||
+        (rc = upload(c, etald, L.eta_line.data(), L.eta_line.size() * 8)) ||
         (rc = upload(c, cpwd, L.cont_pw.data(), L.cont_pw.size() * 8)) ||
         (rc = upload(c, kidx, L.kidx.data(), L.kidx.size() * 4)) || (rc = upload(c, ttd, L.tt.data(), L.tt.size() * 8)) ||
         (rc = upload(c, dmu, &mus[l], 8)))
@@ -932,14 +971,15 @@ static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const dou
         (const A*)ew_bar.p, (const A*)M.p, (const int*)kidx.p, (const double*)ttd.p, (const double*)c->sp.p, nullptr,
         (A*)ew.p, nz, 1, N);
     los_combine_kernel<T, A><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const A*)es.p, (const A*)ew.p,
-                                                                          (const double*)etald.p, (const T*)ethd.p,
+                                                                          (const T*)ktd.p, (const double*)etald.p,
+                                                                          (const T*)ethd.p,
                                                                           (const double*)fac.p, (A*)eps.p, nz, N);
     if (c->has_cont())
       continuum_kernel<A><<<ceil_div(nz * N, 128), 128, 0, c->stream>>>((const A*)xa.p, (const double*)cpwd.p,
                                                                        (const double*)c->cont_sig.p, (A*)eps.p, nz,
                                                                        1, nO, N);
     delo_kernel<T, A><<<ceil_div(N, 128), 128, 0, c->stream>>>((const A*)eps.p, (const T*)ktd.p,
-                                                             c->formal ? (const T*)pard.p : nullptr,
+                                                             c->formal ? (const double*)pard.p : nullptr,
                                                              (const double*)dmu.p, nullptr, (A*)lam.p, nz, 1, N, 1,
                                                              c->WT[0]);
     cast_kernel<A, T><<<ceil_div(N * 4, 128), 128, 0, c->stream>>>((const A*)lam.p + (size_t)(nz - 1) * N * 4,

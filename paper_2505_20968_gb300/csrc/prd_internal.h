@@ -58,7 +58,7 @@ struct Ctx {
   int nnu = 0;
   std::vector<double> grid;
   int grid_kind = 0, n_mu_half = 0, n_chi = 0, mu_rule = 0, mode = 0;
-  int m_in = 2;
+  int m_in = 3;   // preconditioner sweeps (the fastest Mg II solve of a sweep over 1..3)
 
   // ---- derived on host
   int nO = 0;
@@ -118,8 +118,8 @@ struct Ctx {
   DBuf r3J;          // [z][uv] complex scratch
   DBuf r3ab;         // [z][uv] complex (beta-alpha) * k * c3
   DBuf kt;           // [z][o][n][10] K'/eta1 (6), 1/eta1, exp(-d), alpha, beta
-  DBuf par;          // [z][o][n][3] DELOPAR source weights psi_M, psi_O, psi_P of the step arriving there
-  DBuf eta_line;     // [z][o][n] the line's eta_I (double): the Kirchhoff factor normalises the line only
+  DBuf par;          // [z][o][n][3] DELOPAR source weights psi_M, psi_O, psi_P of the step arriving there (double)
+  DBuf eta_line;     // [z][o][n] the line's share eta_line/eta_total of eta_I (double): f normalises the line only
   DBuf cont_pw;      // [o][o'][4][4] w_o' P(o, o') dipole phase matrix of continuum scattering (double)
   DBuf cont_sig;     // [z][n] sigma_c (double)
   int formal = 0;    // formal solver: 0 DELO-linear, 1 DELOPAR (PRD_OPT_FORMAL_SOLVER)
@@ -156,6 +156,8 @@ struct Ctx {
   bool tc_ready = false;
   int use_tc = 0;
   long long tc_spin = 0;   // poll limit of the contraction's pipeline waits (0: the default)
+  int tc_bf16 = 0;         // contraction products: 0 3xTF32, 1 split-BF16 (BF16x3)
+  int tc_stages = 0;       // tile ring depth of the contraction (0: the deepest that fits)
   // stage timing (prd_set_profiling): events on the ctx stream around each stage
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -203,7 +205,7 @@ struct LosTables {
   std::vector<double> rout;    // [z][nuv][nl][4][2]
   std::vector<double> kt;      // [z][N][10]
   std::vector<double> par;     // [z][N][3]  DELOPAR source weights
-  std::vector<double> eta_line;   // [z][N]  the line's eta_I
+  std::vector<double> eta_line;   // [z][N]  the line's share eta_line/eta_total of eta_I
   std::vector<double> cont_pw;    // [nO][4][4]  w_o' P(LOS, o') (continuum scattering)
   std::vector<double> epsth;   // [z][N][4]
   std::vector<int> kidx;       // [z][N]   back-interpolation intervals

@@ -26,8 +26,10 @@
 // HBM latency at full bandwidth.
 // Accumulator: 128 TMEM lanes x NM columns.  Every mbarrier wait is bounded; on
 // expiry the CTA records an error flag, drains what it issued and returns.
+#include <algorithm>
 #include <cstdio>
 #include <vector>
+#include <cuda_bf16.h>
 #include "prd_internal.h"
 #include "device_common.cuh"
 
@@ -136,6 +138,40 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
       ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// BF16 operands (kind::f16), FP32 accumulation, K = 16 per instruction
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// shared-memory matrix descriptor: K-major, 32-byte swizzle (rows of 16 bf16),
+// 8-row groups 256 B apart
+__device__ __forceinline__ uint64_t sdesc32(const void* p) {
+  const uint64_t addr = (smem_u32(p) & 0x3FFFF) >> 4;
+  const uint64_t lbo = 1;            // unused for swizzled K-major
+  const uint64_t sbo = 256 >> 4;
+  return addr | (lbo << 16) | (sbo << 32) | (1ull << 46) | (6ull << 61);
+}
+// byte offset of the 4 bf16 of k-group g (k = 4g .. 4g + 3, g < 4) of `row` in a
+// K-major 32-byte-swizzled operand: the 16-byte half (g >> 1) is exchanged with
+// the other in rows whose bit 2 is set
+__device__ __forceinline__ uint32_t swz32(int row, int g) {
+  return (uint32_t)row * 32u + (uint32_t)(((g >> 1) ^ ((row >> 2) & 1)) * 16) + (uint32_t)(g & 1) * 8u;
+}
+// v split into bf16 hi = rn(v) and lo = rn(v - hi): |v - hi - lo| <= 2^-18 |v|;
+// the three products hi*hi + hi*lo + lo*hi then leave <= 3 * 2^-18 |a b|
+__device__ __forceinline__ void bf16_split4(float4 v, uint2& hi, uint2& lo) {
+  const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+  const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+  const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+  const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+  hi.x = *reinterpret_cast<const uint32_t*>(&h0);
+  hi.y = *reinterpret_cast<const uint32_t*>(&h1);
+  lo.x = *reinterpret_cast<const uint32_t*>(&l0);
+  lo.y = *reinterpret_cast<const uint32_t*>(&l1);
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -186,6 +222,10 @@ __device__ __forceinline__ bool gen_all(bool v) {
   return r != 0;
 }
 
+// kBF16: the split-BF16 products (BF16x3) instead of 3xTF32; the builders then
+// split the tile step into bf16 hi and lo planes too, and the operands are
+// K-major with 32-byte rows (16 bf16 of K)
+template <bool kBF16>
 __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned base, derived by offset so that the compiler keeps the
@@ -317,12 +357,23 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         unsigned char* Alo = cbuf + cb * CB;
         unsigned char* Bhi = Alo + SA;
         unsigned char* Blo = Bhi + kBBytes;
-        for (int ks = 0; ks < 2; ++ks) {
-          const int o = ks * 32;                   // 8 fp32 of K per MMA
-          const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(tmem, sdesc(Bhi + o), sdesc(A + o), idesc, acc);
-          mma_tf32(tmem, sdesc(Blo + o), sdesc(A + o), idesc, 1u);
-          mma_tf32(tmem, sdesc(Bhi + o), sdesc(Alo + o), idesc, 1u);
+        if constexpr (kBF16) {
+          // A_hi and A_lo planes share the A_lo buffer (NM x 32 bytes each)
+          const uint32_t idesc16 =
+              (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NM >> 3) << 17) | ((128u >> 4) << 24);
+          unsigned char* Ah = Alo;
+          unsigned char* Al = Alo + SA / 2;
+          mma_bf16(tmem, sdesc32(Bhi), sdesc32(Ah), idesc16, it > 0 ? 1u : 0u);
+          mma_bf16(tmem, sdesc32(Blo), sdesc32(Ah), idesc16, 1u);
+          mma_bf16(tmem, sdesc32(Bhi), sdesc32(Al), idesc16, 1u);
+        } else {
+          for (int ks = 0; ks < 2; ++ks) {
+            const int o = ks * 32;                 // 8 fp32 of K per MMA
+            const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(tmem, sdesc(Bhi + o), sdesc(A + o), idesc, acc);
+            mma_tf32(tmem, sdesc(Blo + o), sdesc(A + o), idesc, 1u);
+            mma_tf32(tmem, sdesc(Bhi + o), sdesc(Alo + o), idesc, 1u);
+          }
         }
         mma_commit(&empty[s]);
         mma_commit(&cfree[cb]);
@@ -437,12 +488,21 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 #pragma unroll
         for (int r = 0; r < kAR; ++r)
           if (gt + r * kGen < nq4) {
-            float4 l;
-            l.x = tf32_hi(v[r].x - tf32_trunc(v[r].x));
-            l.y = tf32_hi(v[r].y - tf32_trunc(v[r].y));
-            l.z = tf32_hi(v[r].z - tf32_trunc(v[r].z));
-            l.w = tf32_hi(v[r].w - tf32_trunc(v[r].w));
-            l4[gt + r * kGen] = l;
+            if constexpr (kBF16) {
+              // float4 idx of the 64-byte-swizzled stage holds k-group g of its row
+              const int idx = gt + r * kGen, row = idx >> 2, g = (idx & 3) ^ ((row >> 1) & 3);
+              uint2 hi, lo;
+              bf16_split4(v[r], hi, lo);
+              *(uint2*)(Alo + swz32(row, g)) = hi;
+              *(uint2*)(Alo + SA / 2 + swz32(row, g)) = lo;
+            } else {
+              float4 l;
+              l.x = tf32_hi(v[r].x - tf32_trunc(v[r].x));
+              l.y = tf32_hi(v[r].y - tf32_trunc(v[r].y));
+              l.z = tf32_hi(v[r].z - tf32_trunc(v[r].z));
+              l.w = tf32_hi(v[r].w - tf32_trunc(v[r].w));
+              l4[gt + r * kGen] = l;
+            }
           }
       }
 #pragma unroll
@@ -516,13 +576,20 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           if (kb + q >= 2 * N) z[q] = 0.f;                  // columns past 2N (zero tile columns)
-        float4 hi, lo;
-        hi.x = tf32_hi(z[0]); lo.x = tf32_hi(z[0] - hi.x);
-        hi.y = tf32_hi(z[1]); lo.y = tf32_hi(z[1] - hi.y);
-        hi.z = tf32_hi(z[2]); lo.z = tf32_hi(z[2] - hi.z);
-        hi.w = tf32_hi(z[3]); lo.w = tf32_hi(z[3] - hi.w);
-        *(float4*)(Bhi + swz64(row, kq * 4)) = hi;
-        *(float4*)(Blo + swz64(row, kq * 4)) = lo;
+        if constexpr (kBF16) {
+          uint2 hi, lo;
+          bf16_split4(make_float4(z[0], z[1], z[2], z[3]), hi, lo);
+          *(uint2*)(Bhi + swz32(row, kq)) = hi;
+          *(uint2*)(Blo + swz32(row, kq)) = lo;
+        } else {
+          float4 hi, lo;
+          hi.x = tf32_hi(z[0]); lo.x = tf32_hi(z[0] - hi.x);
+          hi.y = tf32_hi(z[1]); lo.y = tf32_hi(z[1] - hi.y);
+          hi.z = tf32_hi(z[2]); lo.z = tf32_hi(z[2] - hi.z);
+          hi.w = tf32_hi(z[3]); lo.w = tf32_hi(z[3] - hi.w);
+          *(float4*)(Bhi + swz64(row, kq * 4)) = hi;
+          *(float4*)(Blo + swz64(row, kq * 4)) = lo;
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&ready[cb]);
@@ -604,13 +671,20 @@ int r2_tc_prepare(Ctx* c) {
 }
 
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
-  const int nst = r2_tc_stages(c->nnu);
+  // the deepest ring that fits, or the caller's (autotuned) depth if smaller
+  const int nmax = r2_tc_stages(c->nnu);
+  const int nst = c->tc_stages >= 2 ? std::min(c->tc_stages, nmax) : nmax;
   tc::Params p{(const float*)c->tiles.p, (const float*)c->Y.p, Ic, (const int2*)c->tc_work.p,
                (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p, c->ncls, c->ntile(), c->nO, c->nnu, c->npairs,
                c->ld(), nst, c->tc_spin > 0 ? c->tc_spin : tc::kSpin};
   const int smem = tc::smem_bytes(c->nnu, nst);
-  PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  tc::r2_tc_kernel<<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
+  if (c->tc_bf16) {
+    PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    tc::r2_tc_kernel<true><<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
+  } else {
+    PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    tc::r2_tc_kernel<false><<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
+  }
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

@@ -5,7 +5,7 @@ Run from the repository root:  python tests/golden/make_golden.py [names...]
 Outputs tests/golden/<name>.npz (forward operator and solution),
 twolevel_full_sol.npz (the solution of the full two-level slab), <name>_nb.npz
 (narrow-band signals along lines of sight), <name>_par.npz (the DELOPAR
-formal solver),
+formal solver), batch_*.npz (oracle solutions of the batched solve's instances),
 <name>_adj.npz (transposed operator and adjoint solve), <name>_pc.npz (the
 preconditioner with 1 and 2 sweeps) and grad_mgii_small.npz
 (derivatives of an emergent-intensity functional by central differences of
@@ -174,6 +174,21 @@ def make_delopar(name):
                         sol=sol, res=hist[-1])
 
 
+# ragged instances of the batched solve (the config-2 physics at reduced sizes):
+# the oracle's solutions to 1e-13
+BATCH = {
+    "batch_mgii7": lambda: inputs.mgii(n_z=7, n_core_each=7, n_wing=6, n_mu_half=2, n_chi=4, seed=401),
+    "batch_mgii9": lambda: inputs.mgii(n_z=9, n_core_each=9, n_wing=8, n_mu_half=2, n_chi=4, seed=402),
+    "batch_hi6": lambda: inputs.hi_lya(n_z=6, n_core=9, n_wing=6, n_mu_half=2, n_chi=4, seed=403),
+}
+
+
+def make_batch(name):
+    P = Problem(BATCH[name]())
+    sol, hist = P.solve(tol=1e-13)
+    np.savez_compressed(os.path.join(HERE, name + ".npz"), sol=sol, res=hist[-1])
+
+
 # the full two-level slab (40 heights x 8 directions x 21 frequencies, FP64):
 # the solution to tol 1e-12 and its emergent Stokes vectors
 def make_full_solve():
@@ -203,7 +218,7 @@ def make_sample(name):
 if __name__ == "__main__":
     names = sys.argv[1:] or (list(CASES) + list(SAMPLES) + [a + "_adj" for a in ADJOINT] + ["grad"]
                              + [a + "_pc" for a in PRECOND] + ["twolevel_full_sol"] + [a + "_nb" for a in NB]
-                             + [a + "_par" for a in PAR])
+                             + [a + "_par" for a in PAR] + list(BATCH))
     for nm in names:
         t0 = time.time()
         if nm in CASES:
@@ -222,6 +237,8 @@ if __name__ == "__main__":
             make_narrowband(nm[:-3])
         elif nm.endswith("_par"):
             make_delopar(nm[:-4])
+        elif nm in BATCH:
+            make_batch(nm)
         else:
             raise SystemExit(f"unknown golden set {nm}")
         print(f"{nm}: {time.time() - t0:.1f} s", flush=True)

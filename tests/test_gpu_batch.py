@@ -3,8 +3,11 @@
 Each instance of a batch must give the solution its own prd_solve gives: in
 FP64 mode to 1e-9 relative (both are converged to 1e-12; they differ only by
 the order of floating-point atomics), in FP32 mode to the refinement's
-accuracy on emergent I.
+accuracy on emergent I; and every instance must match the oracle's solution
+(tests/golden/twolevel.npz, batch_*.npz): FP64 within 1e-8, FP32 emergent I
+within 1e-5 relative and Q/I, U/I, V/I within 1e-4 absolute.
 """
+import os
 import numpy as np
 import pytest
 
@@ -35,6 +38,18 @@ def test_batch_matches_single_solves(prec, tol, agree):
         top = P.mu > 0
         d = np.max(np.abs(a[-1, top, :, 0] - b[-1, top, :, 0]) / np.abs(b[-1, top, :, 0]))
         assert d < agree, (P.shape, d)
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    for P, x, name in zip(Ps, xs, ("twolevel", "batch_mgii7", "batch_mgii9", "batch_hi6")):
+        ref = np.load(os.path.join(gold, name + ".npz"))["sol"]
+        a = x.cpu().numpy().astype(np.float64)
+        if prec == "fp64":
+            assert np.max(np.abs(a - ref)) / np.max(np.abs(ref)) < 1e-8, name
+        else:
+            top = P.mu > 0
+            g, o = a[-1, top], ref[-1, top]
+            assert np.max(np.abs(g[..., 0] - o[..., 0]) / o[..., 0]) < 1e-5, name
+            for s_ in (1, 2, 3):
+                assert np.max(np.abs(g[..., s_] / g[..., 0] - o[..., s_] / o[..., 0])) < 1e-4, name
     for P in Ps:
         P.close()
 

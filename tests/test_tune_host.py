@@ -36,3 +36,28 @@ def test_fastest_decay_is_chosen_and_set():
     rates = {m: r[0] for m, r in res.items()}
     assert best == max(rates, key=rates.get) == 1
     assert S.m == 1 and S.calls == [0, 1, 2, 3]
+
+
+class _Applier:
+    """Apply time per ring depth: 5 units for the deepest (0), depth 3 fastest."""
+    cost = {0: 5.0, 2: 6.0, 3: 4.0, 4: 4.5, 5: 5.0}
+
+    def __init__(self, clock):
+        self.clock, self.st, self.set_calls = clock, None, []
+
+    def set_tile_stages(self, n):
+        self.st = n
+        self.set_calls.append(n)
+
+    def apply_operator(self, x, out=None):
+        self.clock.t += self.cost[self.st] * 1e-3
+        return out
+
+
+def test_fastest_tile_ring_is_chosen_and_set():
+    from paper_2505_20968_gb300.tune import tune_tile_stages
+    clock = _Clock()
+    A = _Applier(clock)
+    best, res = tune_tile_stages(A, clock=clock)
+    assert best == 3 and A.st == 3
+    assert abs(res[3] - 4.0) < 1e-9 and abs(res[2] - 6.0) < 1e-9
