@@ -301,11 +301,10 @@ def main():
     from paper_2505_20968_gb300.binding import PRD
 
     t0 = time.time()
-    P = PRD(cfg, device=local)
+    # bf16x3: a PRD_FP32_BF16X3 context, whose tiles are stored as bf16 hi/lo planes
+    P = PRD(cfg, device=local, precision="fp32_bf16x3" if args.contraction == "bf16x3" else None)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
-    if P.prec == 1:
-        P.set_contraction(args.contraction)
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     x = torch.rand(P.shape, device="cuda", dtype=P.dtype, generator=g)
     x[..., 1:] *= 0.05
@@ -409,30 +408,6 @@ def main():
                                  "frac": delo_bytes / (delo_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                  "l2_resident": delo_bytes < 129e6}
 
-    # the split-BF16 contraction (BF16x3) on the same context: contraction time and
-    # the refined solve at the same tolerance (the FP64 residuals fix the accuracy)
-    modes = {}
-    if cfg.get("precision", "fp32") == "fp32" and not args.no_solve and args.contraction == "tf32x3":
-        P.set_contraction("bf16x3")
-        for _ in range(2):
-            P.apply_operator(x, y)
-        P.set_profiling(True)
-        for _ in range(3):
-            P.apply_operator(x, y)
-        st16 = P.stage_times()
-        P.set_profiling(False)
-        b16_ms = st16["S3_R2_contraction"][0] / max(st16["S3_R2_contraction"][1], 1)
-        torch.cuda.synchronize()
-        t0 = time.time()
-        sol16, info16 = P.solve(tol=args.solve_tol, max_iter=900, restart=200, check=False)
-        torch.cuda.synchronize()
-        modes["bf16x3"] = {"contraction_ms": b16_ms, "useful_tflops": useful / (b16_ms * 1e-3) / 1e12,
-                           "issued_frac_of_bf16_peak": 3.0 * flops / (b16_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
-                           "solve_seconds": time.time() - t0, "solve_applies": info16["iters"],
-                           "solve_true_rel_res": info16["true_rel_res"], "rc": info16["rc"]}
-        P.set_contraction("tf32x3")
-        modes["tf32x3"] = {"contraction_ms": r2_ms, "useful_tflops": achieved_tf}
-
     solve = None
     if not args.no_solve:
         torch.cuda.synchronize()
@@ -441,6 +416,41 @@ def main():
         torch.cuda.synchronize()
         solve = {"seconds": time.time() - t0, "tol": args.solve_tol, "applies": info["iters"],
                  "true_rel_res": info["true_rel_res"], "rc": info["rc"], "setup_seconds": setup_s}
+
+    # the split-BF16 contraction (BF16x3): a PRD_FP32_BF16X3 context on the same
+    # atmosphere (set up after this one is released: both would not fit beside
+    # their FP64 residual copies), its contraction time and its refined solve at
+    # the same tolerance (the FP64 residuals fix the accuracy)
+    modes = {}
+    if cfg.get("precision", "fp32") == "fp32" and not args.no_solve and args.contraction == "tf32x3":
+        modes["tf32x3"] = {"contraction_ms": r2_ms, "useful_tflops": achieved_tf,
+                           "solve_seconds": solve["seconds"], "solve_applies": solve["applies"]}
+        P.close()
+        del P
+        torch.cuda.synchronize()
+        t0 = time.time()
+        Pb = PRD(cfg, device=local, precision="fp32_bf16x3")
+        torch.cuda.synchronize()
+        setup_b = time.time() - t0
+        for _ in range(2):
+            Pb.apply_operator(x, y)
+        Pb.set_profiling(True)
+        for _ in range(3):
+            Pb.apply_operator(x, y)
+        st16 = Pb.stage_times()
+        Pb.set_profiling(False)
+        b16_ms = st16["S3_R2_contraction"][0] / max(st16["S3_R2_contraction"][1], 1)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        sol16, info16 = Pb.solve(tol=args.solve_tol, max_iter=900, restart=200, check=False)
+        torch.cuda.synchronize()
+        modes["bf16x3"] = {"contraction_ms": b16_ms, "useful_tflops": useful / (b16_ms * 1e-3) / 1e12,
+                           "issued_frac_of_bf16_peak": 3.0 * flops / (b16_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                           "hbm_frac": tile_bytes / (b16_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                           "solve_seconds": time.time() - t0, "solve_applies": info16["iters"],
+                           "solve_true_rel_res": info16["true_rel_res"], "rc": info16["rc"],
+                           "setup_seconds": setup_b, "tiles": "bf16 hi/lo planes (PRD_FP32_BF16X3)"}
+        Pb.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

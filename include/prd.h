@@ -57,8 +57,12 @@ enum {
  * tensor cores as 3xTF32 split products (<= 3 * 2^-22 per product).
  * PRD_FP32_BF16X3: the same, with split-BF16 products (hi*hi + hi*lo + lo*hi
  * of bf16 halves, <= 3 * 2^-18 per product, twice the TF32 tensor rate); the
- * context is a PRD_FP32 context (vectors are float) whose contraction is
- * BF16x3, see PRD_OPT_CONTRACTION. */
+ * context is a PRD_FP32 context (vectors are float) whose R_II tiles are
+ * stored split into bf16 hi and lo planes in the operand layout of the MMA
+ * (the same bytes as FP32), so its contraction is BF16x3 on the tensor cores
+ * only: PRD_OPT_CONTRACTION = TF32X3 and PRD_OPT_TENSOR_CORES = 0 return
+ * PRD_E_ARG.  A PRD_FP32 context can also run BF16x3 (PRD_OPT_CONTRACTION),
+ * splitting its FP32 tiles on the fly. */
 enum { PRD_FP64 = 0, PRD_FP32 = 1, PRD_FP32_BF16X3 = 2 };
 enum { PRD_TWO_LEVEL = 0, PRD_TWO_TERM = 1 };
 enum { PRD_GRID_LAMBDA = 0, PRD_GRID_X = 1 };
@@ -258,12 +262,24 @@ int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
  * same with either; the inner iterations count changes.
  * PRD_OPT_TILE_STAGES: depth of the contraction's tile ring, 2..5 (capped at
  * the deepest that fits in shared memory beside the resident I~) or 0 for
- * that deepest ring (default); a schedule parameter for measured tuning. */
+ * that deepest ring (default); a schedule parameter for measured tuning.
+ * PRD_OPT_GRAPH: 1 (default) runs each GMRES iteration of prd_solve,
+ * prd_solve_adjoint and prd_solve_batch as one launch of a CUDA graph (the
+ * Arnoldi step: operator, preconditioner, both Gram-Schmidt passes, the
+ * rotation kernel and the next basis vector, with the step index kept on the
+ * device), captured on the first iteration and kept with the solver's
+ * workspace; 0 launches the same kernels one by one.  Results are identical.
+ * Any option change, prd_set_precond_sweeps and prd_setup drop the captured
+ * graphs; stage profiling (prd_set_profiling) runs the kernels one by one. */
 enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2, PRD_OPT_WAIT_POLLS = 3, PRD_OPT_TEST_ZERO_OPERATOR = 4,
-       PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6, PRD_OPT_CONTRACTION = 7, PRD_OPT_TILE_STAGES = 8 };
+       PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6, PRD_OPT_CONTRACTION = 7, PRD_OPT_TILE_STAGES = 8,
+       PRD_OPT_GRAPH = 9 };
 enum { PRD_CONTRACTION_TF32X3 = 0, PRD_CONTRACTION_BF16X3 = 1 };
 enum { PRD_DELO_LINEAR = 0, PRD_DELOPAR = 1 };
 int prd_set_option(prd_ctx* ctx, int option, int value);
+/* Number of CUDA-graph launches of the GMRES step made by this context so far
+ * (each is one whole Arnoldi iteration); *n receives it.  PRD_E_ARG on NULL. */
+int prd_graph_launches(const prd_ctx* ctx, int64_t* n);
 /* Synchronise the ctx stream and report device-side failures: a CUDA error,
  * or PRD_E_TIMEOUT if a bounded wait inside a kernel expired since the last
  * call (the kernel then returned early and its output is invalid). */

@@ -40,7 +40,7 @@ EXPORTS = ["prd_create", "prd_destroy", "prd_last_error", "prd_set_stream", "prd
            "prd_set_profiling", "prd_stage_times", "prd_apply_sigma_noalloc", "prd_set_option",
            "prd_device_status", "prd_contraction_work",
            "prd_apply_operator_T", "prd_solve_adjoint", "prd_solve_batch",
-           "prd_grad_B", "prd_set_allocator", "prd_narrowband", "prd_set_continuum"]
+           "prd_grad_B", "prd_set_allocator", "prd_narrowband", "prd_set_continuum", "prd_graph_launches"]
 
 
 def lib():
@@ -85,6 +85,7 @@ def lib():
         L.prd_set_profiling.argtypes = [P, I]
         L.prd_set_option.argtypes = [P, I, I]
         L.prd_device_status.argtypes = [P]
+        L.prd_graph_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.prd_stage_times.argtypes = [P, DP, ctypes.POINTER(ctypes.c_int64), I]
         _lib = L
     return _lib
@@ -279,6 +280,16 @@ class PRD:
 
     def device_status(self):
         self._check(lib().prd_device_status(self.h))
+
+    def set_graph(self, on):
+        """Run each GMRES iteration as one CUDA-graph launch (default) or not."""
+        self._check(lib().prd_set_option(self.h, 9, 1 if on else 0))
+
+    def graph_launches(self):
+        """CUDA-graph launches of the GMRES step made by this context so far."""
+        n = ctypes.c_int64()
+        self._check(lib().prd_graph_launches(self.h, ctypes.byref(n)))
+        return n.value
 
     def set_precond_sweeps(self, m):
         self._check(lib().prd_set_precond_sweeps(self.h, m))

@@ -67,7 +67,10 @@ static void free_all(Ctx* c) {
                   &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M, &c->pc_lii, &c->pc_eta,
                   &c->pc_delo, &c->pc_s1, &c->pc_s2, &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->gm_w, &c->gm_r, &c->gm_t, &c->gm_dots,
                   &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64, &c->r3out64,
-                  &c->r3prof64, &c->r3ab64, &c->par, &c->eta_line, &c->cont_pw, &c->cont_sig};
+                  &c->r3prof64, &c->r3ab64, &c->par, &c->eta_line, &c->cont_pw, &c->cont_sig,
+                  &c->gk_V, &c->gk_r, &c->gk_w, &c->gk_cur, &c->gk_S, &c->kt64, &c->epsth64};
+  invalidate_graphs(c);
+  c->gk_m = 0;
   c->has64 = false;
   c->tc_ready = false;
   for (DBuf* b : bufs) dfree(*b);
@@ -111,6 +114,8 @@ void stage_collect(Ctx* c) {
 Ctx::~Ctx() {
   stage_collect(this);
   free_all(this);
+  if (gk_host) cudaFreeHost(gk_host);
+  if (gk_cap) cudaStreamDestroy(gk_cap);
 }
 
 int launch_precond_setup(Ctx* c);
@@ -192,6 +197,7 @@ int prd_create(prd_ctx** out, int device, int precision) {
   h->c.esz = precision == PRD_FP64 ? 8 : 4;
   h->c.use_tc = precision == PRD_FP32 ? 1 : 0;   // tcgen05 contraction by default in FP32
   h->c.tc_bf16 = bf16x3 ? 1 : 0;
+  h->c.split_tiles = bf16x3;                    // tiles stored as the bf16 hi/lo planes
   if (cudaDeviceGetAttribute(&h->c.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete h;
     return PRD_E_CUDA;
@@ -358,7 +364,8 @@ int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
   if (!ctx || !bytes) return PRD_E_ARG;
   const Ctx* c = &ctx->c;
   const prd::DBuf* bufs[] = {&c->tiles, &c->Y, &c->r3w, &c->r3in, &c->r3out, &c->r3prof, &c->r3J, &c->r3ab,
-                             &c->kt, &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk, &c->tin, &c->tbk,
+                             &c->kt, &c->kt64, &c->epsth64, &c->epsth, &c->f, &c->sp, &c->ugrid, &c->iin, &c->ibk,
+                             &c->tin, &c->tbk,
                              &c->cls_dev, &c->scratch1, &c->scratch2, &c->scratch3, &c->pc_phi, &c->pc_M,
                              &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t, &c->dmu, &c->pc_s1, &c->pc_s2,
                              &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64,
@@ -429,7 +436,14 @@ int prd_apply_preconditioner(prd_ctx* ctx, const void* y_dev, void* x_dev) {
 int prd_set_precond_sweeps(prd_ctx* ctx, int m_in) {
   CTX_OR_ARG(ctx);
   if (m_in < 0 || m_in > 64) return fail(c, PRD_E_ARG, "m_in must be in [0, 64]");
+  prd::invalidate_graphs(c);
   c->m_in = m_in;
+  return PRD_OK;
+}
+
+int prd_graph_launches(const prd_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return PRD_E_ARG;
+  *n = ctx->c.gk_launches;
   return PRD_OK;
 }
 
@@ -481,21 +495,38 @@ int prd_solve_batch(prd_ctx* const* ctxs, int n, double tol, int max_iter, int r
   }
   std::vector<int> rc(n, PRD_OK), it(n, 0);
   std::vector<double> res(n, 0.0);
+  // lockstep rounds (one graph launch runs every waiting instance's Arnoldi
+  // step) when all instances sit on one device; else each replays its own graph
+  bool one_device = true;
+  for (int i = 1; i < n; ++i) one_device = one_device && ctxs[i]->c.device == ctxs[0]->c.device;
+  prd::BatchRound* round = nullptr;
+  if (one_device && n > 1) {
+    cudaSetDevice(ctxs[0]->c.device);
+    round = prd::batch_round_create(n);
+  }
+  for (int i = 0; i < n; ++i) ctxs[i]->c.batch = round;
   std::vector<std::thread> th;
   th.reserve(n);
   for (int i = 0; i < n; ++i)
     th.emplace_back([&, i]() {
       Ctx* c = &ctxs[i]->c;
-      if (!c->ready) { rc[i] = fail(c, PRD_E_STATE, "call prd_setup first"); return; }
-      if (cudaSetDevice(c->device) != cudaSuccess) { rc[i] = fail(c, PRD_E_CUDA, "cudaSetDevice failed"); return; }
+      auto leave = [&]() {
+        if (c->batch) prd::batch_round_leave(c->batch);
+        c->batch = nullptr;
+      };
+      if (!c->ready) { rc[i] = fail(c, PRD_E_STATE, "call prd_setup first"); leave(); return; }
+      if (cudaSetDevice(c->device) != cudaSuccess) { rc[i] = fail(c, PRD_E_CUDA, "cudaSetDevice failed"); leave(); return; }
       try {
         rc[i] = prd::solve(c, tol, max_iter, restart, nullptr, x_devs[i], &it[i], &res[i], nullptr);
+        leave();
         if (!rc[i] && c->tc_err.p) rc[i] = prd::r2_tc_check_error(c);
       } catch (const std::exception& e) {
+        leave();
         rc[i] = fail(c, PRD_E_NOMEM, std::string("host exception in solve: ") + e.what());
       }
     });
   for (auto& t : th) t.join();
+  prd::batch_round_destroy(round);
   int first = PRD_OK;
   for (int i = 0; i < n; ++i) {
     if (iters) iters[i] = it[i];
@@ -576,8 +607,15 @@ int prd_narrowband(prd_ctx* ctx, const void* x_dev, int nlos, const double* mu, 
 
 int prd_set_option(prd_ctx* ctx, int option, int value) {
   CTX_OR_ARG(ctx);
+  prd::invalidate_graphs(c);   // the captured solver step bakes in every option
+  if (option == PRD_OPT_GRAPH) {
+    c->use_graph = value ? 1 : 0;
+    return PRD_OK;
+  }
   if (option == PRD_OPT_TENSOR_CORES) {
     if (value && c->prec != PRD_FP32) return fail(c, PRD_E_ARG, "tensor-core contraction needs PRD_FP32");
+    if (!value && c->split_tiles)
+      return fail(c, PRD_E_ARG, "PRD_FP32_BF16X3 stores its tiles as bf16 planes for the tensor cores only");
     c->use_tc = value ? 1 : 0;
     return PRD_OK;
   }
@@ -605,6 +643,8 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
     if (value != PRD_CONTRACTION_TF32X3 && value != PRD_CONTRACTION_BF16X3)
       return fail(c, PRD_E_ARG, "unknown contraction product");
     if (c->prec != PRD_FP32) return fail(c, PRD_E_ARG, "the split products are for PRD_FP32 contexts");
+    if (c->split_tiles && value != PRD_CONTRACTION_BF16X3)
+      return fail(c, PRD_E_ARG, "PRD_FP32_BF16X3 stores its tiles as bf16 planes: BF16x3 products only");
     c->tc_bf16 = value == PRD_CONTRACTION_BF16X3 ? 1 : 0;
     return PRD_OK;
   }

@@ -371,6 +371,9 @@ int build_device_tables(Ctx* c) {
       (rc = upload(c, c->par, par.data(), par.size() * 8)) ||
       (rc = upload(c, c->eta_line, etal.data(), npt * 8)))
     return rc;
+  if (c->prec == PRD_FP32 &&
+      ((rc = upload(c, c->kt64, kt.data(), kt.size() * 8)) || (rc = upload(c, c->epsth64, epsth.data(), epsth.size() * 8))))
+    return rc;
   if (c->has_cont()) {
     std::vector<double> pw((size_t)nO * nO * 16);
     for (int o = 0; o < nO; ++o)

@@ -787,8 +787,8 @@ int compute_normalisation(Ctx* c) {
                   : sigma_T<float, double>(c, (const double*)xin.p, (double*)num.p, false, (double*)eb.p, (double*)Mb.p,
                                            (double*)Ic.p);
     if (!rc)
-      normalise_kernel<float, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
-          (const double*)num.p, (const float*)c->kt.p, (const double*)c->eta_line.p, (const double*)fac.p,
+      normalise_kernel<double, double><<<ceil_div(npt, 256), 256, 0, c->stream>>>(
+          (const double*)num.p, (const double*)c->kt64.p, (const double*)c->eta_line.p, (const double*)fac.p,
           (double*)c->f.p, nz, nO, N);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -815,27 +815,18 @@ int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws /* 4 x nve
   int rc = c->has64 ? sigma_T<double, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv, nullptr, true)
                      : sigma_T<float, double>(c, x, eps, true, ws + nv, ws + 2 * nv, ws + 3 * nv);
   if (rc) return rc;
-  delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
-      eps, (const float*)c->kt.p, (const double*)c->par_active(), (const double*)c->dmu.p, x, y, c->nz, c->nO, c->nnu,
-      0, c->WT[0]);
+  delo_kernel<double, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
+      eps, (const double*)c->kt64.p, (const double*)c->par_active(), (const double*)c->dmu.p, x, y, c->nz, c->nO,
+      c->nnu, 0, c->WT[0]);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }
 
 int rhs_acc(Ctx* c, double* b) {
-  const size_t nv = nvec(c);
-  DBuf e64;
-  int rc = dalloc(c, e64, nv * 8);
-  if (rc) return rc;
-  std::vector<float> h(nv);
-  cudaMemcpy(h.data(), c->epsth.p, nv * 4, cudaMemcpyDeviceToHost);
-  std::vector<double> hd(h.begin(), h.end());
-  cudaMemcpy(e64.p, hd.data(), nv * 8, cudaMemcpyHostToDevice);
-  delo_kernel<float, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
-      (const double*)e64.p, (const float*)c->kt.p, (const double*)c->par_active(), (const double*)c->dmu.p, nullptr, b,
-      c->nz, c->nO, c->nnu, 1, c->WT[0]);
+  delo_kernel<double, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
+      (const double*)c->epsth64.p, (const double*)c->kt64.p, (const double*)c->par_active(), (const double*)c->dmu.p,
+      nullptr, b, c->nz, c->nO, c->nnu, 1, c->WT[0]);
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  dfree(e64);
   if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("rhs_acc: ") + cudaGetErrorString(e));
   return PRD_OK;
 }

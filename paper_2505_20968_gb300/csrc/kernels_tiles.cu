@@ -17,6 +17,7 @@
 // (v = 0), accumulate the moments in FP64, then the warp folds P_M Q and
 // writes the row (Re in [0, N), Im in [N, 2N)).
 #include <cstdio>
+#include <cuda_bf16.h>
 #include "prd_internal.h"
 #include "device_common.cuh"
 
@@ -314,9 +315,16 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) r3_kernel(R3Params p, T* o
 //   tiles[c][ngrp + t][.] = G_t - mean of its group
 // so that the large dispersion parts that cancel between Zeeman components
 // of one J level are summed once, in FP64, before rounding to the storage type.
+// the FP32 value v of a tile entry stored as bf16 planes hi = rn(v), lo = rn(v - hi)
+__device__ __forceinline__ void store_split(__nv_bfloat16* t, int n, int k, int N, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  t[tile_off_split(n, k, N, false)] = hi;
+  t[tile_off_split(n, k, N, true)] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 template <typename T>
 __global__ void group_split_kernel(const double* __restrict__ src, T* __restrict__ dst, const int* __restrict__ grp,
-                                   int ncls, int ntrip, int ngrp, int N, int ld, int tiled) {
+                                   int ncls, int ntrip, int ngrp, int N, int ld, int tiled, int split) {
   const int rowlen = 2 * N * N;                 // one FP64 scratch tile: N rows of 2N
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (c, n*2N + k)
   if (idx >= (long long)ncls * rowlen) return;
@@ -332,10 +340,18 @@ __global__ void group_split_kernel(const double* __restrict__ src, T* __restrict
     mean[g] += src[((size_t)c * ntrip + t) * rowlen + e];
     cnt[g] += 1;
   }
-  for (int g = 0; g < ngrp; ++g) {
-    mean[g] = cnt[g] ? mean[g] / cnt[g] : 0.0;
-    dst[((size_t)c * (ngrp + ntrip) + g) * tsz + o] = (T)mean[g];
+  for (int g = 0; g < ngrp; ++g) mean[g] = cnt[g] ? mean[g] / cnt[g] : 0.0;
+  if (split) {
+    // split layout (BF16x3 contexts): T is float, each tile's bytes hold the two bf16 planes
+    for (int g = 0; g < ngrp; ++g)
+      store_split(reinterpret_cast<__nv_bfloat16*>(dst + ((size_t)c * (ngrp + ntrip) + g) * tsz), n, kk, N,
+                  (float)mean[g]);
+    for (int t = 0; t < ntrip; ++t)
+      store_split(reinterpret_cast<__nv_bfloat16*>(dst + ((size_t)c * (ngrp + ntrip) + ngrp + t) * tsz), n, kk, N,
+                  (float)(src[((size_t)c * ntrip + t) * rowlen + e] - mean[grp[t]]));
+    return;
   }
+  for (int g = 0; g < ngrp; ++g) dst[((size_t)c * (ngrp + ntrip) + g) * tsz + o] = (T)mean[g];
   for (int t = 0; t < ntrip; ++t)
     dst[((size_t)c * (ngrp + ntrip) + ngrp + t) * tsz + o] =
         (T)(src[((size_t)c * ntrip + t) * rowlen + e] - mean[grp[t]]);
@@ -413,15 +429,15 @@ int launch_tiles(Ctx* c) {
     if (c->prec == PRD_FP64)
       group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)c->tiles.p + iz * ztile,
                                                             (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
-                                                            c->tiled());
+                                                            c->tiled(), 0);
     else {
       group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)c->tiles.p + iz * ztile,
                                                            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
-                                                           c->tiled());
+                                                           c->tiled(), c->split_tiles ? 1 : 0);
       if (c->has64)
         group_split_kernel<double><<<sb, 256, 0, c->stream>>>(
             (const double*)scr.p, (double*)c->tiles64.p + (size_t)iz * c->ncls * c->ntile() * N * c->ld64(),
-            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld64(), 0);
+            (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld64(), 0, 0);
     }
     if (cudaPeekAtLastError() != cudaSuccess) err = 1;
   }
@@ -481,10 +497,10 @@ int gen_tiles_z(Ctx* c, int iz, const std::vector<double>& thetas, void* outT) {
   const int sb = ceil_div((long long)ncl * rowlen, 256);
   if (c->prec == PRD_FP64)
     group_split_kernel<double><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (double*)outT, (const int*)dgrp.p, ncl,
-                                                          c->ntrip, c->ngrp, N, c->ld(), c->tiled());
+                                                          c->ntrip, c->ngrp, N, c->ld(), c->tiled(), 0);
   else
     group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)outT, (const int*)dgrp.p, ncl,
-                                                         c->ntrip, c->ngrp, N, c->ld(), c->tiled());
+                                                         c->ntrip, c->ngrp, N, c->ld(), c->tiled(), 0);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cleanup();
   if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("line-of-sight tiles: ") + cudaGetErrorString(e));

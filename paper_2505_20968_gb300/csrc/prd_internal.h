@@ -118,6 +118,10 @@ struct Ctx {
   DBuf r3J;          // [z][uv] complex scratch
   DBuf r3ab;         // [z][uv] complex (beta-alpha) * k * c3
   DBuf kt;           // [z][o][n][10] K'/eta1 (6), 1/eta1, exp(-d), alpha, beta
+  // FP32 mode: FP64 copies of kt and epsth for the refinement's FP64 residuals,
+  // the right-hand side and f (the formal solution of the residual operator
+  // then carries no FP32 table rounding)
+  DBuf kt64, epsth64;
   DBuf par;          // [z][o][n][3] DELOPAR source weights psi_M, psi_O, psi_P of the step arriving there (double)
   DBuf eta_line;     // [z][o][n] the line's share eta_line/eta_total of eta_I (double): f normalises the line only
   DBuf cont_pw;      // [o][o'][4][4] w_o' P(o, o') dipole phase matrix of continuum scattering (double)
@@ -145,6 +149,18 @@ struct Ctx {
   // GMRES
   std::vector<DBuf> krylov;
   DBuf gm_w, gm_r, gm_t, gm_dots;
+  // GMRES workspace kept across solves (basis V[m+1], residual r, operator
+  // output w, current basis vector, device state), and the Arnoldi step
+  // captured once as a CUDA graph over it: [0] A, [1] A^T
+  DBuf gk_V, gk_r, gk_w, gk_cur, gk_S;
+  int gk_m = 0;
+  double* gk_host = nullptr;               // pinned copy of the step's scalars
+  cudaGraphExec_t gk_exec[2] = {nullptr, nullptr};
+  cudaGraph_t gk_graph[2] = {nullptr, nullptr};   // the captured steps (children of a batch round)
+  int use_graph = 1;                       // PRD_OPT_GRAPH
+  cudaStream_t gk_cap = nullptr;           // private stream the step is captured on
+  struct BatchRound* batch = nullptr;      // set while prd_solve_batch runs this context in lockstep
+  long long gk_launches = 0;               // graph launches (prd_graph_launches)
   std::vector<DBuf> owned;
   prd_alloc_fn alloc_fn = nullptr;   // caller's allocator (prd_set_allocator), NULL: cudaMalloc
   prd_free_fn free_fn = nullptr;
@@ -157,6 +173,7 @@ struct Ctx {
   int use_tc = 0;
   long long tc_spin = 0;   // poll limit of the contraction's pipeline waits (0: the default)
   int tc_bf16 = 0;         // contraction products: 0 3xTF32, 1 split-BF16 (BF16x3)
+  bool split_tiles = false;   // PRD_FP32_BF16X3: R_II tiles stored as bf16 hi/lo planes (tile_off_split)
   int tc_stages = 0;       // tile ring depth of the contraction (0: the deepest that fits)
   // stage timing (prd_set_profiling): events on the ctx stream around each stage
   bool prof = false;
@@ -243,6 +260,15 @@ int upload_faddeeva_coeffs(Ctx* c);
 size_t nvec(const Ctx* c);   // 4*nz*nO*nnu
 int r2_tc_prepare(Ctx* c);
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb);
+// drop the captured solver graphs (options, tables or workspace changed)
+void invalidate_graphs(Ctx* c);
+// Lockstep rounds of a batched solve (solver.cu): every context of the batch
+// that is inside an Arnoldi step waits until all contexts still solving have
+// either reached their step or left; then one launch of a graph whose
+// children are their captured steps runs all of them.
+BatchRound* batch_round_create(int n);
+void batch_round_leave(BatchRound* b);
+void batch_round_destroy(BatchRound* b);
 int r2_tc_check_error(Ctx* c);
 
 // Stage ids for prd_stage_times.
@@ -262,6 +288,20 @@ __host__ __device__ inline size_t tile_off(int n, int k, int N, int ld, bool til
   if (!tiled) return (size_t)n * ld + k;
   const int kc = k >> 4, kl = k & 15;
   return (size_t)kc * N * 16 + (size_t)n * 16 + (size_t)((((kl >> 2) ^ ((n >> 1) & 3)) << 2) | (kl & 3));
+}
+
+// Offset, in bf16 units, of the hi (lo = false) or lo plane entry of tile
+// element (row n, column k) in the split layout of a BF16x3 context: the tile
+// is cut into K chunks of 16 columns like the FP32 tensor-core layout, and
+// chunk kc (N x 64 bytes, the same bytes as FP32) holds two planes of N rows
+// x 32 bytes, hi = rn_bf16(v) then lo = rn_bf16(v - hi) for v the FP32 value;
+// each row's two 16-byte halves are exchanged in rows whose bit 2 is set (the
+// 32-byte shared-memory swizzle), so one bulk copy per plane lands a K step
+// in the operand layout of a kind::f16 MMA.
+__host__ __device__ inline size_t tile_off_split(int n, int k, int N, bool lo) {
+  const int kc = k >> 4, kl = k & 15, g = kl >> 2;
+  const size_t base = (size_t)kc * N * 32 + (lo ? (size_t)N * 16 : 0);
+  return base + (size_t)n * 16 + (size_t)(((g >> 1) ^ ((n >> 2) & 1)) * 8 + (g & 1) * 4 + (kl & 3));
 }
 
 }  // namespace prd

@@ -61,13 +61,17 @@ constexpr int kAuxBytes = 1024;               // work-item tables, barriers, TME
 constexpr int kSmemMax = 227 * 1024;          // shared memory per CTA
 static_assert(kNCPMax == 128 && (kGenWarps == 8 || kGenWarps == 16), "B items: 16 (32-row group, 4-k chunk) over the builder warps");
 // Shared memory of one CTA for N tile rows with `st` tile stages: the tile ring
-// (NM x 64 bytes per K step), the builder ring (A_lo of NM rows, B_hi, B_lo),
-// two Y buffers, the resident I~ of kISlots incident directions (stride N + 1
-// float4, odd modulo 8 so that different slots fall in different bank groups)
-// and the auxiliary tables, plus 1 KB to align the base.
-__host__ __device__ constexpr int smem_bytes(int N, int st) {
-  return st * ((N + 15) / 16 * 16) * 64 + kCBufs * (((N + 15) / 16 * 16) * 64 + 2 * kBBytes) + 2 * kYBytes +
-         kISlots * (N + 1) * 16 + kAuxBytes + 1024;
+// (NM x 64 bytes per K step), the builder ring (A_lo of NM rows unless the
+// tiles come split, B_hi, B_lo), two Y buffers, the resident I~ of kISlots
+// incident directions (stride N + 1 float4, odd modulo 8 so that different
+// slots fall in different bank groups) and the auxiliary tables, plus 1 KB to
+// align the base.
+__host__ __device__ constexpr int cbuf_bytes(int N, bool split) {
+  return (split ? 0 : ((N + 15) / 16 * 16) * 64) + 2 * kBBytes;
+}
+__host__ __device__ constexpr int smem_bytes(int N, int st, bool split) {
+  return st * ((N + 15) / 16 * 16) * 64 + kCBufs * cbuf_bytes(N, split) + 2 * kYBytes + kISlots * (N + 1) * 16 +
+         kAuxBytes + 1024;
 }
 constexpr long long kSpin = 1ll << 24;        // bounded waits (default limit of the pipeline waits; drains)
 
@@ -222,11 +226,14 @@ __device__ __forceinline__ bool gen_all(bool v) {
   return r != 0;
 }
 
-// kBF16: the split-BF16 products (BF16x3) instead of 3xTF32; the builders then
-// split the tile step into bf16 hi and lo planes too, and the operands are
-// K-major with 32-byte rows (16 bf16 of K)
-template <bool kBF16>
+// kBF16: the split-BF16 products (BF16x3) instead of 3xTF32, operands K-major
+// with 32-byte rows (16 bf16 of K).  kSplit (with kBF16): the tiles are stored
+// split (tile_off_split), so the producer's two bulk copies per step land the
+// hi and lo planes in the operand layout and the builders never touch the
+// tile; without it the builders split the FP32 tile step into the planes.
+template <bool kBF16, bool kSplit>
 __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
+  static_assert(kBF16 || !kSplit, "split tiles are bf16 planes");
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned base, derived by offset so that the compiler keeps the
   // shared address space on every pointer below (plain LDS/STS, no generic access)
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int nst = p.nst;
   const int IS = N + 1;                          // float4 stride of a resident I~ slot
   unsigned char* cbuf = sm + nst * SA;                             // [buffer] A_lo, B_hi, B_lo
-  const int CB = SA + 2 * kBBytes;
+  const int CB = cbuf_bytes(N, kSplit);
   float* Ys = (float*)(cbuf + kCBufs * CB);                        // [buffer][pair][16][2]
   float4* Ir = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [slot][k < N], resident
   int* eptr = (int*)((unsigned char*)Ir + (size_t)kISlots * IS * 16);   // local pair range of each output
@@ -331,7 +338,13 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         // that the epilogue never reads
         const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
         mbar_expect_tx(&full[s], abytes);
-        bulk_load(sm + s * SA, src, abytes, &full[s], pol_t);
+        if constexpr (kSplit) {
+          // hi plane (N x 32 bytes) at the stage, lo plane at its second half
+          bulk_load(sm + s * SA, src, abytes / 2, &full[s], pol_t);
+          bulk_load(sm + s * SA + SA / 2, src + (size_t)N * kKC / 2, abytes / 2, &full[s], pol_t);
+        } else {
+          bulk_load(sm + s * SA, src, abytes, &full[s], pol_t);
+        }
       }
       if (*abort_flag) {
         // drain copies that were issued and may not have been consumed
@@ -352,17 +365,20 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       for (int it = 0; it < iters; ++it) {
         const int s = it % nst, cb = it % kCBufs;
         if (!mbar_wait(&ready[cb], (it / kCBufs) & 1, abort_flag, p.spin)) break;
+        // split tiles: the builders do not wait for the tile step, the MMAs do
+        if (kSplit && !mbar_wait(&full[s], (it / nst) & 1, abort_flag, p.spin)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         unsigned char* A = sm + s * SA;
         unsigned char* Alo = cbuf + cb * CB;
-        unsigned char* Bhi = Alo + SA;
+        unsigned char* Bhi = Alo + (kSplit ? 0 : SA);
         unsigned char* Blo = Bhi + kBBytes;
         if constexpr (kBF16) {
-          // A_hi and A_lo planes share the A_lo buffer (NM x 32 bytes each)
+          // A_hi and A_lo planes (NM x 32 bytes each): the stage itself for split
+          // tiles, else the A_lo buffer the builders filled
           const uint32_t idesc16 =
               (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NM >> 3) << 17) | ((128u >> 4) << 24);
-          unsigned char* Ah = Alo;
-          unsigned char* Al = Alo + SA / 2;
+          unsigned char* Ah = kSplit ? A : Alo;
+          unsigned char* Al = Ah + SA / 2;
           mma_bf16(tmem, sdesc32(Bhi), sdesc32(Ah), idesc16, it > 0 ? 1u : 0u);
           mma_bf16(tmem, sdesc32(Blo), sdesc32(Ah), idesc16, 1u);
           mma_bf16(tmem, sdesc32(Bhi), sdesc32(Al), idesc16, 1u);
@@ -440,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     for (int it = 0; it < iters; ++it) {
       const int s = it % nst, cb = it % kCBufs;
       const int ti = it / KCH, kc = it - ti * KCH;
-      bool got = !aborted && mbar_wait(&full[s], (it / nst) & 1, abort_flag, p.spin);
+      bool got = !aborted && (kSplit || mbar_wait(&full[s], (it / nst) & 1, abort_flag, p.spin));
       if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag, p.spin);
       float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
       if (kc == 0) {
@@ -475,9 +491,9 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       }
       unsigned char* A = sm + s * SA;
       unsigned char* Alo = cbuf + cb * CB;
-      unsigned char* Bhi = Alo + SA;
+      unsigned char* Bhi = Alo + (kSplit ? 0 : SA);
       unsigned char* Blo = Bhi + kBBytes;
-      {
+      if constexpr (!kSplit) {
         const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
         const int nq4 = N * (kKC / 4);             // <= kAR kGen
@@ -635,16 +651,16 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
 }  // namespace tc
 
 // Tile stages for N rows: the most (<= kStagesMax) whose shared memory fits.
-static int r2_tc_stages(int N) {
+static int r2_tc_stages(int N, bool split) {
   for (int st = tc::kStagesMax; st >= 2; --st)
-    if (tc::smem_bytes(N, st) <= tc::kSmemMax) return st;
+    if (tc::smem_bytes(N, st, split) <= tc::kSmemMax) return st;
   return 0;
 }
 
 // Work list and error flag of the tensor-core contraction.
 int r2_tc_prepare(Ctx* c) {
   if (c->prec != PRD_FP32) return PRD_OK;
-  if (!c->tiled() || r2_tc_stages(c->nnu) < 2)
+  if (!c->tiled() || r2_tc_stages(c->nnu, false) < 2)
     return fail(c, PRD_E_ARG, "tensor-core contraction needs FP32 tiles and N small enough for two tile stages "
                               "beside the resident I~ (N <= 232)");
   if (!c->tc_err.p) {
@@ -672,19 +688,22 @@ int r2_tc_prepare(Ctx* c) {
 
 int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
   // the deepest ring that fits, or the caller's (autotuned) depth if smaller
-  const int nmax = r2_tc_stages(c->nnu);
+  const int nmax = r2_tc_stages(c->nnu, c->split_tiles);
   const int nst = c->tc_stages >= 2 ? std::min(c->tc_stages, nmax) : nmax;
   tc::Params p{(const float*)c->tiles.p, (const float*)c->Y.p, Ic, (const int2*)c->tc_work.p,
                (const int*)c->cls_dev.p, eb, (int*)c->tc_err.p, c->ncls, c->ntile(), c->nO, c->nnu, c->npairs,
                c->ld(), nst, c->tc_spin > 0 ? c->tc_spin : tc::kSpin};
-  const int smem = tc::smem_bytes(c->nnu, nst);
-  if (c->tc_bf16) {
-    PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    tc::r2_tc_kernel<true><<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
-  } else {
-    PRD_CUDA_TRY(c, cudaFuncSetAttribute(tc::r2_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    tc::r2_tc_kernel<false><<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
-  }
+  const int smem = tc::smem_bytes(c->nnu, nst, c->split_tiles);
+  auto go = [&](auto kern) -> int {
+    PRD_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    kern<<<dim3(c->tc_nwork, c->nz), tc::kThreads, smem, c->stream>>>(p);
+    return PRD_OK;
+  };
+  int rc;
+  if (c->split_tiles) rc = go(tc::r2_tc_kernel<true, true>);
+  else if (c->tc_bf16) rc = go(tc::r2_tc_kernel<true, false>);
+  else rc = go(tc::r2_tc_kernel<false, false>);
+  if (rc) return rc;
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

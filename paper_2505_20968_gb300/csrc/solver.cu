@@ -6,10 +6,19 @@
 // Hessenberg column, forms the next rotation and the residual estimate (FP64).
 // The host reads back that estimate once per iteration (to stop), and the
 // least-squares back substitution runs on the device at the end of a cycle.
+// The step index j lives in device memory too, so one Arnoldi step (operator,
+// preconditioner, both Gram-Schmidt passes, the rotation kernel, the scaled
+// next basis vector and the copy of the scalars to pinned host memory) is the
+// same launch sequence for every j: it is captured once per context as a CUDA
+// graph and replayed, one graph launch per iteration.
 // The stopping test is the unpreconditioned relative residual ||b - A x|| /
 // ||b|| of Sect. 5.1, recomputed in FP64 before returning.
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 #include "prd_internal.h"
 #include "device_common.cuh"
@@ -32,25 +41,6 @@ __global__ void multidot_kernel(const T* __restrict__ V, size_t ld, const T* __r
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(&dots[k], red[0]);
-}
-
-// w -= sum_k h[k] V[k]   (h in device memory)
-template <typename T>
-__global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ld, const double* __restrict__ h, int nv, T* w,
-                                 size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    double s = (double)w[i];
-    for (int k = 0; k < nv; ++k) s -= h[k] * (double)V[(size_t)k * ld + i];
-    w[i] = (T)s;
-  }
-}
-
-// b = a * (*s)   (scale factor in device memory)
-template <typename T>
-__global__ void scale_copy_kernel(const T* __restrict__ a, const double* __restrict__ s, T* __restrict__ b, size_t n) {
-  const double f = *s;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    b[i] = (T)((double)a[i] * f);
 }
 
 // x += sum_k y[k] V[k]   (y in device memory)
@@ -88,10 +78,58 @@ struct GState {
   __host__ __device__ size_t sc() const { return h2() + m + 1; }
   __host__ __device__ size_t total() const { return sc() + 8; }
 };
-enum { kSS = 0, kInv = 1, kEst = 2, kNorm = 3, kBeta0 = 4 };
+enum { kSS = 0, kInv = 1, kEst = 2, kNorm = 3, kBeta0 = 4, kJ = 5, kTr = 6 };
+
+// dots[k] = sum_i V[k][i] * w[i] for k <= j, j = st[kJ] read on the device
+// (dots zeroed by the caller); blocks stride over k so the grid is fixed
+template <typename T>
+__global__ void multidot_j_kernel(const T* __restrict__ V, size_t ld, const T* __restrict__ w, size_t n,
+                                  const double* __restrict__ sc, double* dots) {
+  const int nv = (int)sc[kJ] + 1;
+  __shared__ double red[256];
+  for (int k = blockIdx.y; k < nv; k += gridDim.y) {
+    const T* v = V + (size_t)k * ld;
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      s += (double)v[i] * (double)w[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+      if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&dots[k], red[0]);
+    __syncthreads();
+  }
+}
+
+// w -= sum_{k <= j} h[k] V[k],  j = st[kJ]
+template <typename T>
+__global__ void multiaxpy_j_kernel(const T* __restrict__ V, size_t ld, const double* __restrict__ h,
+                                   const double* __restrict__ sc, T* w, size_t n) {
+  const int nv = (int)sc[kJ] + 1;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double s = (double)w[i];
+    for (int k = 0; k < nv; ++k) s -= h[k] * (double)V[(size_t)k * ld + i];
+    w[i] = (T)s;
+  }
+}
+
+// V[j] = cur = a * st[kInv],  j = st[kJ] (the basis vector the next step applies A to)
+template <typename T>
+__global__ void scale_j_kernel(const T* __restrict__ a, const double* __restrict__ sc, T* __restrict__ V, size_t ld,
+                               T* __restrict__ cur, size_t n) {
+  const double f = sc[kInv];
+  T* dst = V + (size_t)(int)sc[kJ] * ld;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T v = (T)((double)a[i] * f);
+    dst[i] = v;
+    cur[i] = v;
+  }
+}
 
 // start of a cycle: beta = sqrt(ss); g = beta e_1; 1/beta for the first basis vector
-__global__ void gm_cycle_start_kernel(double* st, GState L) {
+__global__ void gm_cycle_start_kernel(double* st, GState L, double tr) {
   double* sc = st + L.sc();
   const double beta = sqrt(sc[kSS]);
   double* g = st + L.g();
@@ -100,13 +138,17 @@ __global__ void gm_cycle_start_kernel(double* st, GState L) {
   sc[kBeta0] = beta;
   sc[kNorm] = beta;
   sc[kInv] = beta > 0.0 ? 1.0 / beta : 0.0;
+  sc[kJ] = 0.0;
+  sc[kTr] = tr;
 }
 
 // Arnoldi step j: Hessenberg column from the two Gram-Schmidt passes and the
 // norm of the orthogonalised vector, earlier rotations applied, the new
 // rotation formed and applied to g; estimate tr |g[j+1]| / beta0.
-__global__ void gm_arnoldi_kernel(double* st, GState L, int j, double tr) {
+__global__ void gm_arnoldi_kernel(double* st, GState L) {
   const int m = L.m;
+  const int j = (int)st[L.sc() + kJ];
+  const double tr = st[L.sc() + kTr];
   double* H = st + L.H();
   double* cs = st + L.cs();
   double* sn = st + L.sn();
@@ -133,6 +175,7 @@ __global__ void gm_arnoldi_kernel(double* st, GState L, int j, double tr) {
   sc[kNorm] = hn;
   sc[kInv] = hn > 0.0 ? 1.0 / hn : 0.0;
   sc[kEst] = tr * fabs(g[j + 1]) / sc[kBeta0];
+  sc[kJ] = (double)(j + 1);
 }
 
 // y = H(0:j, 0:j)^-1 g(0:j)  (upper triangular after the rotations)
@@ -169,14 +212,6 @@ struct Vops {
     PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
-  int axpy_many(const void* V, size_t ld, const double* h, int nv, void* w) {
-    if (c->prec == PRD_FP64)
-      multiaxpy_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, h, nv, (double*)w, n);
-    else
-      multiaxpy_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)V, ld, h, nv, (float*)w, n);
-    PRD_CUDA_TRY(c, cudaPeekAtLastError());
-    return PRD_OK;
-  }
   int update(const void* V, size_t ld, const double* y, int nv, void* x) {
     if (c->prec == PRD_FP64)
       update_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, y, nv, (double*)x, n);
@@ -185,17 +220,36 @@ struct Vops {
     PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
-  int scale(const void* a, const double* s, void* b) {
-    if (c->prec == PRD_FP64)
-      scale_copy_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)a, s, (double*)b, n);
-    else
-      scale_copy_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)a, s, (float*)b, n);
-    PRD_CUDA_TRY(c, cudaPeekAtLastError());
-    return PRD_OK;
-  }
   int rsub(const void* b, void* r) {
     if (c->prec == PRD_FP64) rsub_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)b, (double*)r, n);
     else rsub_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)b, (float*)r, n);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
+    return PRD_OK;
+  }
+  // dots[k] = <V[k], w> for k <= j (device j), dots zeroed first
+  int dot_j(const void* V, size_t ld, const void* w, const double* sc, double* dots, int m) {
+    PRD_CUDA_TRY(c, cudaMemsetAsync(dots, 0, (m + 1) * sizeof(double), c->stream));
+    const dim3 g(grid, 8);
+    if (c->prec == PRD_FP64)
+      multidot_j_kernel<double><<<g, 256, 0, c->stream>>>((const double*)V, ld, (const double*)w, n, sc, dots);
+    else
+      multidot_j_kernel<float><<<g, 256, 0, c->stream>>>((const float*)V, ld, (const float*)w, n, sc, dots);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
+    return PRD_OK;
+  }
+  int axpy_j(const void* V, size_t ld, const double* h, const double* sc, void* w) {
+    if (c->prec == PRD_FP64)
+      multiaxpy_j_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)V, ld, h, sc, (double*)w, n);
+    else
+      multiaxpy_j_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)V, ld, h, sc, (float*)w, n);
+    PRD_CUDA_TRY(c, cudaPeekAtLastError());
+    return PRD_OK;
+  }
+  int scale_j(const void* a, const double* sc, void* V, void* cur) {
+    if (c->prec == PRD_FP64)
+      scale_j_kernel<double><<<grid, 256, 0, c->stream>>>((const double*)a, sc, (double*)V, n, (double*)cur, n);
+    else
+      scale_j_kernel<float><<<grid, 256, 0, c->stream>>>((const float*)a, sc, (float*)V, n, (float*)cur, n);
     PRD_CUDA_TRY(c, cudaPeekAtLastError());
     return PRD_OK;
   }
@@ -229,6 +283,211 @@ static int op_apply(Ctx* c, const void* x, void* y) {
   return c->op_transpose ? apply_operator_t(c, x, y) : apply_operator(c, x, y);
 }
 
+void invalidate_graphs(Ctx* c) {
+  for (auto& g : c->gk_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  for (auto& g : c->gk_graph)
+    if (g) {
+      cudaGraphDestroy(g);
+      g = nullptr;
+    }
+}
+
+// ---- lockstep rounds of prd_solve_batch
+struct BatchRound {
+  std::mutex mu;
+  std::condition_variable cv;
+  int live = 0;                              // contexts still taking part
+  long long gen = 0;                         // rounds launched
+  std::vector<std::pair<Ctx*, int>> req;     // (context, graph key) waiting in this round
+  cudaError_t err = cudaSuccess;             // status of the last round
+  cudaStream_t stream = nullptr;             // the rounds' launch stream
+  cudaEvent_t ev = nullptr;
+  std::map<std::vector<std::pair<Ctx*, int>>, cudaGraphExec_t> cache;   // by the set of children
+  long long launches = 0;
+};
+
+BatchRound* batch_round_create(int n) {
+  BatchRound* b = new BatchRound;
+  b->live = n;
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    batch_round_destroy(b);
+    return nullptr;
+  }
+  return b;
+}
+
+void batch_round_destroy(BatchRound* b) {
+  if (!b) return;
+  for (auto& kv : b->cache) cudaGraphExecDestroy(kv.second);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Launch the round for the waiting contexts (caller holds the lock): the
+// launch stream waits for each context's stream, one launch of the graph with
+// their steps as children, then every context's stream waits for the round.
+static cudaError_t batch_round_launch(BatchRound* b) {
+  std::vector<std::pair<Ctx*, int>> key = b->req;
+  std::sort(key.begin(), key.end());
+  cudaError_t e = cudaSuccess;
+  auto it = b->cache.find(key);
+  if (it == b->cache.end()) {
+    cudaGraph_t pg = nullptr;
+    e = cudaGraphCreate(&pg, 0);
+    for (size_t i = 0; e == cudaSuccess && i < key.size(); ++i) {
+      cudaGraphNode_t node;
+      e = cudaGraphAddChildGraphNode(&node, pg, nullptr, 0, key[i].first->gk_graph[key[i].second]);
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, pg, 0);
+    if (pg) cudaGraphDestroy(pg);
+    if (e != cudaSuccess) return e;
+    it = b->cache.emplace(key, ex).first;
+  }
+  for (auto& r : key) {
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev, r.first->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev, 0);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(it->second, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) {
+    ++b->launches;
+    for (auto& r : key) ++r.first->gk_launches;
+  }
+  return e;
+}
+
+// A context's Arnoldi step inside a batch round: wait for the round (the last
+// context to arrive launches it) and return its status.
+static cudaError_t batch_round_step(BatchRound* b, Ctx* c, int key) {
+  std::unique_lock<std::mutex> lk(b->mu);
+  const long long g = b->gen;
+  b->req.emplace_back(c, key);
+  if ((int)b->req.size() == b->live) {
+    b->err = batch_round_launch(b);
+    b->req.clear();
+    ++b->gen;
+    b->cv.notify_all();
+    return b->err;
+  }
+  b->cv.wait(lk, [&] { return b->gen != g; });
+  return b->err;
+}
+
+// A context stops taking part (its solve ended, or it runs its steps one by
+// one from now on); if everyone left is waiting, their round is launched.
+void batch_round_leave(BatchRound* b) {
+  if (!b) return;
+  std::unique_lock<std::mutex> lk(b->mu);
+  --b->live;
+  if (!b->req.empty() && (int)b->req.size() == b->live) {
+    b->err = batch_round_launch(b);
+    b->req.clear();
+    ++b->gen;
+    b->cv.notify_all();
+  }
+}
+
+// GMRES workspace of restart length m, kept by the context (the captured step
+// refers to its addresses); reallocated, and the graphs dropped, when m grows.
+static int gmres_workspace(Ctx* c, int m) {
+  if (c->gk_m >= m && c->gk_V.p) return PRD_OK;
+  invalidate_graphs(c);
+  dfree(c->gk_V); dfree(c->gk_r); dfree(c->gk_w); dfree(c->gk_cur); dfree(c->gk_S);
+  c->gk_m = 0;
+  const size_t vb = nvec(c) * c->esz;
+  const GState L{m};
+  int rc;
+  if ((rc = dalloc(c, c->gk_V, vb * (m + 1))) || (rc = dalloc(c, c->gk_r, vb)) || (rc = dalloc(c, c->gk_w, vb)) ||
+      (rc = dalloc(c, c->gk_cur, vb)) || (rc = dalloc(c, c->gk_S, L.total() * sizeof(double))))
+    return rc;
+  if (!c->gk_host) PRD_CUDA_TRY(c, cudaMallocHost((void**)&c->gk_host, 8 * sizeof(double)));
+  c->gk_m = m;
+  return PRD_OK;
+}
+
+// One Arnoldi step on the context's workspace (restart length L.m): w = A cur,
+// r = P^-1 w, two Gram-Schmidt passes against V[0..j], ||r||^2, the rotation
+// kernel (j -> j + 1), V[j + 1] = cur = r / ||r||, and the scalars copied to
+// pinned host memory.  Every address and launch shape is independent of j.
+static int record_step(Ctx* c, Vops& ops, const GState& L) {
+  const size_t n = nvec(c);
+  double* st = (double*)c->gk_S.p;
+  const double* sc = st + L.sc();
+  int rc;
+  if ((rc = op_apply(c, c->gk_cur.p, c->gk_w.p)) || (rc = apply_precond(c, c->gk_w.p, c->gk_r.p)) ||
+      (rc = ops.dot_j(c->gk_V.p, n, c->gk_r.p, sc, st + L.h(), L.m)) ||
+      (rc = ops.axpy_j(c->gk_V.p, n, st + L.h(), sc, c->gk_r.p)) ||
+      (rc = ops.dot_j(c->gk_V.p, n, c->gk_r.p, sc, st + L.h2(), L.m)) ||
+      (rc = ops.axpy_j(c->gk_V.p, n, st + L.h2(), sc, c->gk_r.p)) ||
+      (rc = ops.dot_many(c->gk_r.p, 0, 1, c->gk_r.p, st + L.sc() + kSS)))
+    return rc;
+  gm_arnoldi_kernel<<<1, 1, 0, c->stream>>>(st, L);
+  if ((rc = ops.scale_j(c->gk_r.p, sc, c->gk_V.p, c->gk_cur.p))) return rc;
+  PRD_CUDA_TRY(c, cudaMemcpyAsync(c->gk_host, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return PRD_OK;
+}
+
+// Run one Arnoldi step and wait for its scalars: replay the captured graph
+// (captured on first use), or launch directly (graphs off, or stage profiling
+// on, whose events are host-timed per launch).
+static int arnoldi_step(Ctx* c, Vops& ops, const GState& L, double* sc_host) {
+  const int key = c->op_transpose ? 1 : 0;
+  int rc = PRD_OK;
+  if (c->use_graph && !c->prof && !c->test_zero_op && !c->gk_exec[key]) {
+    // capture on the context's private stream (the caller's may be the legacy
+    // default stream, which cannot be captured); the graph is launched on the
+    // caller's.  A step that cannot be captured runs as direct launches from then on.
+    bool ok = c->gk_cap || cudaStreamCreateWithFlags(&c->gk_cap, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
+    cudaStream_t user = c->stream;
+    if (ok) ok = cudaStreamBeginCapture(c->gk_cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      c->stream = c->gk_cap;
+      rc = record_step(c, ops, L);
+      c->stream = user;
+      cudaGraph_t g = nullptr;
+      ok = cudaStreamEndCapture(c->gk_cap, &g) == cudaSuccess && rc == PRD_OK && g &&
+           cudaGraphInstantiate(&c->gk_exec[key], g, 0) == cudaSuccess;
+      if (ok) c->gk_graph[key] = g;
+      else if (g) cudaGraphDestroy(g);
+    }
+    if (!ok) {
+      invalidate_graphs(c);
+      c->use_graph = 0;
+      cudaGetLastError();
+      c->err = "ok";
+    }
+  }
+  const bool graph = c->use_graph && !c->prof && !c->test_zero_op && c->gk_exec[key];
+  if (c->batch && !graph) {
+    // this context runs its steps one by one: it no longer holds up the rounds
+    batch_round_leave(c->batch);
+    c->batch = nullptr;
+  }
+  if (c->batch) {
+    const cudaError_t e = batch_round_step(c->batch, c, key);
+    if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("batched Arnoldi round: ") + cudaGetErrorString(e));
+    std::memcpy(sc_host, c->gk_host, 8 * sizeof(double));
+    return PRD_OK;
+  }
+  if (graph) {
+    PRD_CUDA_TRY(c, cudaGraphLaunch(c->gk_exec[key], c->stream));
+    ++c->gk_launches;
+  } else if ((rc = record_step(c, ops, L))) {
+    return rc;
+  }
+  PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(sc_host, c->gk_host, 8 * sizeof(double));
+  return PRD_OK;
+}
+
 // GMRES on A x = b in the ctx precision; x holds the initial guess on entry.
 // inner: correction solve of the mixed-precision refinement.  x is zero on
 // entry and the solve ends as soon as the Arnoldi estimate is below tol (the
@@ -242,21 +501,16 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   Vops ops{c, n};
   int rc = ops.init();
   if (rc) return rc;
-  const GState L{m};
-  DBuf V, r, w, S;
+  if ((rc = gmres_workspace(c, m))) return rc;
+  const GState L{c->gk_m};                  // the workspace's layout (restart length >= m)
+  void* r = c->gk_r.p;
+  void* w = c->gk_w.p;
   struct { void* p; } b{const_cast<void*>(bvec)};
-  auto cleanup = [&]() { dfree(V); dfree(r); dfree(w); dfree(S); };
-  if ((rc = dalloc(c, V, vb * (m + 1))) || (rc = dalloc(c, r, vb)) || (rc = dalloc(c, w, vb)) ||
-      (rc = dalloc(c, S, L.total() * sizeof(double)))) {
-    cleanup();
-    return rc;
-  }
-  double* st = (double*)S.p;
+  double* st = (double*)c->gk_S.p;
   double* ss = st + L.sc() + kSS;
-  auto vec = [&](int k) { return (void*)((char*)V.p + (size_t)k * vb); };
   double bnorm;
-  if ((rc = ops.norm(b.p, ss, &bnorm))) { cleanup(); return rc; }
-  if (!(bnorm > 0) || !std::isfinite(bnorm)) { cleanup(); return fail(c, PRD_E_NAN, "right-hand side norm is zero or not finite"); }
+  if ((rc = ops.norm(b.p, ss, &bnorm))) return rc;
+  if (!(bnorm > 0) || !std::isfinite(bnorm)) return fail(c, PRD_E_NAN, "right-hand side norm is zero or not finite");
   int it = 0, nh = nh_io ? *nh_io : 0;
   double tol_in = tol;
   double tr = 1.0;
@@ -266,40 +520,30 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   while (it < max_iter) {
     // r = P^-1 (b - A x)
     if (inner && first) {
-      PRD_CUDA_TRY(c, cudaMemcpyAsync(w.p, b.p, vb, cudaMemcpyDeviceToDevice, c->stream));
+      PRD_CUDA_TRY(c, cudaMemcpyAsync(w, b.p, vb, cudaMemcpyDeviceToDevice, c->stream));
       tr = 1.0;
     } else {
-      if ((rc = op_apply(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
+      if ((rc = op_apply(c, x, w)) || (rc = ops.rsub(b.p, w))) break;
       double rn_true;
-      if ((rc = ops.norm(w.p, ss, &rn_true))) break;
+      if ((rc = ops.norm(w, ss, &rn_true))) break;
       tr = rn_true / bnorm;
     }
     first = false;
     if (!std::isfinite(tr)) { rc = fail(c, PRD_E_NAN, "residual is not finite"); break; }
     if (tr < tol) { status = PRD_OK; break; }
-    if ((rc = apply_precond(c, w.p, r.p))) break;
-    if ((rc = ops.dot_many(r.p, 0, 1, r.p, ss))) break;
-    gm_cycle_start_kernel<<<1, 1, 0, c->stream>>>(st, L);
+    if ((rc = apply_precond(c, w, r))) break;
+    if ((rc = ops.dot_many(r, 0, 1, r, ss))) break;
+    gm_cycle_start_kernel<<<1, 1, 0, c->stream>>>(st, L, tr);
+    // V[0] = cur = r / beta
+    if ((rc = ops.scale_j(r, st + L.sc(), c->gk_V.p, c->gk_cur.p))) break;
     if ((rc = ops.read(st + L.sc(), sc, 8))) break;
     const double beta0 = sc[kBeta0];
     if (!(beta0 > 0)) { status = PRD_OK; break; }
-    if ((rc = ops.scale(r.p, st + L.sc() + kInv, vec(0)))) break;
     int j = 0;
     bool breakdown = false, est_ok = false;
     for (; j < m && it < max_iter; ++j) {
-      if ((rc = op_apply(c, vec(j), w.p)) || (rc = apply_precond(c, w.p, r.p))) break;
+      if ((rc = arnoldi_step(c, ops, L, sc))) break;
       ++it;
-      // CGS2, projections kept on the device
-      if ((rc = ops.dot_many(V.p, n, j + 1, r.p, st + L.h())) ||
-          (rc = ops.axpy_many(V.p, n, st + L.h(), j + 1, r.p)) ||
-          (rc = ops.dot_many(V.p, n, j + 1, r.p, st + L.h2())) ||
-          (rc = ops.axpy_many(V.p, n, st + L.h2(), j + 1, r.p)) ||
-          (rc = ops.dot_many(r.p, 0, 1, r.p, ss)))
-        break;
-      gm_arnoldi_kernel<<<1, 1, 0, c->stream>>>(st, L, j, tr);
-      // the next basis vector is scaled on the device before the host looks
-      if ((rc = ops.scale(r.p, st + L.sc() + kInv, vec(j + 1)))) break;
-      if ((rc = ops.read(st + L.sc(), sc, 8))) break;
       const double hn = sc[kNorm], est = sc[kEst];
       if (!std::isfinite(hn) || !std::isfinite(est)) { rc = fail(c, PRD_E_NAN, "Arnoldi vector is not finite"); break; }
       if (hist && nh <= max_iter) hist[nh++] = est * hist_scale;
@@ -309,7 +553,7 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
     if (rc) break;
     // back substitution H y = g and x += V y, on the device
     gm_backsolve_kernel<<<1, 1, 0, c->stream>>>(st, L, j);
-    if ((rc = ops.update(V.p, n, st + L.y(), j, x))) break;
+    if ((rc = ops.update(c->gk_V.p, n, st + L.y(), j, x))) break;
     if (inner && (est_ok || breakdown)) {
       double gj;
       if ((rc = ops.read(st + L.g() + j, &gj, 1))) break;
@@ -318,9 +562,9 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
       break;
     }
     if (breakdown) {
-      if ((rc = op_apply(c, x, w.p)) || (rc = ops.rsub(b.p, w.p))) break;
+      if ((rc = op_apply(c, x, w)) || (rc = ops.rsub(b.p, w))) break;
       double rn;
-      if ((rc = ops.norm(w.p, ss, &rn))) break;
+      if ((rc = ops.norm(w, ss, &rn))) break;
       tr = rn / bnorm;
       status = tr < tol ? PRD_OK : PRD_E_BREAKDOWN;
       break;
@@ -329,9 +573,9 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   }
   if (!rc && status == PRD_E_NOCONV && !inner) {
     // final true residual
-    if (!(rc = op_apply(c, x, w.p)) && !(rc = ops.rsub(b.p, w.p))) {
+    if (!(rc = op_apply(c, x, w)) && !(rc = ops.rsub(b.p, w))) {
       double rn;
-      if (!(rc = ops.norm(w.p, ss, &rn))) {
+      if (!(rc = ops.norm(w, ss, &rn))) {
         tr = rn / bnorm;
         if (tr < tol) status = PRD_OK;
       }
@@ -340,7 +584,6 @@ static int gmres_core(Ctx* c, const void* bvec, void* x, double tol, int max_ite
   if (iters) *iters = it;
   if (true_res) *true_res = tr;
   if (nh_io) *nh_io = nh;
-  cleanup();
   if (rc) return rc;
   if (status == PRD_E_NOCONV) return fail(c, PRD_E_NOCONV, "GMRES reached max_iter before tol");
   if (status == PRD_E_BREAKDOWN) return fail(c, PRD_E_BREAKDOWN, "GMRES breakdown before tol");

@@ -260,6 +260,18 @@ def test_bf16x3_contraction_and_solve(name):
         worst = max(worst, np.max(np.abs(eg[iz] - G["sigma"][iz])) / scale)
     print(f"BF16x3 Sigma {name}: {worst:.2e} of the height maximum")
     assert worst < 1e-4
+    # the context's tiles are stored as bf16 planes: the same products as a
+    # PRD_FP32 context splitting its FP32 tiles on the fly (to FP32 atomics order)
+    from paper_2505_20968_gb300.binding import PrdError
+    Q = PRD(CASES[name](), precision="fp32", device=0)
+    Q.set_contraction("bf16x3")
+    eq = Q.apply_sigma(_t(G["x"], P)).cpu().numpy().astype(np.float64)
+    Q.close()
+    for iz in range(P.nz):
+        scale = np.max(np.abs(eq[iz, ..., 0]))
+        assert np.max(np.abs(eg[iz] - eq[iz])) <= 1e-6 * scale, iz
+    with pytest.raises(PrdError):
+        P.set_contraction("tf32x3")
     xg, info = P.solve(tol=1e-10, max_iter=900, restart=200)
     top = P.mu > 0
     Ig = xg.cpu().numpy()[-1, top].astype(np.float64)

@@ -4,7 +4,9 @@ columns it is a bijection onto [0, N ld); every 16-column K step is one
 contiguous block of N x 64 bytes (one bulk copy, 16-byte aligned start and
 size); and inside a block each row's 64 bytes are permuted by the 64-byte
 shared-memory swizzle, written here in its own form (byte address bits [4:5]
-XOR bits [7:8]), which is the layout the MMA descriptors declare."""
+XOR bits [7:8]), which is the layout the MMA descriptors declare.  The split
+layout of BF16x3 contexts (tile_off_split: bf16 hi and lo planes in the same
+bytes) is checked the same way against the 32-byte swizzle."""
 import os
 import shutil
 import subprocess
@@ -36,6 +38,23 @@ int main() {
       }
     if (((size_t)N * ld * 4) % 64 || ((size_t)N * 64) % 16) { std::printf("N=%d: alignment\n", N); return 4; }
     if (prd::tile_off(N - 1, 2 * N - 1, N, 2 * N + 4, false) != (size_t)(N - 1) * (2 * N + 4) + 2 * N - 1) return 5;
+    // split layout (bf16 planes): a bijection onto the same bytes; each K step
+    // one block of N x 64 bytes, hi plane first; rows of 32 bytes under the
+    // 32-byte swizzle (byte address bit 4 XOR bit 7)
+    std::vector<char> seen2((size_t)N * ld * 2, 0);
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < ld; ++k)
+        for (int lo = 0; lo < 2; ++lo) {
+          const size_t off = prd::tile_off_split(n, k, N, lo != 0);
+          if (off >= (size_t)N * ld * 2 || seen2[off]) { std::printf("split N=%d n=%d k=%d\n", N, n, k); return 6; }
+          seen2[off] = 1;
+          const int kc = k / 16, kl = k % 16;
+          const size_t plane = (size_t)kc * N * 32 + (size_t)lo * N * 16;   // bf16 units
+          if (off < plane || off >= plane + (size_t)N * 16) { std::printf("split N=%d: plane\n", N); return 7; }
+          const unsigned lin = (unsigned)(n * 32 + kl * 2);
+          const unsigned swz = lin ^ (((lin >> 7) & 1u) << 4);
+          if ((off - plane) * 2 != swz) { std::printf("split N=%d n=%d k=%d: swizzle\n", N, n, k); return 8; }
+        }
   }
   std::printf("ok\n");
   return 0;
