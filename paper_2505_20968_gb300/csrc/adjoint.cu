@@ -341,13 +341,20 @@ int apply_operator_t(Ctx* c, const void* x, void* y) {
   const double* r3ab = (const double*)(fp32 ? c->r3ab64.p : c->r3ab.p);
   const int ld = fp32 ? c->ld64() : c->ld();
   const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
-  DBuf x64, g1, g2, ib, ybr, mbr, F;
-  auto cleanup = [&]() { dfree(x64); dfree(g1); dfree(g2); dfree(ib); dfree(ybr); dfree(mbr); dfree(F); };
+  // scratch kept by the context (allocated on first use), so that the apply
+  // allocates nothing and can be captured into the adjoint solver's graph
+  DBuf& x64 = c->adj[0];
+  DBuf& g1 = c->adj[1];
+  DBuf& g2 = c->adj[2];
+  DBuf& ib = c->adj[3];
+  DBuf& ybr = c->adj[4];
+  DBuf& mbr = c->adj[5];
+  DBuf& F = c->adj[6];
   int rc;
-  if ((rc = dalloc(c, x64, nv * 8)) || (rc = dalloc(c, g1, nv * 8)) || (rc = dalloc(c, g2, nv * 8)) ||
-      (rc = dalloc(c, ib, nv * 8)) || (rc = dalloc(c, ybr, (size_t)nrows * N * 8)) ||
-      (rc = dalloc(c, mbr, (size_t)nrows * N * 8)) || (rc = dalloc(c, F, (size_t)nz * nuv * 2 * 8))) {
-    cleanup();
+  if (!F.p && ((rc = dalloc(c, x64, nv * 8)) || (rc = dalloc(c, g1, nv * 8)) || (rc = dalloc(c, g2, nv * 8)) ||
+               (rc = dalloc(c, ib, nv * 8)) || (rc = dalloc(c, ybr, (size_t)nrows * N * 8)) ||
+               (rc = dalloc(c, mbr, (size_t)nrows * N * 8)) || (rc = dalloc(c, F, (size_t)nz * nuv * 2 * 8)))) {
+    for (auto& b : c->adj) dfree(b);
     return rc;
   }
   const double* xd = (const double*)x;
@@ -355,15 +362,9 @@ int apply_operator_t(Ctx* c, const void* x, void* y) {
     to_f64_kernel<<<c->grid_ew(), 256, 0, c->stream>>>((const float*)x, (double*)x64.p, nv);
     xd = (const double*)x64.p;
   }
-  // Lambda^T
-  if (fp32)
-    delo_t_kernel<float><<<cdiv((long long)nO * N, 128), 128, 0, c->stream>>>(xd, (const float*)c->kt.p,
-                                                                               (const double*)c->dmu.p, (double*)g1.p,
-                                                                               nz, nO, N);
-  else
-    delo_t_kernel<double><<<cdiv((long long)nO * N, 128), 128, 0, c->stream>>>(xd, (const double*)c->kt.p,
-                                                                                (const double*)c->dmu.p, (double*)g1.p,
-                                                                                nz, nO, N);
+  // Lambda^T (FP32 mode: on the FP64 copy of the tables, as the forward residuals)
+  delo_t_kernel<double><<<cdiv((long long)nO * N, 128), 128, 0, c->stream>>>(
+      xd, (const double*)(fp32 ? c->kt64.p : c->kt.p), (const double*)c->dmu.p, (double*)g1.p, nz, nO, N);
   // S6^T (with f): cotangent of the comoving emissivity
   spline_t_kernel<<<cdiv(nrows, 64), 64, 0, c->stream>>>((const double*)g1.p, (const int*)c->ibk.p,
                                                          (const double*)c->tbk.p, (const double*)c->sp.p,
@@ -393,9 +394,6 @@ int apply_operator_t(Ctx* c, const void* x, void* y) {
                                                                               nrows, N);
   sub_out_kernel<<<c->grid_ew(), 256, 0, c->stream>>>(xd, (const double*)g1.p, y, nv, fp32 ? 1 : 0);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  cleanup();
-  if (e != cudaSuccess) return fail(c, PRD_E_CUDA, std::string("adjoint apply: ") + cudaGetErrorString(e));
   return PRD_OK;
 }
 

@@ -74,6 +74,7 @@ static void free_all(Ctx* c) {
   c->has64 = false;
   c->tc_ready = false;
   for (DBuf* b : bufs) dfree(*b);
+  for (auto& b : c->adj) dfree(b);
   for (auto& b : c->krylov) dfree(b);
   c->krylov.clear();
   for (auto& b : c->owned) dfree(b);

@@ -122,6 +122,7 @@ struct Ctx {
   // the right-hand side and f (the formal solution of the residual operator
   // then carries no FP32 table rounding)
   DBuf kt64, epsth64;
+  DBuf adj[7];       // scratch of the transposed operator (allocated on first use)
   DBuf par;          // [z][o][n][3] DELOPAR source weights psi_M, psi_O, psi_P of the step arriving there (double)
   DBuf eta_line;     // [z][o][n] the line's share eta_line/eta_total of eta_I (double): f normalises the line only
   DBuf cont_pw;      // [o][o'][4][4] w_o' P(o, o') dipole phase matrix of continuum scattering (double)
