@@ -270,10 +270,17 @@ int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
  * device), captured on the first iteration and kept with the solver's
  * workspace; 0 launches the same kernels one by one.  Results are identical.
  * Any option change, prd_set_precond_sweeps and prd_setup drop the captured
- * graphs; stage profiling (prd_set_profiling) runs the kernels one by one. */
+ * graphs; stage profiling (prd_set_profiling) runs the kernels one by one.
+ * PRD_OPT_STAGED_SWEEP: 1 (default) runs the formal solution of the operator
+ * and of prd_apply_lambda / prd_rhs with the heights' inputs streamed into
+ * shared memory by bulk asynchronous copies (a ring of 8 heights per block of
+ * 128 rays) when the frequency count is even; 0, or an odd count, runs one
+ * thread per ray reading its inputs directly.  Results are identical.  Its
+ * waits are bounded like the contraction's (PRD_E_TIMEOUT through
+ * prd_device_status). */
 enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2, PRD_OPT_WAIT_POLLS = 3, PRD_OPT_TEST_ZERO_OPERATOR = 4,
        PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6, PRD_OPT_CONTRACTION = 7, PRD_OPT_TILE_STAGES = 8,
-       PRD_OPT_GRAPH = 9 };
+       PRD_OPT_GRAPH = 9, PRD_OPT_STAGED_SWEEP = 10 };
 enum { PRD_CONTRACTION_TF32X3 = 0, PRD_CONTRACTION_BF16X3 = 1 };
 enum { PRD_DELO_LINEAR = 0, PRD_DELOPAR = 1 };
 int prd_set_option(prd_ctx* ctx, int option, int value);

@@ -613,6 +613,10 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
     c->use_graph = value ? 1 : 0;
     return PRD_OK;
   }
+  if (option == PRD_OPT_STAGED_SWEEP) {
+    c->staged_sweep = value ? 1 : 0;
+    return PRD_OK;
+  }
   if (option == PRD_OPT_TENSOR_CORES) {
     if (value && c->prec != PRD_FP32) return fail(c, PRD_E_ARG, "tensor-core contraction needs PRD_FP32");
     if (!value && c->split_tiles)

@@ -452,11 +452,6 @@ __device__ __forceinline__ void kprime(const T* t, A K[4][4]) {
   K[2][3] = t[5]; K[3][2] = -t[5];
 }
 
-// Formal solution along every ray (Sect. 3): DELO-linear, or DELOPAR when
-// `par` holds the parabolic source weights (psi_M, psi_O, psi_P) of the step
-// arriving at each point (the source vector parabolic through the upwind,
-// current and downwind points; the K'I term stays linear, with DELO-linear's
-// a, b; the last point of a ray has psi = (a, b, 0)).
 // Per-point inputs of one step of the formal solution.
 template <typename T, typename A>
 struct DeloPoint {
@@ -476,14 +471,84 @@ __device__ __forceinline__ void delo_load(DeloPoint<T, A>& d, const A* __restric
     for (int i = 0; i < 3; ++i) d.ps[i] = par[pt * 3 + i];
 }
 
-// Formal solution along every ray (Sect. 3): DELO-linear, or DELOPAR when
-// `par` holds the parabolic source weights (psi_M, psi_O, psi_P) of the step
-// arriving at each point (the source vector parabolic through the upwind,
-// current and downwind points; the K'I term stays linear, with DELO-linear's
-// a, b; the last point of a ray has psi = (a, b, 0)).  One thread per ray
-// (Omega, nu); the sweep is sequential in height, so the inputs of the next
-// two points are loaded while a point is solved (few rays per SM, so the
-// memory parallelism has to come from within each ray).
+// One step of the formal solution (Sect. 3) at the p-th point of a ray: DELO-
+// linear, or DELOPAR when `par` (the parabolic source weights psi_M, psi_O,
+// psi_P of the step arriving at the point; the source vector parabolic through
+// the upwind, current and downwind points, the K'I term linear with DELO-
+// linear's a, b; psi = (a, b, 0) at the last point) is set; `nxt` is the next
+// point (read only under DELOPAR, p + 1 < nz).  I, Sp, Kp carry the upwind
+// intensity, source and K' from step to step.
+template <typename T, typename A>
+__device__ __forceinline__ void delo_step(const DeloPoint<T, A>& cur, const DeloPoint<T, A>& nxt, bool par,
+                                          bool has_next, int p, bool up, int boundary, double WT0, A I[4], A Sp[4],
+                                          A Kp[4][4]) {
+  const T* t = cur.t;
+  A Kk[4][4];
+  kprime(t, Kk);
+  const A ie = t[6];
+  A S[4];
+  for (int s = 0; s < 4; ++s) S[s] = cur.e[s] * ie;
+  if (p == 0) {
+    I[0] = (boundary && up) ? (A)WT0 : (A)0;
+    I[1] = I[2] = I[3] = (A)0;
+  } else {
+    // Optically thick step (e = exp(-dtau) <= 1/2): solve for D = I_k - S_k,
+    //   (Id + b K'_k) D = e (I_{k-1} - S_k) + a (S_{k-1} - S_k) - a K'_{k-1} I_{k-1} - b K'_k S_k,
+    // which reproduces a constant unpolarised source exactly whatever the
+    // rounding of the stored weights (b = 1 - e - a enters only the dichroic
+    // terms).  Thin step: the standard form for I_k, free of the
+    // cancellation I_{k-1} - S_k when I << S.
+    const A e = t[7], al = t[8], be = t[9];
+    const bool thick = e <= (A)0.5;
+    // source weights: DELO-linear (a, b, 0) or DELOPAR's parabolic ones, with the
+    // downwind source S_P; psi_M + psi_O + psi_P = 1 - e in both
+    A pM = al, pO = be, pP = (A)0;
+    A SP[4] = {0, 0, 0, 0};
+    if (par) {
+      pM = (A)cur.ps[0];
+      pO = (A)cur.ps[1];
+      pP = (A)cur.ps[2];
+      if (has_next) {
+        const A ie2 = nxt.t[6];
+        for (int s = 0; s < 4; ++s) SP[s] = nxt.e[s] * ie2;
+      }
+    }
+    A rhs[4];
+    for (int i = 0; i < 4; ++i) {
+      A v = thick ? e * (I[i] - S[i]) + pM * (Sp[i] - S[i]) + pP * (SP[i] - S[i])
+                  : e * I[i] + pM * Sp[i] + pO * S[i] + pP * SP[i];
+      for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + (thick ? be * Kk[i][j] * S[j] : (A)0);
+      rhs[i] = v;
+    }
+    A M4[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) M4[i][j] = (i == j ? (A)1 : (A)0) + be * Kk[i][j];
+    for (int c0 = 0; c0 < 4; ++c0) {
+      const A inv = (A)1 / M4[c0][c0];
+      for (int r = c0 + 1; r < 4; ++r) {
+        const A f = M4[r][c0] * inv;
+        for (int cc = c0; cc < 4; ++cc) M4[r][cc] -= f * M4[c0][cc];
+        rhs[r] -= f * rhs[c0];
+      }
+    }
+    A D[4];
+    for (int r = 3; r >= 0; --r) {
+      A v = rhs[r];
+      for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * D[cc];
+      D[r] = v / M4[r][r];
+    }
+    for (int i = 0; i < 4; ++i) I[i] = thick ? S[i] + D[i] : D[i];
+  }
+  for (int i = 0; i < 4; ++i) {
+    Sp[i] = S[i];
+    for (int j = 0; j < 4; ++j) Kp[i][j] = Kk[i][j];
+  }
+}
+
+// Formal solution along every ray, one thread per ray (Omega, nu); the sweep is
+// sequential in height, so the inputs of the next two points are loaded while
+// a point is solved.  Used where the staged sweep below does not apply (odd
+// frequency counts, lines of sight, the FP64 residual path).
 template <typename T, typename A>
 __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt, const double* __restrict__ par,
                             const double* __restrict__ mu, const A* __restrict__ x_sub, A* __restrict__ out, int nz,
@@ -502,71 +567,167 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
   for (int p = 0; p < nz; ++p) {
     const size_t pt = point(p);
     if (p + 2 < nz) delo_load(nx2, eps, kt, par, x_sub, point(p + 2));
-    const T* t = cur.t;
-    A Kk[4][4];
-    kprime(t, Kk);
-    const A ie = t[6];
-    A S[4];
-    for (int s = 0; s < 4; ++s) S[s] = cur.e[s] * ie;
-    if (p == 0) {
-      I[0] = (boundary && up) ? (A)WT0 : (A)0;
-      I[1] = I[2] = I[3] = (A)0;
-    } else {
-      // Optically thick step (e = exp(-dtau) <= 1/2): solve for D = I_k - S_k,
-      //   (Id + b K'_k) D = e (I_{k-1} - S_k) + a (S_{k-1} - S_k) - a K'_{k-1} I_{k-1} - b K'_k S_k,
-      // which reproduces a constant unpolarised source exactly whatever the
-      // rounding of the stored weights (b = 1 - e - a enters only the dichroic
-      // terms).  Thin step: the standard form for I_k, free of the
-      // cancellation I_{k-1} - S_k when I << S.
-      const A e = t[7], al = t[8], be = t[9];
-      const bool thick = e <= (A)0.5;
-      // source weights: DELO-linear (a, b, 0) or DELOPAR's parabolic ones, with the
-      // downwind source S_P; psi_M + psi_O + psi_P = 1 - e in both
-      A pM = al, pO = be, pP = (A)0;
-      A SP[4] = {0, 0, 0, 0};
-      if (par) {
-        pM = (A)cur.ps[0];
-        pO = (A)cur.ps[1];
-        pP = (A)cur.ps[2];
-        if (p + 1 < nz) {
-          const A ie2 = nx1.t[6];
-          for (int s = 0; s < 4; ++s) SP[s] = nx1.e[s] * ie2;
-        }
-      }
-      A rhs[4];
-      for (int i = 0; i < 4; ++i) {
-        A v = thick ? e * (I[i] - S[i]) + pM * (Sp[i] - S[i]) + pP * (SP[i] - S[i])
-                    : e * I[i] + pM * Sp[i] + pO * S[i] + pP * SP[i];
-        for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + (thick ? be * Kk[i][j] * S[j] : (A)0);
-        rhs[i] = v;
-      }
-      A M4[4][4];
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) M4[i][j] = (i == j ? (A)1 : (A)0) + be * Kk[i][j];
-      for (int c0 = 0; c0 < 4; ++c0) {
-        const A inv = (A)1 / M4[c0][c0];
-        for (int r = c0 + 1; r < 4; ++r) {
-          const A f = M4[r][c0] * inv;
-          for (int cc = c0; cc < 4; ++cc) M4[r][cc] -= f * M4[c0][cc];
-          rhs[r] -= f * rhs[c0];
-        }
-      }
-      A D[4];
-      for (int r = 3; r >= 0; --r) {
-        A v = rhs[r];
-        for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * D[cc];
-        D[r] = v / M4[r][r];
-      }
-      for (int i = 0; i < 4; ++i) I[i] = thick ? S[i] + D[i] : D[i];
-    }
+    delo_step(cur, nx1, par != nullptr, p + 1 < nz, p, up, boundary, WT0, I, Sp, Kp);
     for (int s = 0; s < 4; ++s) out[pt * 4 + s] = x_sub ? cur.xs[s] - I[s] : I[s];
-    for (int i = 0; i < 4; ++i) {
-      Sp[i] = S[i];
-      for (int j = 0; j < 4; ++j) Kp[i][j] = Kk[i][j];
-    }
     cur = nx1;
     nx1 = nx2;
   }
+}
+
+// ---- staged sweep: one CTA per (direction, chunk of kDR frequencies).  Warp 0
+// lane 0 streams each height's slices of the inputs (K'/eta1 and DELO weights,
+// emissivity, the x of y = x - Lambda eps, DELOPAR weights: contiguous runs of
+// kDR points) with bulk asynchronous copies into a ring of kDStages heights;
+// the kDR consumer threads (one per ray) take their point from shared memory.
+// Needs an even frequency count (16-byte aligned slices).  Every wait is
+// bounded: on expiry the CTA stops, the producer drains its copies, and the
+// error flag is raised (PRD_E_TIMEOUT through prd_device_status).
+constexpr int kDR = 128;                       // rays per CTA
+constexpr int kDStages = 8;                    // heights in flight per CTA
+constexpr long long kDSpin = 1ll << 24;
+
+__device__ __forceinline__ uint32_t dsm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool dbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\tselp.b32 %0, 1, 0, P;\n\t}\n"
+      : "=r"(ok)
+      : "r"(dsm_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool dbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  for (long long i = 0; i < kDSpin; ++i) {
+    if (dbar_try(b, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+template <typename T, typename A>
+struct DeloStage {
+  // byte offsets of the slices inside one stage (each a multiple of 16)
+  static constexpr int kKT = 0;
+  static constexpr int kEps = kKT + kDR * 10 * (int)sizeof(T);
+  static constexpr int kXs = kEps + kDR * 4 * (int)sizeof(A);
+  static constexpr int kPar = kXs + kDR * 4 * (int)sizeof(A);
+  static constexpr int kBytes = kPar + kDR * 3 * 8;
+};
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(32 + kDR) delo_staged_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
+                                                               const double* __restrict__ par,
+                                                               const double* __restrict__ mu,
+                                                               const A* __restrict__ x_sub, A* __restrict__ out,
+                                                               int nz, int nO, int N, int boundary, double WT0,
+                                                               int* err) {
+  using L = DeloStage<T, A>;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  uint64_t* full = (uint64_t*)(dsm + kDStages * L::kBytes);
+  uint64_t* empty = full + kDStages;
+  volatile int* abort_flag = (volatile int*)(empty + kDStages);
+  const int o = blockIdx.y, n0 = blockIdx.x * kDR;
+  const int R = min(kDR, N - n0);                // rays of this CTA (even)
+  const bool up = mu[o] > 0.0;
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < kDStages; ++d) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(dsm_u32(&full[d])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(dsm_u32(&empty[d])), "r"(kDR));
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto row = [&](int p) { return ((size_t)(up ? p : nz - 1 - p) * nO + o) * N + n0; };
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      const uint32_t bkt = (uint32_t)R * 10 * sizeof(T), bv = (uint32_t)R * 4 * sizeof(A), bp = (uint32_t)R * 24;
+      const uint32_t bytes = bkt + bv + (x_sub ? bv : 0u) + (par ? bp : 0u);
+      int p = 0;
+      for (; p < nz; ++p) {
+        const int d = p % kDStages;
+        if (p >= kDStages && !dbar_wait(&empty[d], ((p / kDStages) - 1) & 1, abort_flag)) break;
+        unsigned char* st = dsm + d * L::kBytes;
+        const size_t r0 = row(p);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(dsm_u32(&full[d])), "r"(bytes)
+                     : "memory");
+        auto copy = [&](unsigned char* dst, const void* src, uint32_t nb) {
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  dsm_u32(dst)),
+              "l"((uint64_t)src), "r"(nb), "r"(dsm_u32(&full[d]))
+              : "memory");
+        };
+        copy(st + L::kKT, kt + r0 * 10, bkt);
+        copy(st + L::kEps, eps + r0 * 4, bv);
+        if (x_sub) copy(st + L::kXs, x_sub + r0 * 4, bv);
+        if (par) copy(st + L::kPar, par + r0 * 3, bp);
+      }
+      if (*abort_flag)   // drain copies that were issued and may not have been consumed
+        for (int q = max(0, p - kDStages); q < p; ++q)
+          for (long long i = 0; i < kDSpin && !dbar_try(&full[q % kDStages], (q / kDStages) & 1); ++i) {
+          }
+    }
+  } else {
+    const int r = threadIdx.x - 32;
+    const bool live = r < R;
+    A I[4] = {0, 0, 0, 0};
+    A Sp[4] = {0, 0, 0, 0};
+    A Kp[4][4];
+    DeloPoint<T, A> cur, nxt;
+    // take point p of this ray from its stage, then release the stage
+    auto take = [&](int p, DeloPoint<T, A>& dp) -> bool {
+      const int d = p % kDStages;
+      if (!dbar_wait(&full[d], (p / kDStages) & 1, abort_flag)) return false;
+      const unsigned char* st = dsm + d * L::kBytes;
+      if (live) {
+        const T* tk = (const T*)(st + L::kKT) + r * 10;
+        for (int i = 0; i < 10; ++i) dp.t[i] = tk[i];
+        const A* ev = (const A*)(st + L::kEps) + r * 4;
+        for (int s = 0; s < 4; ++s) dp.e[s] = ev[s];
+        const A* xv = (const A*)(st + L::kXs) + r * 4;
+        for (int s = 0; s < 4; ++s) dp.xs[s] = x_sub ? xv[s] : (A)0;
+        if (par) {
+          const double* pv = (const double*)(st + L::kPar) + r * 3;
+          for (int i = 0; i < 3; ++i) dp.ps[i] = pv[i];
+        }
+      }
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(dsm_u32(&empty[d])) : "memory");
+      return true;
+    };
+    bool ok = take(0, cur);
+    for (int p = 0; p < nz && ok; ++p) {
+      if (p + 1 < nz) ok = take(p + 1, nxt);
+      if (!ok) break;
+      if (live) {
+        delo_step(cur, nxt, par != nullptr, p + 1 < nz, p, up, boundary, WT0, I, Sp, Kp);
+        A* dst = out + (row(p) + r) * 4;
+        for (int s = 0; s < 4; ++s) dst[s] = x_sub ? cur.xs[s] - I[s] : I[s];
+      }
+      cur = nxt;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag && err) atomicExch(err, 1);
+}
+
+template <typename T, typename A>
+static int launch_delo(Ctx* c, const A* eps, const T* kt, const double* par, const double* mu, const A* x_sub, A* out,
+                       int boundary, bool allow_staged) {
+  const int nz = c->nz, nO = c->nO, N = c->nnu;
+  if (allow_staged && c->staged_sweep && N % 2 == 0 && c->tc_err.p) {
+    using L = DeloStage<T, A>;
+    const int smem = kDStages * L::kBytes + 2 * kDStages * 8 + 16;
+    PRD_CUDA_TRY(c, cudaFuncSetAttribute(delo_staged_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    delo_staged_kernel<T, A><<<dim3(ceil_div(N, kDR), nO), 32 + kDR, smem, c->stream>>>(
+        eps, kt, par, mu, x_sub, out, nz, nO, N, boundary, c->WT[0], (int*)c->tc_err.p);
+  } else {
+    delo_kernel<T, A><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>(eps, kt, par, mu, x_sub, out, nz, nO, N, boundary,
+                                                                    c->WT[0]);
+  }
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
 }
 
 // f = (1 - eps) W_T eta_I / [Sigma (W_T, 0, 0, 0)]_I with the line's eta_I (App. E),
@@ -738,19 +899,15 @@ int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool 
   const double* dmu = (const double*)c->dmu.p;
   cudaEvent_t e0;
   stage_begin(c, ST_S7, &e0);
+  int rc;
   if (c->prec == PRD_FP64)
-    delo_kernel<double, double><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const double*)eps, (const double*)c->kt.p,
-                                                                       (const double*)c->par_active(), dmu,
-                                                                       (const double*)sub_from, (double*)out, nz, nO,
-                                                                       N, boundary ? 1 : 0, c->WT[0]);
+    rc = launch_delo<double, double>(c, (const double*)eps, (const double*)c->kt.p, (const double*)c->par_active(), dmu,
+                                     (const double*)sub_from, (double*)out, boundary ? 1 : 0, true);
   else
-    delo_kernel<float, float><<<ceil_div(nO * N, 128), 128, 0, c->stream>>>((const float*)eps, (const float*)c->kt.p,
-                                                                      (const double*)c->par_active(), dmu,
-                                                                      (const float*)sub_from, (float*)out, nz, nO, N,
-                                                                      boundary ? 1 : 0, c->WT[0]);
+    rc = launch_delo<float, float>(c, (const float*)eps, (const float*)c->kt.p, (const double*)c->par_active(), dmu,
+                                   (const float*)sub_from, (float*)out, boundary ? 1 : 0, true);
   stage_end(c, ST_S7, e0);
-  PRD_CUDA_TRY(c, cudaPeekAtLastError());
-  return PRD_OK;
+  return rc;
 }
 
 // Kirchhoff factor f = (1-eps) W_T eta_I / [Sigma (W_T,0,0,0)]_I (App. E).  In

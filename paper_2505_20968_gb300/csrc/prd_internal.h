@@ -159,6 +159,7 @@ struct Ctx {
   cudaGraphExec_t gk_exec[2] = {nullptr, nullptr};
   cudaGraph_t gk_graph[2] = {nullptr, nullptr};   // the captured steps (children of a batch round)
   int use_graph = 1;                       // PRD_OPT_GRAPH
+  int staged_sweep = 1;                    // PRD_OPT_STAGED_SWEEP: bulk-copy-staged formal solution
   cudaStream_t gk_cap = nullptr;           // private stream the step is captured on
   struct BatchRound* batch = nullptr;      // set while prd_solve_batch runs this context in lockstep
   long long gk_launches = 0;               // graph launches (prd_graph_launches)

@@ -38,11 +38,12 @@ namespace prd {
 namespace tc {
 
 constexpr int kStagesMax = 5;                 // tile ring depth: 2..5, the most that fit beside the rest
-constexpr int kCBufs = 2;                     // builder ring: A_lo, B_hi, B_lo
+constexpr int kCBufsMax = 4;                  // builder ring (A_lo, B_hi, B_lo): 2 buffers, 4 for split tiles
 constexpr int kKC = 16;                       // fp32 per stage along K (64-byte rows)
 constexpr int kMaxE = 32;                     // output directions per CTA
 constexpr int kNCPMax = 4 * kMaxE;            // MMA N (Stokes columns)
 constexpr int kBBytes = kNCPMax * kKC * 4;
+__host__ __device__ constexpr int n_cbufs(bool split) { return split ? 4 : 2; }
 // Builder warps: the B build and the TF32 splits are chains of dependent
 // shared-memory loads and FMAs, so the builders are latency-bound; more warps
 // hide more of that latency (16 warps, one B item each, fit 576 threads x 112
@@ -66,11 +67,12 @@ static_assert(kNCPMax == 128 && (kGenWarps == 8 || kGenWarps == 16), "B items: 1
 // incident directions (stride N + 1 float4, odd modulo 8 so that different
 // slots fall in different bank groups) and the auxiliary tables, plus 1 KB to
 // align the base.
+// (split tiles: no A_lo, and the B planes are bf16, 4 KB each)
 __host__ __device__ constexpr int cbuf_bytes(int N, bool split) {
-  return (split ? 0 : ((N + 15) / 16 * 16) * 64) + 2 * kBBytes;
+  return split ? kBBytes : ((N + 15) / 16 * 16) * 64 + 2 * kBBytes;
 }
 __host__ __device__ constexpr int smem_bytes(int N, int st, bool split) {
-  return st * ((N + 15) / 16 * 16) * 64 + kCBufs * cbuf_bytes(N, split) + 2 * kYBytes + kISlots * (N + 1) * 16 +
+  return st * ((N + 15) / 16 * 16) * 64 + n_cbufs(split) * cbuf_bytes(N, split) + 2 * kYBytes + kISlots * (N + 1) * 16 +
          kAuxBytes + 1024;
 }
 constexpr long long kSpin = 1ll << 24;        // bounded waits (default limit of the pipeline waits; drains)
@@ -245,7 +247,9 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int IS = N + 1;                          // float4 stride of a resident I~ slot
   unsigned char* cbuf = sm + nst * SA;                             // [buffer] A_lo, B_hi, B_lo
   const int CB = cbuf_bytes(N, kSplit);
-  float* Ys = (float*)(cbuf + kCBufs * CB);                        // [buffer][pair][16][2]
+  constexpr int NCB = n_cbufs(kSplit);                             // builder ring depth
+  constexpr int BPL = kSplit ? kBBytes / 2 : kBBytes;              // bytes of one B plane
+  float* Ys = (float*)(cbuf + NCB * CB);                           // [buffer][pair][16][2]
   float4* Ir = (float4*)((unsigned char*)Ys + 2 * kYBytes);         // [slot][k < N], resident
   int* eptr = (int*)((unsigned char*)Ir + (size_t)kISlots * IS * 16);   // local pair range of each output
   int* fast_p = eptr + kMaxE + 1;                                  // fast-path flag, staged slots
@@ -254,8 +258,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   uint64_t* full = (uint64_t*)(((uintptr_t)(slot_dir + kISlots) + 7) & ~(uintptr_t)7);
   uint64_t* empty = full + kStagesMax;
   uint64_t* ready = empty + kStagesMax;
-  uint64_t* cfree = ready + kCBufs;
-  uint64_t* done = cfree + kCBufs;
+  uint64_t* cfree = ready + kCBufsMax;
+  uint64_t* done = cfree + kCBufsMax;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       mbar_init(&full[s], 1);        // armed by the producer with the bytes of the tile copy
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < kCBufs; ++b) {
+    for (int b = 0; b < NCB; ++b) {
       mbar_init(&ready[b], kGen);
       mbar_init(&cfree[b], 1);
     }
@@ -330,10 +334,11 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       int it = 0;
       const uint64_t pol_t = policy_evict_first();
       const uint32_t abytes = (uint32_t)N * kKC * 4;
-      for (; it < iters; ++it) {
-        const int s = it % nst;
-        if (it >= nst && !mbar_wait(&empty[s], ((it / nst) - 1) & 1, abort_flag, p.spin)) break;
-        const int ti = it / KCH, kc = it - ti * KCH;
+      // stage s = it % nst with phase parity ps = (it / nst) & 1, tile ti = it / KCH and
+      // its K step kc, all advanced incrementally (no divisions per step)
+      int s = 0, ps = 0, ti = 0, kc = 0;
+      for (; it < iters; ++it, s = (s + 1 == nst) ? (ps ^= 1, 0) : s + 1, kc = (kc + 1 == KCH) ? (++ti, 0) : kc + 1) {
+        if (it >= nst && !mbar_wait(&empty[s], ps ^ 1, abort_flag, p.spin)) break;
         // rows n >= N of the stage keep stale data: they only reach output rows
         // that the epilogue never reads
         const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
@@ -362,16 +367,17 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       // operand is A, the streamed tile is B, so one MMA covers every row n
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NM >> 3) << 17) | ((128u >> 4) << 24);
       int issued = 0;
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % nst, cb = it % kCBufs;
-        if (!mbar_wait(&ready[cb], (it / kCBufs) & 1, abort_flag, p.spin)) break;
+      int s = 0, ps = 0;                         // it % nst and (it / nst) & 1
+      for (int it = 0; it < iters; ++it, s = (s + 1 == nst) ? (ps ^= 1, 0) : s + 1) {
+        const int cb = it & (NCB - 1);
+        if (!mbar_wait(&ready[cb], (it / NCB) & 1, abort_flag, p.spin)) break;
         // split tiles: the builders do not wait for the tile step, the MMAs do
-        if (kSplit && !mbar_wait(&full[s], (it / nst) & 1, abort_flag, p.spin)) break;
+        if (kSplit && !mbar_wait(&full[s], ps, abort_flag, p.spin)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         unsigned char* A = sm + s * SA;
         unsigned char* Alo = cbuf + cb * CB;
         unsigned char* Bhi = Alo + (kSplit ? 0 : SA);
-        unsigned char* Blo = Bhi + kBBytes;
+        unsigned char* Blo = Bhi + BPL;
         if constexpr (kBF16) {
           // A_hi and A_lo planes (NM x 32 bytes each): the stage itself for split
           // tiles, else the A_lo buffer the builders filled
@@ -453,11 +459,12 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       gen_sync();
     }
     bool aborted = false;
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % nst, cb = it % kCBufs;
-      const int ti = it / KCH, kc = it - ti * KCH;
-      bool got = !aborted && (kSplit || mbar_wait(&full[s], (it / nst) & 1, abort_flag, p.spin));
-      if (got && it >= kCBufs) got = mbar_wait(&cfree[cb], ((it / kCBufs) - 1) & 1, abort_flag, p.spin);
+    int s = 0, ps = 0, ti = 0, kc = 0;           // it % nst, (it / nst) & 1, it / KCH, it % KCH
+    for (int it = 0; it < iters;
+         ++it, s = (s + 1 == nst) ? (ps ^= 1, 0) : s + 1, kc = (kc + 1 == KCH) ? (++ti, 0) : kc + 1) {
+      const int cb = it & (NCB - 1);
+      bool got = !aborted && (kSplit || mbar_wait(&full[s], ps, abort_flag, p.spin));
+      if (got && it >= NCB) got = mbar_wait(&cfree[cb], ((it / NCB) - 1) & 1, abort_flag, p.spin);
       float* Ysb = Ys + (ti & 1) * (kYPairs * 32);
       if (kc == 0) {
         // a new tile: stage its Y, then all builders agree to go on (every builder
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       unsigned char* A = sm + s * SA;
       unsigned char* Alo = cbuf + cb * CB;
       unsigned char* Bhi = Alo + (kSplit ? 0 : SA);
-      unsigned char* Blo = Bhi + kBBytes;
+      unsigned char* Blo = Bhi + BPL;
       if constexpr (!kSplit) {
         const float4* a4 = (const float4*)A;
         float4* l4 = (float4*)Alo;
@@ -659,14 +666,16 @@ static int r2_tc_stages(int N, bool split) {
 
 // Work list and error flag of the tensor-core contraction.
 int r2_tc_prepare(Ctx* c) {
+  // the device error flag of the bounded waits (contraction and staged sweep), all precisions
+  if (!c->tc_err.p) {
+    int rc = dalloc(c, c->tc_err, sizeof(int));
+    if (rc) return rc;
+    PRD_CUDA_TRY(c, cudaMemset(c->tc_err.p, 0, sizeof(int)));
+  }
   if (c->prec != PRD_FP32) return PRD_OK;
   if (!c->tiled() || r2_tc_stages(c->nnu, false) < 2)
     return fail(c, PRD_E_ARG, "tensor-core contraction needs FP32 tiles and N small enough for two tile stages "
                               "beside the resident I~ (N <= 232)");
-  if (!c->tc_err.p) {
-    int rc = dalloc(c, c->tc_err, sizeof(int));
-    if (rc) return rc;
-  }
   // work items: every class split into chunks of <= kMaxE output directions
   std::vector<int> work;
   for (int k = 0; k < c->ncls; ++k)

@@ -176,8 +176,11 @@ def test_delopar_formal_solver_matches_oracle(name):
     the right-hand side (FP64 1e-9, FP32 2e-5 of the maximum, the DELO-linear
     bounds), and the solution of the whole problem: FP64 within 1e-8; FP32
     (refined solve) emergent I within 1e-5 relative and Q/I, U/I, V/I within
-    1e-4 absolute of the oracle's DELOPAR solution.  The transposed operator
-    is refused under DELOPAR."""
+    1e-4 absolute of the oracle's DELOPAR solution, at GMRES tol 1e-11: the
+    H I case has a line-core point whose emergent I is 5.5e-5 of the maximum,
+    where Q/I to 1e-4 needs Q to ~5e-9 of the maximum intensity; at tol 1e-10
+    the DELOPAR problem left 1.1e-4 there.  The transposed operator is refused
+    under DELOPAR."""
     from paper_2505_20968_gb300.binding import PRD, PrdError, lib
     G = np.load(os.path.join(GOLD, name + ".npz"))
     R = np.load(os.path.join(GOLD, name + "_par.npz"))
@@ -189,7 +192,7 @@ def test_delopar_formal_solver_matches_oracle(name):
     assert np.max(np.abs(lam - R["lam"])) / np.max(np.abs(R["lam"])) < tol
     b = P.rhs().cpu().numpy().astype(np.float64)
     assert np.max(np.abs(b - R["rhs"])) / np.max(np.abs(R["rhs"])) < tol
-    x, info = P.solve(tol=1e-11 if fp64 else 1e-10, max_iter=600, restart=80)
+    x, info = P.solve(tol=1e-11, max_iter=600, restart=80)
     x = x.cpu().numpy().astype(np.float64)
     if fp64:
         assert np.max(np.abs(x - R["sol"])) / np.max(np.abs(R["sol"])) < 1e-8
