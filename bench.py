@@ -258,7 +258,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-tol", type=float, default=1e-10,
                     help="GMRES tol; 1e-10 is the largest meeting 1e-5 on emergent I in the Mg II parity case")
-    ap.add_argument("--contraction", default="tf32x3", choices=["tf32x3", "bf16x3"],
+    ap.add_argument("--contraction", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x2"],
                     help="split products of the timed R_II contraction (tf32x3: FP32-level accuracy)")
     ap.add_argument("--workload", default="mgii", choices=["mgii", "mgii_small", "lambda_wide"],
                     help="mgii_small (8 heights) is only for ncu captures of single kernels; lambda_wide "
@@ -302,7 +302,7 @@ def main():
 
     t0 = time.time()
     # bf16x3: a PRD_FP32_BF16X3 context, whose tiles are stored as bf16 hi/lo planes
-    P = PRD(cfg, device=local, precision="fp32_bf16x3" if args.contraction == "bf16x3" else None)
+    P = PRD(cfg, device=local, precision={"bf16x3": "fp32_bf16x3", "bf16x2": "fp32_bf16x2"}.get(args.contraction))
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
@@ -451,6 +451,31 @@ def main():
                            "solve_true_rel_res": info16["true_rel_res"], "rc": info16["rc"],
                            "setup_seconds": setup_b, "tiles": "bf16 hi/lo planes (PRD_FP32_BF16X3)"}
         Pb.close()
+        del Pb
+        # BF16x2: the hi plane alone (half the tile bytes), two products
+        torch.cuda.synchronize()
+        t0 = time.time()
+        Pc = PRD(cfg, device=local, precision="fp32_bf16x2")
+        torch.cuda.synchronize()
+        setup_c = time.time() - t0
+        for _ in range(2):
+            Pc.apply_operator(x, y)
+        Pc.set_profiling(True)
+        for _ in range(3):
+            Pc.apply_operator(x, y)
+        stc = Pc.stage_times()
+        Pc.set_profiling(False)
+        c2_ms = stc["S3_R2_contraction"][0] / max(stc["S3_R2_contraction"][1], 1)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        solc, infoc = Pc.solve(tol=args.solve_tol, max_iter=900, restart=200, check=False)
+        torch.cuda.synchronize()
+        modes["bf16x2"] = {"contraction_ms": c2_ms, "useful_tflops": useful / (c2_ms * 1e-3) / 1e12,
+                           "hbm_frac": tile_bytes / 2 / (c2_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                           "solve_seconds": time.time() - t0, "solve_applies": infoc["iters"],
+                           "solve_true_rel_res": infoc["true_rel_res"], "rc": infoc["rc"],
+                           "setup_seconds": setup_c, "tiles": "bf16 hi plane (PRD_FP32_BF16X2)"}
+        Pc.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -62,8 +62,13 @@ enum {
  * (the same bytes as FP32), so its contraction is BF16x3 on the tensor cores
  * only: PRD_OPT_CONTRACTION = TF32X3 and PRD_OPT_TENSOR_CORES = 0 return
  * PRD_E_ARG.  A PRD_FP32 context can also run BF16x3 (PRD_OPT_CONTRACTION),
- * splitting its FP32 tiles on the fly. */
-enum { PRD_FP64 = 0, PRD_FP32 = 1, PRD_FP32_BF16X3 = 2 };
+ * splitting its FP32 tiles on the fly.
+ * PRD_FP32_BF16X2: the same with the tiles stored as the bf16 hi plane alone
+ * (half the bytes of FP32) and two products per element, hi(B)*hi(A) +
+ * lo(B)*hi(A): the tile's rounding to bf16 (<= 2^-9 relative) is kept, so the
+ * contraction is a ~1e-3-accurate inner operator; prd_solve's FP64 residuals
+ * (FP64 table copy) still fix the solution's accuracy. */
+enum { PRD_FP64 = 0, PRD_FP32 = 1, PRD_FP32_BF16X3 = 2, PRD_FP32_BF16X2 = 3 };
 enum { PRD_TWO_LEVEL = 0, PRD_TWO_TERM = 1 };
 enum { PRD_GRID_LAMBDA = 0, PRD_GRID_X = 1 };
 enum { PRD_MU_GL_HEMISPHERES = 0, PRD_MU_GL_FULL = 1 };
@@ -87,7 +92,7 @@ typedef struct {
 } prd_atom;
 
 /* Create a context on CUDA device `device` with arithmetic `precision`
- * (PRD_FP64, PRD_FP32 or PRD_FP32_BF16X3).  *out receives the handle (NULL
+ * (PRD_FP64, PRD_FP32, PRD_FP32_BF16X3 or PRD_FP32_BF16X2).  *out receives the handle (NULL
  * on failure). */
 int prd_create(prd_ctx** out, int device, int precision);
 /* Free the context and all library-owned device memory.  NULL is a no-op. */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libprd.so")
 PRD_OK = 0
 ERRORS = {-1: "PRD_E_ARG", -2: "PRD_E_STATE", -3: "PRD_E_CUDA", -4: "PRD_E_NOMEM", -5: "PRD_E_NOCONV",
           -6: "PRD_E_BREAKDOWN", -7: "PRD_E_NAN", -8: "PRD_E_TIMEOUT"}
-PRD_FP64, PRD_FP32, PRD_FP32_BF16X3 = 0, 1, 2
+PRD_FP64, PRD_FP32, PRD_FP32_BF16X3, PRD_FP32_BF16X2 = 0, 1, 2, 3
 
 
 class PrdError(RuntimeError):
@@ -130,7 +130,7 @@ class PRD:
         L = lib()
         prec = cfg.get("precision", "fp32") if precision is None else precision
         self.prec = PRD_FP64 if prec in ("fp64", PRD_FP64) else PRD_FP32
-        create = PRD_FP32_BF16X3 if prec == "fp32_bf16x3" else self.prec
+        create = {"fp32_bf16x3": PRD_FP32_BF16X3, "fp32_bf16x2": PRD_FP32_BF16X2}.get(prec, self.prec)
         self.dtype = torch.float64 if self.prec == PRD_FP64 else torch.float32
         self.device = torch.device("cuda", device)
         h = ctypes.c_void_p()

@@ -127,7 +127,7 @@ static int setup(Ctx* c) {
   int rc = build_host_tables(c);
   if (rc) return rc;
   // memory check for the tiles
-  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * c->ld() * c->esz;
+  const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * c->ld() * c->tile_esz();
   size_t fr = 0, tot = 0;
   PRD_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
   if (tile_bytes > fr * 0.9)
@@ -182,8 +182,11 @@ extern "C" {
 int prd_create(prd_ctx** out, int device, int precision) {
   if (!out) return PRD_E_ARG;
   *out = nullptr;
-  if (precision != PRD_FP64 && precision != PRD_FP32 && precision != PRD_FP32_BF16X3) return PRD_E_ARG;
-  const bool bf16x3 = precision == PRD_FP32_BF16X3;
+  if (precision != PRD_FP64 && precision != PRD_FP32 && precision != PRD_FP32_BF16X3 &&
+      precision != PRD_FP32_BF16X2)
+    return PRD_E_ARG;
+  const bool bf16x2 = precision == PRD_FP32_BF16X2;
+  const bool bf16x3 = precision == PRD_FP32_BF16X3 || bf16x2;
   if (bf16x3) precision = PRD_FP32;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -198,7 +201,8 @@ int prd_create(prd_ctx** out, int device, int precision) {
   h->c.esz = precision == PRD_FP64 ? 8 : 4;
   h->c.use_tc = precision == PRD_FP32 ? 1 : 0;   // tcgen05 contraction by default in FP32
   h->c.tc_bf16 = bf16x3 ? 1 : 0;
-  h->c.split_tiles = bf16x3;                    // tiles stored as the bf16 hi/lo planes
+  h->c.split_tiles = bf16x3;                    // tiles stored as bf16 planes (hi and lo, or hi only)
+  h->c.hi_only = bf16x2;
   if (cudaDeviceGetAttribute(&h->c.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete h;
     return PRD_E_CUDA;
@@ -386,7 +390,7 @@ int prd_contraction_work(const prd_ctx* ctx, double* flops, double* bytes) {
   double outs = 0;                                                               // Stokes outputs per class
   for (int k = 0; k < c->ncls; ++k) outs += 4.0 * (c->cout_ptr[k + 1] - c->cout_ptr[k]);
   if (flops) *flops = 2.0 * c->nz * per_tile_out * outs;
-  if (bytes) *bytes = (double)c->nz * c->ncls * per_tile_out * c->esz;
+  if (bytes) *bytes = (double)c->nz * c->ncls * per_tile_out * c->tile_esz();
   return PRD_OK;
 }
 
@@ -649,7 +653,7 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
       return fail(c, PRD_E_ARG, "unknown contraction product");
     if (c->prec != PRD_FP32) return fail(c, PRD_E_ARG, "the split products are for PRD_FP32 contexts");
     if (c->split_tiles && value != PRD_CONTRACTION_BF16X3)
-      return fail(c, PRD_E_ARG, "PRD_FP32_BF16X3 stores its tiles as bf16 planes: BF16x3 products only");
+      return fail(c, PRD_E_ARG, "PRD_FP32_BF16X3/X2 store their tiles as bf16 planes: their own products only");
     c->tc_bf16 = value == PRD_CONTRACTION_BF16X3 ? 1 : 0;
     return PRD_OK;
   }

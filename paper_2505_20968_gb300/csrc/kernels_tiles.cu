@@ -316,12 +316,15 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) r3_kernel(R3Params p, T* o
 // so that the large dispersion parts that cancel between Zeeman components
 // of one J level are summed once, in FP64, before rounding to the storage type.
 // the FP32 value v of a tile entry stored as bf16 planes hi = rn(v), lo = rn(v - hi)
-__device__ __forceinline__ void store_split(__nv_bfloat16* t, int n, int k, int N, float v) {
+__device__ __forceinline__ void store_split(__nv_bfloat16* t, int n, int k, int N, int ld, float v) {
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-  t[tile_off_split(n, k, N, false)] = hi;
-  t[tile_off_split(n, k, N, true)] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  t[tile_off_split(n, k, N, ld, false)] = hi;
+  t[tile_off_split(n, k, N, ld, true)] = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// split: 0 the storage type T (plain or tiled), 1 the bf16 hi and lo planes of
+// BF16x3 contexts (the bytes of an FP32 tile), 2 the hi plane alone (BF16x2:
+// half the bytes; dst is then read as bf16 with tiles of N ld elements)
 template <typename T>
 __global__ void group_split_kernel(const double* __restrict__ src, T* __restrict__ dst, const int* __restrict__ grp,
                                    int ncls, int ntrip, int ngrp, int N, int ld, int tiled, int split) {
@@ -341,13 +344,22 @@ __global__ void group_split_kernel(const double* __restrict__ src, T* __restrict
     cnt[g] += 1;
   }
   for (int g = 0; g < ngrp; ++g) mean[g] = cnt[g] ? mean[g] / cnt[g] : 0.0;
+  if (split == 2) {
+    __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(dst);
+    const size_t oh = tile_off_hi(n, kk, N, ld);
+    for (int g = 0; g < ngrp; ++g) h[((size_t)c * (ngrp + ntrip) + g) * tsz + oh] = __float2bfloat16_rn((float)mean[g]);
+    for (int t = 0; t < ntrip; ++t)
+      h[((size_t)c * (ngrp + ntrip) + ngrp + t) * tsz + oh] =
+          __float2bfloat16_rn((float)(src[((size_t)c * ntrip + t) * rowlen + e] - mean[grp[t]]));
+    return;
+  }
   if (split) {
     // split layout (BF16x3 contexts): T is float, each tile's bytes hold the two bf16 planes
     for (int g = 0; g < ngrp; ++g)
-      store_split(reinterpret_cast<__nv_bfloat16*>(dst + ((size_t)c * (ngrp + ntrip) + g) * tsz), n, kk, N,
+      store_split(reinterpret_cast<__nv_bfloat16*>(dst + ((size_t)c * (ngrp + ntrip) + g) * tsz), n, kk, N, ld,
                   (float)mean[g]);
     for (int t = 0; t < ntrip; ++t)
-      store_split(reinterpret_cast<__nv_bfloat16*>(dst + ((size_t)c * (ngrp + ntrip) + ngrp + t) * tsz), n, kk, N,
+      store_split(reinterpret_cast<__nv_bfloat16*>(dst + ((size_t)c * (ngrp + ntrip) + ngrp + t) * tsz), n, kk, N, ld,
                   (float)(src[((size_t)c * ntrip + t) * rowlen + e] - mean[grp[t]]));
     return;
   }
@@ -431,9 +443,9 @@ int launch_tiles(Ctx* c) {
                                                             (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
                                                             c->tiled(), 0);
     else {
-      group_split_kernel<float><<<sb, 256, 0, c->stream>>>((const double*)scr.p, (float*)c->tiles.p + iz * ztile,
-                                                           (const int*)dgrp.p, c->ncls, c->ntrip, c->ngrp, N, c->ld(),
-                                                           c->tiled(), c->split_tiles ? 1 : 0);
+      group_split_kernel<float><<<sb, 256, 0, c->stream>>>(
+          (const double*)scr.p, (float*)((char*)c->tiles.p + iz * ztile * c->tile_esz()), (const int*)dgrp.p, c->ncls,
+          c->ntrip, c->ngrp, N, c->ld(), c->tiled(), c->hi_only ? 2 : (c->split_tiles ? 1 : 0));
       if (c->has64)
         group_split_kernel<double><<<sb, 256, 0, c->stream>>>(
             (const double*)scr.p, (double*)c->tiles64.p + (size_t)iz * c->ncls * c->ntile() * N * c->ld64(),

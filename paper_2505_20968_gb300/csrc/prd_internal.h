@@ -79,12 +79,13 @@ struct Ctx {
   int ngrp = 1;
   std::vector<int> trip_grp;
   int ntile() const { return ngrp + ntrip; }
-  // row stride of a stored tile: 2N rounded up to 4 elements (16-byte rows for TMA)
   // Stored tile row length: FP32 tiles are kept in the tensor-core layout of
-  // tile_off (K chunks of 16, each a contiguous [n][16] block), FP64 tiles as
-  // plain rows; both padded so every row or chunk starts on 16 bytes.
+  // tile_off (the Re and Im halves each padded to a multiple of 16 columns,
+  // K chunks of 16, each a contiguous [n][16] block), FP64 tiles as plain rows
+  // of 2N rounded up to 4; so every row or chunk starts on 16 bytes.
   bool tiled() const { return prec == PRD_FP32; }
-  int ld() const { return tiled() ? (2 * nnu + 15) / 16 * 16 : (2 * nnu + 3) / 4 * 4; }
+  int np16() const { return (nnu + 15) / 16 * 16; }
+  int ld() const { return tiled() ? 2 * np16() : (2 * nnu + 3) / 4 * 4; }
   int nq3 = 0;                           // R_III incident combos (ku, kv, kl)
   double nu0 = 0;
   std::vector<double> dnuD, vD;          // per z (Hz, km/s)
@@ -175,7 +176,10 @@ struct Ctx {
   int use_tc = 0;
   long long tc_spin = 0;   // poll limit of the contraction's pipeline waits (0: the default)
   int tc_bf16 = 0;         // contraction products: 0 3xTF32, 1 split-BF16 (BF16x3)
-  bool split_tiles = false;   // PRD_FP32_BF16X3: R_II tiles stored as bf16 hi/lo planes (tile_off_split)
+  bool split_tiles = false;   // PRD_FP32_BF16X3/X2: R_II tiles stored as bf16 planes (tile_off_split)
+  bool hi_only = false;       // PRD_FP32_BF16X2: the hi plane only (tile_off_hi), two products
+  // bytes of one stored tile element (tile_bytes / elements of the padded layout)
+  size_t tile_esz() const { return hi_only ? 2 : esz; }
   int tc_stages = 0;       // tile ring depth of the contraction (0: the deepest that fits)
   // stage timing (prd_set_profiling): events on the ctx stream around each stage
   bool prof = false;
@@ -281,29 +285,44 @@ void stage_end(Ctx* c, int stage, cudaEvent_t start);
 void stage_collect(Ctx* c);
 
 // Offset of tile element (row n, column k in [0, 2N): Re | Im halves) within
-// one tile of N rows.  Plain layout: n * ld + k.  Tensor-core layout (FP32):
-// the tile is cut into K chunks of 16 columns; chunk kc is a contiguous block
-// of N rows of 64 bytes, each row's four 16-byte groups permuted by the 64-byte
-// shared-memory swizzle of its row index (group g stored at g ^ ((n >> 1) & 3)),
-// so one bulk copy of N * 64 bytes lands a K step in the operand layout.
+// one tile of N rows.  Plain layout: n * ld + k.  Tensor-core layout (FP32,
+// ld = 2 NP with NP = N rounded up to 16): column k sits at kp = k in the Re
+// half and kp = NP + k - N in the Im half (the columns N..NP-1 of each half
+// stay zero), so no K chunk mixes the halves; the tile is cut into K chunks of
+// 16 columns of kp, chunk kc a contiguous block of N rows of 64 bytes, each
+// row's four 16-byte groups permuted by the 64-byte shared-memory swizzle of
+// its row index (group g stored at g ^ ((n >> 1) & 3)), so one bulk copy of
+// N * 64 bytes lands a K step in the operand layout.
+__host__ __device__ inline int tile_col(int k, int N, int NP) { return k < N ? k : NP + (k - N); }
 __host__ __device__ inline size_t tile_off(int n, int k, int N, int ld, bool tiled) {
   if (!tiled) return (size_t)n * ld + k;
-  const int kc = k >> 4, kl = k & 15;
+  const int kp = tile_col(k, N, ld >> 1);
+  const int kc = kp >> 4, kl = kp & 15;
   return (size_t)kc * N * 16 + (size_t)n * 16 + (size_t)((((kl >> 2) ^ ((n >> 1) & 3)) << 2) | (kl & 3));
 }
 
 // Offset, in bf16 units, of the hi (lo = false) or lo plane entry of tile
 // element (row n, column k) in the split layout of a BF16x3 context: the tile
-// is cut into K chunks of 16 columns like the FP32 tensor-core layout, and
+// is cut into K chunks of 16 padded columns kp like the FP32 tensor-core layout, and
 // chunk kc (N x 64 bytes, the same bytes as FP32) holds two planes of N rows
 // x 32 bytes, hi = rn_bf16(v) then lo = rn_bf16(v - hi) for v the FP32 value;
 // each row's two 16-byte halves are exchanged in rows whose bit 2 is set (the
 // 32-byte shared-memory swizzle), so one bulk copy per plane lands a K step
 // in the operand layout of a kind::f16 MMA.
-__host__ __device__ inline size_t tile_off_split(int n, int k, int N, bool lo) {
-  const int kc = k >> 4, kl = k & 15, g = kl >> 2;
+__host__ __device__ inline size_t tile_off_split(int n, int k, int N, int ld, bool lo) {
+  const int kp = tile_col(k, N, ld >> 1);
+  const int kc = kp >> 4, kl = kp & 15, g = kl >> 2;
   const size_t base = (size_t)kc * N * 32 + (lo ? (size_t)N * 16 : 0);
   return base + (size_t)n * 16 + (size_t)(((g >> 1) ^ ((n >> 2) & 1)) * 8 + (g & 1) * 4 + (kl & 3));
+}
+
+// Offset, in bf16 units, of tile element (row n, column k) in the hi-only
+// layout of a BF16x2 context: the hi plane of tile_off_split alone, K chunk kc
+// a contiguous block of N rows x 32 bytes under the 32-byte swizzle.
+__host__ __device__ inline size_t tile_off_hi(int n, int k, int N, int ld) {
+  const int kp = tile_col(k, N, ld >> 1);
+  const int kc = kp >> 4, kl = kp & 15, g = kl >> 2;
+  return (size_t)kc * N * 16 + (size_t)n * 16 + (size_t)(((g >> 1) ^ ((n >> 2) & 1)) * 8 + (g & 1) * 4 + (kl & 3));
 }
 
 }  // namespace prd

@@ -72,7 +72,8 @@ __host__ __device__ constexpr int cbuf_bytes(int N, bool split) {
   return split ? kBBytes : ((N + 15) / 16 * 16) * 64 + 2 * kBBytes;
 }
 __host__ __device__ constexpr int smem_bytes(int N, int st, bool split) {
-  return st * ((N + 15) / 16 * 16) * 64 + n_cbufs(split) * cbuf_bytes(N, split) + 2 * kYBytes + kISlots * (N + 1) * 16 +
+  return st * ((N + 15) / 16 * 16) * 64 + n_cbufs(split) * cbuf_bytes(N, split) + 2 * kYBytes +
+         kISlots * ((N + 15) / 16 * 16 + 1) * 16 +
          kAuxBytes + 1024;
 }
 constexpr long long kSpin = 1ll << 24;        // bounded waits (default limit of the pipeline waits; drains)
@@ -233,9 +234,12 @@ __device__ __forceinline__ bool gen_all(bool v) {
 // split (tile_off_split), so the producer's two bulk copies per step land the
 // hi and lo planes in the operand layout and the builders never touch the
 // tile; without it the builders split the FP32 tile step into the planes.
-template <bool kBF16, bool kSplit>
+// kHi (with kSplit): the tiles hold the hi plane alone (BF16x2 contexts, half
+// the bytes) and each step is the two products hi*hi + lo(B)*hi.
+template <bool kBF16, bool kSplit, bool kHi>
 __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   static_assert(kBF16 || !kSplit, "split tiles are bf16 planes");
+  static_assert(kSplit || !kHi, "hi-only tiles are split tiles");
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned base, derived by offset so that the compiler keeps the
   // shared address space on every pointer below (plain LDS/STS, no generic access)
@@ -244,7 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int NM = (N + 15) / 16 * 16;             // MMA N: the tile rows n (<= 256)
   const int SA = NM * kKC * 4;                   // one K step of the tile (multiple of 1024 bytes)
   const int nst = p.nst;
-  const int IS = N + 1;                          // float4 stride of a resident I~ slot
+  const int NP = p.ld >> 1;                      // padded half width (N rounded up to 16)
+  const int IS = NP + 1;                         // float4 stride of a resident I~ slot (zero for k >= N)
   unsigned char* cbuf = sm + nst * SA;                             // [buffer] A_lo, B_hi, B_lo
   const int CB = cbuf_bytes(N, kSplit);
   constexpr int NCB = n_cbufs(kSplit);                             // builder ring depth
@@ -272,7 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
   const int* pair_in = pair_ptr + ne_tot + 1;
   const int E = min(kMaxE, cout_ptr[c + 1] - e0);
   const int NCP = ((4 * E + 15) / 16) * 16;      // MMA N (multiple of 16, <= 128)
-  const int KCH = (2 * N + kKC - 1) / kKC;
+  const int KCH = p.ld / kKC;                    // K steps per tile: KH of the Re half, then KH of the Im half
+  const int KH = KCH >> 1;
   const int iters = p.ntile * KCH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gt = threadIdx.x - 64;               // builder thread index (warps 2..)
@@ -333,7 +339,9 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
     if (lane == 0) {
       int it = 0;
       const uint64_t pol_t = policy_evict_first();
-      const uint32_t abytes = (uint32_t)N * kKC * 4;
+      // bytes of one K step of the stored tile: N rows x 64 (FP32, or the two bf16
+      // planes), N x 32 (hi plane alone)
+      const uint32_t abytes = (uint32_t)N * kKC * (kHi ? 2 : 4);
       // stage s = it % nst with phase parity ps = (it / nst) & 1, tile ti = it / KCH and
       // its K step kc, all advanced incrementally (no divisions per step)
       int s = 0, ps = 0, ti = 0, kc = 0;
@@ -341,12 +349,15 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         if (it >= nst && !mbar_wait(&empty[s], ps ^ 1, abort_flag, p.spin)) break;
         // rows n >= N of the stage keep stale data: they only reach output rows
         // that the epilogue never reads
-        const float* src = p.tiles + (size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC;
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(p.tiles) +
+                                   ((size_t)(slab0 + ti) * N * p.ld + (size_t)kc * N * kKC) * (kHi ? 2 : 4);
         mbar_expect_tx(&full[s], abytes);
-        if constexpr (kSplit) {
+        if constexpr (kHi) {
+          bulk_load(sm + s * SA, src, abytes, &full[s], pol_t);          // hi plane at the stage
+        } else if constexpr (kSplit) {
           // hi plane (N x 32 bytes) at the stage, lo plane at its second half
           bulk_load(sm + s * SA, src, abytes / 2, &full[s], pol_t);
-          bulk_load(sm + s * SA + SA / 2, src + (size_t)N * kKC / 2, abytes / 2, &full[s], pol_t);
+          bulk_load(sm + s * SA + SA / 2, src + abytes / 2, abytes / 2, &full[s], pol_t);
         } else {
           bulk_load(sm + s * SA, src, abytes, &full[s], pol_t);
         }
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           unsigned char* Al = Ah + SA / 2;
           mma_bf16(tmem, sdesc32(Bhi), sdesc32(Ah), idesc16, it > 0 ? 1u : 0u);
           mma_bf16(tmem, sdesc32(Blo), sdesc32(Ah), idesc16, 1u);
-          mma_bf16(tmem, sdesc32(Bhi), sdesc32(Al), idesc16, 1u);
+          if constexpr (!kHi) mma_bf16(tmem, sdesc32(Bhi), sdesc32(Al), idesc16, 1u);
         } else {
           for (int ks = 0; ks < 2; ++ks) {
             const int o = ks * 32;                 // 8 fp32 of K per MMA
@@ -442,22 +453,37 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           ypre[r] = *((const float4*)(p.Y + ((ybase + (q >> 3)) * p.ntile + ti) * 32) + (q & 7));
       }
     };
-    // fast path: each lane keeps its items' Y rows and I~ slot offsets for the tile
-    // in registers.  I~ does not depend on the tile: column k of the Re half and
-    // column N + k of the Im half both read I~(k).  So the I~ of the CTA's staged
-    // incident directions is loaded into shared memory once, here, while the
-    // producer already streams the first tile steps.
-    float4 yreg[kItems][2][2];
+    // fast path: each lane keeps, per item and pair, the four coefficients of the
+    // current half (Re Y_ij for the Re half, -Im Y_ij for the Im half) and the I~
+    // slot offset in registers.  I~ does not depend on the tile: column k of either
+    // half reads I~(k).  So the I~ of the CTA's staged incident directions is loaded
+    // into shared memory once, here (zero for N <= k < NP, so the padded columns
+    // need no test), while the producer already streams the first tile steps.
+    float4 ycf[kItems][2];
     int soff[kItems][2];
     load_y(0);
     {
       const float4* Icz4 = reinterpret_cast<const float4*>(Icz);
-      for (int idx = gt; idx < ns * N; idx += kGen) {
-        const int sl = idx / N, k = idx - sl * N;
-        Ir[sl * IS + k] = Icz4[(size_t)slot_dir[sl] * N + k];
+      for (int idx = gt; idx < ns * NP; idx += kGen) {
+        const int sl = idx / NP, k = idx - sl * NP;
+        Ir[sl * IS + k] = k < N ? Icz4[(size_t)slot_dir[sl] * N + k] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       gen_sync();
     }
+    // the coefficients of item r's pairs for the Re (im = false) or Im half of the tile in Ysb
+    auto load_cf = [&](const float* Ysb, bool im) {
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const int npr = it_pb[r] - it_pa[r], i = it_row[r] & 3;
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp)
+          if (pp < npr) {
+            const float4* y4 = reinterpret_cast<const float4*>(Ysb) + (it_pa[r] + pp) * 8 + i * 2;
+            const float4 ya = y4[0], yb = y4[1];
+            ycf[r][pp] = im ? make_float4(-ya.y, -ya.w, -yb.y, -yb.w) : make_float4(ya.x, ya.z, yb.x, yb.z);
+          }
+      }
+    };
     bool aborted = false;
     int s = 0, ps = 0, ti = 0, kc = 0;           // it % nst, (it / nst) & 1, it / KCH, it % KCH
     for (int it = 0; it < iters;
@@ -476,21 +502,18 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
         }
         got = gen_all(got);
         if (got && fast) {
+          load_cf(Ysb, false);
 #pragma unroll
           for (int r = 0; r < kItems; ++r) {
-            const int npr = it_pb[r] - it_pa[r], i = it_row[r] & 3;
+            const int npr = it_pb[r] - it_pa[r];
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-              if (pp < npr) {
-                const float4* y4 = reinterpret_cast<const float4*>(Ysb) + (it_pa[r] + pp) * 8 + i * 2;
-                yreg[r][pp][0] = y4[0];
-                yreg[r][pp][1] = y4[1];
-                soff[r][pp] = pslot[it_pa[r] + pp] * IS;
-              }
-            }
+            for (int pp = 0; pp < 2; ++pp)
+              if (pp < npr) soff[r][pp] = pslot[it_pa[r] + pp] * IS;
           }
         }
         if (ti + 1 < p.ntile) load_y(ti + 1);
+      } else if (kc == KH && got && fast) {
+        load_cf(Ysb, true);                        // the Im half of the tile begins
       }
       if (!got) {
         aborted = true;
@@ -532,50 +555,21 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       for (int r = 0; r < kItems; ++r) {
         const int row = it_row[r], kq = it_kq[r], i = row & 3;
         if (row >= NCP) continue;
-        const int kb = kc * kKC + kq * 4;
+        // k of this step within its half (uniform over the CTA: no step mixes the halves)
+        const bool im = kc >= KH;
+        const int kb = (im ? kc - KH : kc) * kKC + kq * 4;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (fast) {
           const int npr = it_pb[r] - it_pa[r];
-          // a 4-column chunk lies in the Re half (k < N), the Im half, or across
-          // k = N; the first two are uniform over the warp (same chunk kq)
-          if (kb + 3 < N) {
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-              if (pp < npr) {
-                const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
+          for (int pp = 0; pp < 2; ++pp) {
+            if (pp < npr) {
+              const float4 cf = ycf[r][pp];
+              const float4* ip = Ir + soff[r][pp] + kb;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const float4 iv = Ir[soff[r][pp] + kb + q];
-                  z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
-                }
-              }
-            }
-          } else if (kb >= N) {
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-              if (pp < npr) {
-                const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  // past 2N (last chunk of a ragged tile) the read is clamped into the
-                  // slot and the column zeroed below
-                  const float4 iv = Ir[soff[r][pp] + min(kb + q - N, N - 1)];
-                  z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
-                }
-              }
-            }
-          } else {
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-              if (pp < npr) {
-                const float4 ya = yreg[r][pp][0], yb = yreg[r][pp][1];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const int k = kb + q;
-                  const float4 iv = Ir[soff[r][pp] + (k < N ? k : min(k - N, N - 1))];
-                  if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
-                  else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
-                }
+              for (int q = 0; q < 4; ++q) {
+                const float4 iv = ip[q];
+                z[q] += cf.x * iv.x + cf.y * iv.y + cf.z * iv.z + cf.w * iv.w;
               }
             }
           }
@@ -583,22 +577,18 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
           for (int pl = it_pa[r]; pl < it_pb[r]; ++pl) {
             const float* y = y_in_smem ? Ysb + pl * 32 : p.Y + ((ybase + pl) * p.ntile + ti) * 32;
             const float4 ya = *(const float4*)(y + i * 8), yb = *(const float4*)(y + i * 8 + 4);
+            const float4 cf = im ? make_float4(-ya.y, -ya.w, -yb.y, -yb.w) : make_float4(ya.x, ya.z, yb.x, yb.z);
             const int sl = (pl < kYPairs) ? pslot[pl] : -1;
             const float4* ir = reinterpret_cast<const float4*>(Icz) + (size_t)pair_in[pp0 + pl] * N;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int k = kb + q;
-              if (k >= 2 * N) continue;
-              const int km = k < N ? k : k - N;
-              const float4 iv = sl >= 0 ? Ir[sl * IS + km] : ir[km];
-              if (k < N) z[q] += ya.x * iv.x + ya.z * iv.y + yb.x * iv.z + yb.z * iv.w;
-              else z[q] -= ya.y * iv.x + ya.w * iv.y + yb.y * iv.z + yb.w * iv.w;
+              if (sl < 0 && k >= N) continue;                 // padded column (zero in the staged slots)
+              const float4 iv = sl >= 0 ? Ir[sl * IS + k] : ir[k];
+              z[q] += cf.x * iv.x + cf.y * iv.y + cf.z * iv.z + cf.w * iv.w;
             }
           }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (kb + q >= 2 * N) z[q] = 0.f;                  // columns past 2N (zero tile columns)
         if constexpr (kBF16) {
           uint2 hi, lo;
           bf16_split4(make_float4(z[0], z[1], z[2], z[3]), hi, lo);
@@ -675,7 +665,7 @@ int r2_tc_prepare(Ctx* c) {
   if (c->prec != PRD_FP32) return PRD_OK;
   if (!c->tiled() || r2_tc_stages(c->nnu, false) < 2)
     return fail(c, PRD_E_ARG, "tensor-core contraction needs FP32 tiles and N small enough for two tile stages "
-                              "beside the resident I~ (N <= 232)");
+                              "beside the resident I~ (N <= 224)");
   // work items: every class split into chunks of <= kMaxE output directions
   std::vector<int> work;
   for (int k = 0; k < c->ncls; ++k)
@@ -709,9 +699,10 @@ int r2_tc_launch(Ctx* c, const float* Ic, float* eb) {
     return PRD_OK;
   };
   int rc;
-  if (c->split_tiles) rc = go(tc::r2_tc_kernel<true, true>);
-  else if (c->tc_bf16) rc = go(tc::r2_tc_kernel<true, false>);
-  else rc = go(tc::r2_tc_kernel<false, false>);
+  if (c->hi_only) rc = go(tc::r2_tc_kernel<true, true, true>);
+  else if (c->split_tiles) rc = go(tc::r2_tc_kernel<true, true, false>);
+  else if (c->tc_bf16) rc = go(tc::r2_tc_kernel<true, false, false>);
+  else rc = go(tc::r2_tc_kernel<false, false, false>);
   if (rc) return rc;
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;

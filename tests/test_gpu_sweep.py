@@ -2,8 +2,12 @@
 even frequency counts) against the one-thread-per-ray sweep.
 
 Both run the same per-step arithmetic on the same inputs, the staged one
-reading them from shared memory after bulk copies, so Lambda eps, the
-operator y = x - Lambda Sigma x and the right-hand side must agree bit for bit:
+reading them from shared memory after bulk copies, so Lambda eps and the
+right-hand side must agree bit for bit, and the operator y = x - Lambda Sigma x
+(fused subtraction) to the rounding of Sigma's floating-point atomics, whose
+order changes from apply to apply: ~1e-7 of the maximum in FP32, which
+DELOPAR's opposite-signed parabolic weights amplify (measured 2.3e-6), so
+1e-5 in FP32 and 1e-13 in FP64:
 for FP32 (Mg II, 26 frequencies, one ragged block of rays), FP64 (two-level
 slab, 130 frequencies: one full block of 128 rays and a ragged one of 2), and
 under DELOPAR.  Against the oracle the staged sweep is covered by the Mg II
@@ -41,7 +45,11 @@ def test_staged_sweep_equals_per_ray_sweep(name, formal):
         b = P.rhs().clone()
         P.device_status()
         out[staged] = (lam, y, b)
-    for a, b in zip(out[1], out[0]):
-        assert bool(torch.isfinite(a).all())
-        assert torch.equal(a, b), float((a - b).abs().max())
+    tol = 1e-5 if prec == "fp32" else 1e-13
+    for what, a, b in zip(("Lambda", "operator", "rhs"), out[1], out[0]):
+        assert bool(torch.isfinite(a).all()), what
+        if what == "operator":
+            assert float((a - b).abs().max()) <= tol * float(b.abs().max()), what
+        else:
+            assert torch.equal(a, b), (what, float((a - b).abs().max()))
     P.close()

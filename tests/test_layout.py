@@ -1,12 +1,15 @@
 """The FP32 tile layout of the tensor-core contraction (tile_off in
-csrc/prd_internal.h), checked on the host: within a tile of N rows and ld
-columns it is a bijection onto [0, N ld); every 16-column K step is one
-contiguous block of N x 64 bytes (one bulk copy, 16-byte aligned start and
-size); and inside a block each row's 64 bytes are permuted by the 64-byte
-shared-memory swizzle, written here in its own form (byte address bits [4:5]
-XOR bits [7:8]), which is the layout the MMA descriptors declare.  The split
-layout of BF16x3 contexts (tile_off_split: bf16 hi and lo planes in the same
-bytes) is checked the same way against the 32-byte swizzle."""
+csrc/prd_internal.h), checked on the host: the Re and Im halves each padded
+to NP = N rounded up to 16 columns (ld = 2 NP); within a tile of N rows it is
+injective from the 2N columns into [0, N ld), and every one of them lands in
+the K step of its padded column (kp = k, or NP + k - N in the Im half), so no
+K step mixes the halves; every K step is one contiguous block of N x 64 bytes
+(one bulk copy, 16-byte aligned start and size); and inside a block each
+row's 64 bytes are permuted by the 64-byte shared-memory swizzle, written here
+in its own form (byte address bits [4:5] XOR bits [7:8]), which is the layout
+the MMA descriptors declare.  The split layout of BF16x3 contexts
+(tile_off_split: bf16 hi and lo planes in the same bytes) is checked the same
+way against the 32-byte swizzle."""
 import os
 import shutil
 import subprocess
@@ -22,39 +25,32 @@ SRC = r'''
 int main() {
   const int Ns[] = {1, 7, 8, 9, 150, 200, 208, 255, 256};
   for (int N : Ns) {
-    const int ld = (2 * N + 15) / 16 * 16;
+    const int NP = (N + 15) / 16 * 16, ld = 2 * NP;
     std::vector<char> seen((size_t)N * ld, 0);
     for (int n = 0; n < N; ++n)
-      for (int k = 0; k < ld; ++k) {
+      for (int k = 0; k < 2 * N; ++k) {
         const size_t off = prd::tile_off(n, k, N, ld, true);
         if (off >= (size_t)N * ld || seen[off]) { std::printf("N=%d n=%d k=%d: off %zu\n", N, n, k, off); return 1; }
         seen[off] = 1;
-        const int kc = k / 16, kl = k % 16;
+        const int kp = k < N ? k : NP + k - N;
+        const int kc = kp / 16, kl = kp % 16;
         const size_t base = (size_t)kc * N * 16;            // floats
         if (off < base || off >= base + (size_t)N * 16) { std::printf("N=%d: step %d not contiguous\n", N, kc); return 2; }
+        if ((kc < NP / 16) != (k < N)) { std::printf("N=%d k=%d: step mixes the halves\n", N, k); return 9; }
         const unsigned lin = (unsigned)(n * 64 + kl * 4);   // bytes, unswizzled row-major [n][16]
         const unsigned swz = lin ^ (((lin >> 7) & 3u) << 4);
         if ((off - base) * 4 != swz) { std::printf("N=%d n=%d k=%d: swizzle\n", N, n, k); return 3; }
+        for (int lo = 0; lo < 2; ++lo) {
+          const size_t o2 = prd::tile_off_split(n, k, N, ld, lo != 0);
+          const size_t plane = (size_t)kc * N * 32 + (size_t)lo * N * 16;   // bf16 units
+          if (o2 < plane || o2 >= plane + (size_t)N * 16) { std::printf("split N=%d: plane\n", N); return 7; }
+          const unsigned l2 = (unsigned)(n * 32 + kl * 2);
+          const unsigned s2 = l2 ^ (((l2 >> 7) & 1u) << 4);
+          if ((o2 - plane) * 2 != s2) { std::printf("split N=%d n=%d k=%d: swizzle\n", N, n, k); return 8; }
+        }
       }
     if (((size_t)N * ld * 4) % 64 || ((size_t)N * 64) % 16) { std::printf("N=%d: alignment\n", N); return 4; }
     if (prd::tile_off(N - 1, 2 * N - 1, N, 2 * N + 4, false) != (size_t)(N - 1) * (2 * N + 4) + 2 * N - 1) return 5;
-    // split layout (bf16 planes): a bijection onto the same bytes; each K step
-    // one block of N x 64 bytes, hi plane first; rows of 32 bytes under the
-    // 32-byte swizzle (byte address bit 4 XOR bit 7)
-    std::vector<char> seen2((size_t)N * ld * 2, 0);
-    for (int n = 0; n < N; ++n)
-      for (int k = 0; k < ld; ++k)
-        for (int lo = 0; lo < 2; ++lo) {
-          const size_t off = prd::tile_off_split(n, k, N, lo != 0);
-          if (off >= (size_t)N * ld * 2 || seen2[off]) { std::printf("split N=%d n=%d k=%d\n", N, n, k); return 6; }
-          seen2[off] = 1;
-          const int kc = k / 16, kl = k % 16;
-          const size_t plane = (size_t)kc * N * 32 + (size_t)lo * N * 16;   // bf16 units
-          if (off < plane || off >= plane + (size_t)N * 16) { std::printf("split N=%d: plane\n", N); return 7; }
-          const unsigned lin = (unsigned)(n * 32 + kl * 2);
-          const unsigned swz = lin ^ (((lin >> 7) & 1u) << 4);
-          if ((off - plane) * 2 != swz) { std::printf("split N=%d n=%d k=%d: swizzle\n", N, n, k); return 8; }
-        }
   }
   std::printf("ok\n");
   return 0;
