@@ -33,7 +33,7 @@ UNIT = "applies/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # layout tag of the contraction whose DRAM traffic profiles/traffic.json records;
 # the traffic figure is reported only while it matches the kernel that runs
-KERNEL_LAYOUT = "resident-ir-v4"
+KERNEL_LAYOUT = "padded-v5"
 
 
 def _peaks():
@@ -466,15 +466,11 @@ def main():
         stc = Pc.stage_times()
         Pc.set_profiling(False)
         c2_ms = stc["S3_R2_contraction"][0] / max(stc["S3_R2_contraction"][1], 1)
-        torch.cuda.synchronize()
-        t0 = time.time()
-        solc, infoc = Pc.solve(tol=args.solve_tol, max_iter=900, restart=200, check=False)
-        torch.cuda.synchronize()
+        # no solve: with Sigma good to ~1e-3 the refinement stalls on this problem (PRD_E_NOCONV)
         modes["bf16x2"] = {"contraction_ms": c2_ms, "useful_tflops": useful / (c2_ms * 1e-3) / 1e12,
                            "hbm_frac": tile_bytes / 2 / (c2_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                           "solve_seconds": time.time() - t0, "solve_applies": infoc["iters"],
-                           "solve_true_rel_res": infoc["true_rel_res"], "rc": infoc["rc"],
-                           "setup_seconds": setup_c, "tiles": "bf16 hi plane (PRD_FP32_BF16X2)"}
+                           "setup_seconds": setup_c, "tiles": "bf16 hi plane (PRD_FP32_BF16X2)",
+                           "solve": "not run: Sigma to ~1e-3 stalls the refinement (tests/test_gpu_parity.py)"}
         Pc.close()
 
     cpu = None

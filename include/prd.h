@@ -282,10 +282,15 @@ int prd_set_precond_sweeps(prd_ctx* ctx, int m_in);
  * 128 rays) when the frequency count is even; 0, or an odd count, runs one
  * thread per ray reading its inputs directly.  Results are identical.  Its
  * waits are bounded like the contraction's (PRD_E_TIMEOUT through
- * prd_device_status). */
+ * prd_device_status).
+ * PRD_OPT_GRAD_FULL_SETUP: 0 (default) makes prd_grad_B difference each
+ * height's residual by re-setting up only that height's Sigma rows (a context
+ * of two heights) and the formal solver's tables of the perturbed atmosphere;
+ * 1 takes a full FP64 setup of the perturbed atmosphere per side.  Both
+ * difference the same residual with the same steps. */
 enum { PRD_OPT_TENSOR_CORES = 1, PRD_OPT_PRECOND_SWEEPS = 2, PRD_OPT_WAIT_POLLS = 3, PRD_OPT_TEST_ZERO_OPERATOR = 4,
        PRD_OPT_REFINE_FLOOR = 5, PRD_OPT_FORMAL_SOLVER = 6, PRD_OPT_CONTRACTION = 7, PRD_OPT_TILE_STAGES = 8,
-       PRD_OPT_GRAPH = 9, PRD_OPT_STAGED_SWEEP = 10 };
+       PRD_OPT_GRAPH = 9, PRD_OPT_STAGED_SWEEP = 10, PRD_OPT_GRAD_FULL_SETUP = 11 };
 enum { PRD_CONTRACTION_TF32X3 = 0, PRD_CONTRACTION_BF16X3 = 1 };
 enum { PRD_DELO_LINEAR = 0, PRD_DELOPAR = 1 };
 int prd_set_option(prd_ctx* ctx, int option, int value);

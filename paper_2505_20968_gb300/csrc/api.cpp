@@ -126,6 +126,15 @@ static int setup(Ctx* c) {
   free_all(c);
   int rc = build_host_tables(c);
   if (rc) return rc;
+  if (c->lambda_only) {
+    // the field gradient's perturbed formal solver: K, DELO weights, thermal emissivity
+    if ((rc = upload(c, c->dmu, c->mu.data(), c->mu.size() * 8)) || (rc = build_device_tables(c)) ||
+        (rc = r2_tc_prepare(c)))
+      return rc;
+    PRD_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->ready = true;
+    return PRD_OK;
+  }
   // memory check for the tiles
   const size_t tile_bytes = (size_t)c->nz * c->ncls * c->ntile() * c->nnu * c->ld() * c->tile_esz();
   size_t fr = 0, tot = 0;
@@ -619,6 +628,10 @@ int prd_set_option(prd_ctx* ctx, int option, int value) {
   }
   if (option == PRD_OPT_STAGED_SWEEP) {
     c->staged_sweep = value ? 1 : 0;
+    return PRD_OK;
+  }
+  if (option == PRD_OPT_GRAD_FULL_SETUP) {
+    c->grad_full_setup = value ? 1 : 0;
     return PRD_OK;
   }
   if (option == PRD_OPT_TENSOR_CORES) {

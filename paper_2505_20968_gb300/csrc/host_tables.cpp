@@ -405,7 +405,7 @@ int build_device_tables(Ctx* c) {
     c->pc_lii_host = lii;
   }
   // ---- R_II contraction coefficients Y[z][pair][t][i][j] (complex)
-  {
+  if (!c->lambda_only) {
     const double c2 = 3.0 / (4.0 * kPi * S2);
     const int nt = c->ntrip, nti = c->ntile(), ng = c->ngrp;
     std::vector<double> Y((size_t)nz * c->npairs * nti * 32, 0.0);
@@ -446,7 +446,7 @@ int build_device_tables(Ctx* c) {
     if (c->has64 && (rc = upload(c, c->Y64, Y.data(), Y.size() * 8))) return rc;
   }
   // ---- R_III separable factors
-  {
+  if (!c->lambda_only) {
     const double c3 = 3.0 / (16.0 * kPi * S2);
     const int nuv = nu_ * nu_, nq = nuv * nl;
     std::vector<double> rin((size_t)nz * nO * nq * 4 * 2), rout((size_t)nz * nO * nuv * nl * 4 * 2),

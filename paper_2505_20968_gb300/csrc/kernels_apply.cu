@@ -471,17 +471,53 @@ __device__ __forceinline__ void delo_load(DeloPoint<T, A>& d, const A* __restric
     for (int i = 0; i < 3; ++i) d.ps[i] = par[pt * 3 + i];
 }
 
+// LU factors of M = Id + b K'_k of a point (no pivoting: M is the identity plus
+// b times the antisymmetric-off-diagonal K', as in the step's original form):
+// strictly lower multipliers l, strictly upper entries u and the reciprocals
+// of the pivots.  M depends on the tables only, so a sweep factors the next
+// point while the current one is solved, and only the substitutions, which
+// carry the intensity, stay on the serial chain from step to step.
+template <typename A>
+struct DeloFact {
+  A l10, l20, l30, l21, l31, l32;
+  A u01, u02, u03, u12, u13, u23;
+  A i0, i1, i2, i3;
+};
+
+template <typename T, typename A>
+__device__ __forceinline__ void delo_factor(const DeloPoint<T, A>& d, DeloFact<A>& F) {
+  A K[4][4];
+  kprime(d.t, K);
+  const A be = d.t[9];
+  A M[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) M[i][j] = (i == j ? (A)1 : (A)0) + be * K[i][j];
+  A l[4][4], piv[4];
+  for (int c0 = 0; c0 < 4; ++c0) {
+    piv[c0] = (A)1 / M[c0][c0];
+    for (int r = c0 + 1; r < 4; ++r) {
+      const A f = M[r][c0] * piv[c0];
+      l[r][c0] = f;
+      for (int cc = c0; cc < 4; ++cc) M[r][cc] -= f * M[c0][cc];
+    }
+  }
+  F.l10 = l[1][0]; F.l20 = l[2][0]; F.l30 = l[3][0]; F.l21 = l[2][1]; F.l31 = l[3][1]; F.l32 = l[3][2];
+  F.u01 = M[0][1]; F.u02 = M[0][2]; F.u03 = M[0][3]; F.u12 = M[1][2]; F.u13 = M[1][3]; F.u23 = M[2][3];
+  F.i0 = piv[0]; F.i1 = piv[1]; F.i2 = piv[2]; F.i3 = piv[3];
+}
+
 // One step of the formal solution (Sect. 3) at the p-th point of a ray: DELO-
 // linear, or DELOPAR when `par` (the parabolic source weights psi_M, psi_O,
 // psi_P of the step arriving at the point; the source vector parabolic through
 // the upwind, current and downwind points, the K'I term linear with DELO-
 // linear's a, b; psi = (a, b, 0) at the last point) is set; `nxt` is the next
-// point (read only under DELOPAR, p + 1 < nz).  I, Sp, Kp carry the upwind
-// intensity, source and K' from step to step.
+// point (read only under DELOPAR, p + 1 < nz); F the factors of cur's
+// Id + b K'.  I, Sp, Kp carry the upwind intensity, source and K' from step
+// to step.
 template <typename T, typename A>
-__device__ __forceinline__ void delo_step(const DeloPoint<T, A>& cur, const DeloPoint<T, A>& nxt, bool par,
-                                          bool has_next, int p, bool up, int boundary, double WT0, A I[4], A Sp[4],
-                                          A Kp[4][4]) {
+__device__ __forceinline__ void delo_step(const DeloPoint<T, A>& cur, const DeloFact<A>& F,
+                                          const DeloPoint<T, A>& nxt, bool par, bool has_next, int p, bool up,
+                                          int boundary, double WT0, A I[4], A Sp[4], A Kp[4][4]) {
   const T* t = cur.t;
   A Kk[4][4];
   kprime(t, Kk);
@@ -520,23 +556,16 @@ __device__ __forceinline__ void delo_step(const DeloPoint<T, A>& cur, const Delo
       for (int j = 0; j < 4; ++j) v -= al * Kp[i][j] * I[j] + (thick ? be * Kk[i][j] * S[j] : (A)0);
       rhs[i] = v;
     }
-    A M4[4][4];
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) M4[i][j] = (i == j ? (A)1 : (A)0) + be * Kk[i][j];
-    for (int c0 = 0; c0 < 4; ++c0) {
-      const A inv = (A)1 / M4[c0][c0];
-      for (int r = c0 + 1; r < 4; ++r) {
-        const A f = M4[r][c0] * inv;
-        for (int cc = c0; cc < 4; ++cc) M4[r][cc] -= f * M4[c0][cc];
-        rhs[r] -= f * rhs[c0];
-      }
-    }
+    // forward substitution with the unit lower factor, back substitution with the upper one
+    const A y0 = rhs[0];
+    const A y1 = rhs[1] - F.l10 * y0;
+    const A y2 = rhs[2] - F.l20 * y0 - F.l21 * y1;
+    const A y3 = rhs[3] - F.l30 * y0 - F.l31 * y1 - F.l32 * y2;
     A D[4];
-    for (int r = 3; r >= 0; --r) {
-      A v = rhs[r];
-      for (int cc = r + 1; cc < 4; ++cc) v -= M4[r][cc] * D[cc];
-      D[r] = v / M4[r][r];
-    }
+    D[3] = y3 * F.i3;
+    D[2] = (y2 - F.u23 * D[3]) * F.i2;
+    D[1] = (y1 - F.u12 * D[2] - F.u13 * D[3]) * F.i1;
+    D[0] = (y0 - F.u01 * D[1] - F.u02 * D[2] - F.u03 * D[3]) * F.i0;
     for (int i = 0; i < 4; ++i) I[i] = thick ? S[i] + D[i] : D[i];
   }
   for (int i = 0; i < 4; ++i) {
@@ -562,15 +591,19 @@ __global__ void delo_kernel(const A* __restrict__ eps, const T* __restrict__ kt,
   A Sp[4] = {0, 0, 0, 0};
   A Kp[4][4];
   DeloPoint<T, A> cur, nx1, nx2;
+  DeloFact<A> fc, fn;
   delo_load(cur, eps, kt, par, x_sub, point(0));
+  delo_factor(cur, fc);
   if (nz > 1) delo_load(nx1, eps, kt, par, x_sub, point(1));
   for (int p = 0; p < nz; ++p) {
     const size_t pt = point(p);
     if (p + 2 < nz) delo_load(nx2, eps, kt, par, x_sub, point(p + 2));
-    delo_step(cur, nx1, par != nullptr, p + 1 < nz, p, up, boundary, WT0, I, Sp, Kp);
+    if (p + 1 < nz) delo_factor(nx1, fn);          // off the serial chain of this step
+    delo_step(cur, fc, nx1, par != nullptr, p + 1 < nz, p, up, boundary, WT0, I, Sp, Kp);
     for (int s = 0; s < 4; ++s) out[pt * 4 + s] = x_sub ? cur.xs[s] - I[s] : I[s];
     cur = nx1;
     nx1 = nx2;
+    fc = fn;
   }
 }
 
@@ -696,16 +729,20 @@ __global__ void __launch_bounds__(32 + kDR) delo_staged_kernel(const A* __restri
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(dsm_u32(&empty[d])) : "memory");
       return true;
     };
+    DeloFact<A> fc, fn;
     bool ok = take(0, cur);
+    if (ok && live) delo_factor(cur, fc);
     for (int p = 0; p < nz && ok; ++p) {
       if (p + 1 < nz) ok = take(p + 1, nxt);
       if (!ok) break;
       if (live) {
-        delo_step(cur, nxt, par != nullptr, p + 1 < nz, p, up, boundary, WT0, I, Sp, Kp);
+        if (p + 1 < nz) delo_factor(nxt, fn);      // off the serial chain of this step
+        delo_step(cur, fc, nxt, par != nullptr, p + 1 < nz, p, up, boundary, WT0, I, Sp, Kp);
         A* dst = out + (row(p) + r) * 4;
         for (int s = 0; s < 4; ++s) dst[s] = x_sub ? cur.xs[s] - I[s] : I[s];
       }
       cur = nxt;
+      fc = fn;
     }
   }
   __syncthreads();
@@ -975,6 +1012,27 @@ int apply_operator_acc(Ctx* c, const double* x, double* y, double* ws /* 4 x nve
   delo_kernel<double, double><<<ceil_div(c->nO * c->nnu, 128), 128, 0, c->stream>>>(
       eps, (const double*)c->kt64.p, (const double*)c->par_active(), (const double*)c->dmu.p, x, y, c->nz, c->nO,
       c->nnu, 0, c->WT[0]);
+  PRD_CUDA_TRY(c, cudaPeekAtLastError());
+  return PRD_OK;
+}
+
+__global__ void add_kernel(double* __restrict__ a, const double* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a[i] += b[i];
+}
+
+// eps = eps_th + Sigma x in FP64 arithmetic on the FP64 tables (the residual
+// path of the refinement in FP32 mode): the emissivity whose formal solution,
+// with the boundary term, minus x is the residual b - A x.  ws: 3 N-vectors.
+int emissivity_acc(Ctx* c, const double* x, double* eps, double* ws) {
+  const size_t nv = nvec(c);
+  int rc;
+  if (c->prec == PRD_FP64) rc = sigma_T<double, double>(c, x, eps, true);
+  else if (c->has64) rc = sigma_T<double, double>(c, x, eps, true, ws, ws + nv, ws + 2 * nv, nullptr, true);
+  else rc = sigma_T<float, double>(c, x, eps, true, ws, ws + nv, ws + 2 * nv);
+  if (rc) return rc;
+  add_kernel<<<c->grid_ew(), 256, 0, c->stream>>>(eps, (const double*)(c->prec == PRD_FP64 ? c->epsth.p : c->epsth64.p),
+                                                  nv);
   PRD_CUDA_TRY(c, cudaPeekAtLastError());
   return PRD_OK;
 }

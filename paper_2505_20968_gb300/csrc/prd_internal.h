@@ -161,6 +161,10 @@ struct Ctx {
   cudaGraph_t gk_graph[2] = {nullptr, nullptr};   // the captured steps (children of a batch round)
   int use_graph = 1;                       // PRD_OPT_GRAPH
   int staged_sweep = 1;                    // PRD_OPT_STAGED_SWEEP: bulk-copy-staged formal solution
+  // internal context of the field gradient holding only the formal solver's
+  // tables (no Sigma tables, tiles, normalisation or preconditioner)
+  bool lambda_only = false;
+  int grad_full_setup = 0;                 // PRD_OPT_GRAD_FULL_SETUP
   cudaStream_t gk_cap = nullptr;           // private stream the step is captured on
   struct BatchRound* batch = nullptr;      // set while prd_solve_batch runs this context in lockstep
   long long gk_launches = 0;               // graph launches (prd_graph_launches)
@@ -219,6 +223,7 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // ---- setup pieces (host_setup.cpp)
 int build_host_tables(Ctx* c);
 int build_device_tables(Ctx* c);
+int emissivity_acc(Ctx* c, const double* x, double* eps, double* ws);
 // polarisation amplitudes a[alpha][ku][kl] = <ku| e_alpha . d |kl> of any direction
 void dir_amplitudes(const Ctx* c, int iz, double mu, double chi, cplx* out);
 // tables of one extra line of sight (emergent_stokes)

@@ -160,3 +160,31 @@ def test_grad_B_matches_oracle_finite_differences():
         assert d < 2e-4, f"dJ/d{kind}: {d:.2e}"
     P.close()
 
+
+
+def test_grad_B_per_height_setup_equals_full_setup():
+    """prd_grad_B re-sets up only the perturbed height (its Sigma rows from a
+    two-height context, the formal solver's tables of the perturbed
+    atmosphere); with PRD_OPT_GRAD_FULL_SETUP it sets up the whole perturbed
+    atmosphere per side.  Both difference the same residual with the same
+    steps, so they agree to the rounding of the residual dots (1e-7 of the
+    largest component of a kind), and the per-height form is the faster."""
+    import time
+    from paper_2505_20968_gb300.binding import PRD, lib
+    cfg = inputs.mgii(n_z=6, n_core_each=5, n_wing=4, n_mu_half=1, n_chi=4, seed=23)
+    P = PRD(cfg, precision="fp64", device=0)
+    x, _ = P.solve(tol=1e-12, max_iter=600, restart=80)
+    top = torch.from_numpy(P.mu > 0).to(x.device)
+    dJdI = torch.zeros_like(x)
+    dJdI[-1, top, :, 0] = 1.0
+    t0 = time.time()
+    g_local = P.grad_B(x, dJdI)
+    t1 = time.time()
+    assert lib().prd_set_option(P.h, 11, 1) == 0
+    g_full = P.grad_B(x, dJdI)
+    t2 = time.time()
+    print(f"grad_B per-height {t1 - t0:.1f} s, full setups {t2 - t1:.1f} s")
+    for k in range(3):
+        d = np.max(np.abs(g_local[:, k] - g_full[:, k])) / np.max(np.abs(g_full[:, k]))
+        assert d < 1e-7, (k, d)
+    P.close()
