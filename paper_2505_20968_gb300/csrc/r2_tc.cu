@@ -608,15 +608,17 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
       mbar_arrive(&ready[cb]);
     }
     // ---------------- epilogue: TMEM -> registers -> eps_bar
-    const bool ok = mbar_wait(done, 0, abort_flag, p.spin);
+    // warp-uniform: the TMEM loads and the shuffles below need the whole warp
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag, p.spin));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       const int q = warp & 3;                    // TMEM lane quarter of this warp
       const int par = (warp - 2) >> 2;           // kGenWarps / 4 warps per quarter split the 16-column groups
       const int r = q * 32 + lane;               // D row: Stokes column (output el = r / 4, i = r % 4)
+      const int si = lane & 3;                   // its Stokes index
       const bool live = r < 4 * E;
       const int o = live ? cout_dir[e0 + (r >> 2)] : 0;
-      float* dst = p.eb + (((size_t)iz * p.nO + o) * N) * 4 + (r & 3);
+      float* dst = p.eb + (((size_t)iz * p.nO + o) * N) * 4;
       for (int c0 = par * 16; c0 < NM; c0 += 16 * (kGenWarps / 4)) {
         uint32_t v[16];
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
@@ -626,12 +628,29 @@ __global__ void __launch_bounds__(kThreads, 1) r2_tc_kernel(Params p) {
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (live) {
+        // The 4 lanes of an output hold its 4 Stokes values for the 16 columns; a 4 x 4
+        // transpose per group of 4 columns (three exchanges) gives lane si the 4 Stokes
+        // values of column 4m + si, added with one vector reduction instead of four.
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = c0 + j;
-            if (n < N) atomicAdd(dst + (size_t)n * 4, __uint_as_float(v[j]));
-          }
+        for (int m = 0; m < 4; ++m) {
+          const float a0 = __uint_as_float(v[4 * m]), a1 = __uint_as_float(v[4 * m + 1]);
+          const float a2 = __uint_as_float(v[4 * m + 2]), a3 = __uint_as_float(v[4 * m + 3]);
+          auto pick = [&](int k) { return k == 0 ? a0 : (k == 1 ? a1 : (k == 2 ? a2 : a3)); };
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;   // Stokes 0..3 of column 4m + si
+          auto put = [&](int k, float x) {
+            if (k == 0) s0 = x;
+            else if (k == 1) s1 = x;
+            else if (k == 2) s2 = x;
+            else s3 = x;
+          };
+          put(si, pick(si));
+#pragma unroll
+          for (int x = 1; x < 4; ++x) put(si ^ x, __shfl_xor_sync(0xffffffffu, pick(si ^ x), x));
+          const int n = c0 + 4 * m + si;
+          if (live && n < N)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + (size_t)n * 4), "f"(s0),
+                         "f"(s1), "f"(s2), "f"(s3)
+                         : "memory");
         }
       }
     }

@@ -8,8 +8,9 @@ K step mixes the halves; every K step is one contiguous block of N x 64 bytes
 row's 64 bytes are permuted by the 64-byte shared-memory swizzle, written here
 in its own form (byte address bits [4:5] XOR bits [7:8]), which is the layout
 the MMA descriptors declare.  The split layout of BF16x3 contexts
-(tile_off_split: bf16 hi and lo planes in the same bytes) is checked the same
-way against the 32-byte swizzle."""
+(tile_off_split: bf16 hi and lo planes in the same bytes) and the hi-only layout
+of BF16x2 contexts (tile_off_hi: half the bytes) are checked the same way
+against the 32-byte swizzle."""
 import os
 import shutil
 import subprocess
@@ -47,6 +48,14 @@ int main() {
           const unsigned l2 = (unsigned)(n * 32 + kl * 2);
           const unsigned s2 = l2 ^ (((l2 >> 7) & 1u) << 4);
           if ((o2 - plane) * 2 != s2) { std::printf("split N=%d n=%d k=%d: swizzle\n", N, n, k); return 8; }
+        }
+        // hi plane alone (BF16x2): chunk kc a block of N x 32 bytes, same swizzle
+        const size_t oh = prd::tile_off_hi(n, k, N, ld);
+        const size_t hp = (size_t)kc * N * 16;
+        const unsigned l3 = (unsigned)(n * 32 + kl * 2);
+        if (oh < hp || oh >= hp + (size_t)N * 16 || (oh - hp) * 2 != (l3 ^ (((l3 >> 7) & 1u) << 4))) {
+          std::printf("hi N=%d n=%d k=%d\n", N, n, k);
+          return 10;
         }
       }
     if (((size_t)N * ld * 4) % 64 || ((size_t)N * 64) % 16) { std::printf("N=%d: alignment\n", N); return 4; }
