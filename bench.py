@@ -214,6 +214,40 @@ def useful_contraction_flops(P, n_t):
     return 16.0 * P.nz * n_t * P.nN ** 2 * C, C
 
 
+def batch_throughput(local, n=32):
+    """S12 beside the headline: n ragged Mg II-like instances (6-10 heights,
+    varied frequency grids and fields, FP32), solved to tol 1e-8 once as one
+    prd_solve_batch (lockstep rounds, one parent-graph launch per iteration)
+    and once one after another with prd_solve; solves/s of each (after one
+    untimed batch that captures every instance's Arnoldi step)."""
+    import torch
+    from paper_2505_20968_gb300 import inputs
+    from paper_2505_20968_gb300.binding import PRD, solve_batch
+    cfgs = [inputs.mgii(n_z=6 + (i % 5), n_core_each=5 + (i % 3), n_wing=4 + (i % 2), n_mu_half=2, n_chi=4,
+                        seed=500 + i) for i in range(n)]
+    Ps = [PRD(c, device=local) for c in cfgs]
+    unknowns = sum(P.n for P in Ps)
+    solve_batch(Ps, tol=1e-8, max_iter=600, restart=60)
+    launches0 = [P.graph_launches() for P in Ps]
+    torch.cuda.synchronize()
+    t0 = time.time()
+    _, infos = solve_batch(Ps, tol=1e-8, max_iter=600, restart=60)
+    torch.cuda.synchronize()
+    tb = time.time() - t0
+    rounds = sum(P.graph_launches() - k for P, k in zip(Ps, launches0))
+    t0 = time.time()
+    for P in Ps:
+        P.solve(tol=1e-8, max_iter=600, restart=60)
+    torch.cuda.synchronize()
+    ts = time.time() - t0
+    for P in Ps:
+        P.close()
+    return {"instances": n, "unknowns": unknowns, "tol": 1e-8, "precision": "fp32",
+            "batch_solves_per_s": n / tb, "sequential_solves_per_s": n / ts, "batch_seconds": tb,
+            "sequential_seconds": ts, "applies": sum(i["iters"] for i in infos),
+            "instance_steps_in_graph_rounds": rounds, "all_converged": all(i["rc"] == 0 for i in infos)}
+
+
 def max_over_ranks(ms, dist, device):
     """The job's time: the largest per-rank time over the ranks (any backend)."""
     if dist is None:
@@ -473,6 +507,10 @@ def main():
                            "solve": "not run: Sigma to ~1e-3 stalls the refinement (tests/test_gpu_parity.py)"}
         Pc.close()
 
+    batch = None
+    if rank == 0 and not args.no_solve and args.workload == "mgii":
+        batch = batch_throughput(local)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         pool = OraclePool(cfg)
@@ -488,7 +526,7 @@ def main():
                 "e2e": {"value": job_value(world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes},
                 "gpu_launches": 8 * args.steps, "roofline": roofline, "cpu_baseline": cpu, "solve": solve,
-                "contraction_modes": modes, "autotune": autotune}
+                "contraction_modes": modes, "autotune": autotune, "batch": batch}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

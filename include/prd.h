@@ -171,7 +171,9 @@ int prd_sizes(const prd_ctx* ctx, int* nz, int* n_omega, int* nnu, int* n_theta,
               int64_t* n);
 /* Copy the direction grid (mu, chi, weights; host arrays of length n_omega). */
 int prd_directions(const prd_ctx* ctx, double* mu, double* chi, double* w);
-/* Bytes of device memory the library holds after setup (tiles + tables). */
+/* Bytes of device memory the library holds: tiles and tables from setup, plus
+ * the solver workspace kept after the first prd_solve / prd_solve_adjoint
+ * (Krylov basis, device state) and the transposed operator's scratch. */
 int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes);
 /* Work of one R_II contraction (Eq. G summed over the tiles of every class,
  * Sect. 4): *flops = 2 x (real multiply-adds of Re(T Z) over all heights,

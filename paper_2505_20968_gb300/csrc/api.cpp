@@ -384,9 +384,10 @@ int prd_workspace_bytes(const prd_ctx* ctx, int64_t* bytes) {
                              &c->pc_lii, &c->pc_eta, &c->pc_delo, &c->gm_t, &c->dmu, &c->pc_s1, &c->pc_s2,
                              &c->pc_s3, &c->pc_s4, &c->pc_s5, &c->tc_err, &c->tc_work, &c->tiles64, &c->Y64, &c->r3w64, &c->r3in64,
                              &c->r3out64, &c->r3prof64, &c->r3ab64, &c->par, &c->eta_line, &c->cont_pw,
-                             &c->cont_sig};
+                             &c->cont_sig, &c->gm_w, &c->gk_V, &c->gk_r, &c->gk_w, &c->gk_cur, &c->gk_S};
   int64_t s = 0;
   for (auto* b : bufs) s += (int64_t)b->bytes;
+  for (const auto& b : c->adj) s += (int64_t)b.bytes;   // scratch of the transposed operator, once used
   *bytes = s;
   return PRD_OK;
 }
