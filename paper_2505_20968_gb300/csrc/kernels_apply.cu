@@ -55,7 +55,7 @@ __global__ void spline_M_kernel(const T* __restrict__ y, T* __restrict__ M, cons
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
-template <> struct V4<double> { using type = double4; };
+template <> struct V4<double> { using type = double4_16a; };
 
 // Evaluate the spline of every (z, Omega) row at the tabulated points; the
 // intensity component is multiplied by fI (nullable).
@@ -836,7 +836,7 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   stage_end(c, ST_S1, e0);
   // S5 (initialises eps_bar)
   stage_begin(c, ST_S5, &e0);
-  const int nuv = c->nu_st * c->nu_st, nq = nuv * c->nl_st;
+  const int nuv = c->nu_st * c->nu_st;
   double* J = J_ext ? J_ext : (double*)c->r3J.p;
   PRD_CUDA_TRY(c, cudaMemsetAsync(J, 0, (size_t)nz * nuv * 2 * sizeof(double), c->stream));
   launch_r3_J<T, A>(c, Ic, J, nO, tb);
@@ -845,12 +845,12 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
   // S3 + S4
   stage_begin(c, ST_S3, &e0);
   const int nchunk = (c->max_cout + kCW - 1) / kCW;
+  bool s3_done = false;   // the tensor-core or double-float contraction ran
   if constexpr (std::is_same<T, float>::value && std::is_same<A, float>::value) {
     if (c->use_tc && c->tc_ready && !t64) {
       int rc = r2_tc_launch(c, Ic, eb);
       if (rc) return rc;
-      stage_end(c, ST_S3, e0);
-      goto s6;
+      s3_done = true;
     }
   }
   if constexpr (std::is_same<T, double>::value && std::is_same<A, double>::value) {
@@ -860,19 +860,17 @@ static int sigma_T(Ctx* c, const A* x, A* eps, bool normalised, A* eb_ext = null
       r2_dd_kernel<<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
           (const double*)tb.tiles, (const double*)tb.Y, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N,
           c->npairs, tb.ld);
-      stage_end(c, ST_S3, e0);
-      goto s6;
+      s3_done = true;
     }
   }
-  {
-  const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
-  cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
-      (const T*)tb.tiles, (const T*)tb.Y, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs, tb.ld,
-      tb.tiled);
-  stage_end(c, ST_S3, e0);
+  if (!s3_done) {
+    const size_t smem = sizeof(A) * (size_t)kMB * 2 * kCW * 4 + sizeof(T) * (size_t)2 * N * (kMB + 1);
+    cudaFuncSetAttribute(r2_simt_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    r2_simt_kernel<T, A><<<dim3(nchunk, c->ncls, nz), 256, smem, c->stream>>>(
+        (const T*)tb.tiles, (const T*)tb.Y, Ic, (const int*)c->cls_dev.p, eb, c->ncls, c->ntile(), nO, N, c->npairs,
+        tb.ld, tb.tiled);
   }
-s6:
+  stage_end(c, ST_S3, e0);
   // S6
   stage_begin(c, ST_S6, &e0);
   spline_M_kernel<A><<<ceil_div(nz * nO * 4, 128), 128, 0, c->stream>>>(eb, Mb, sp, nz, nO, N);
@@ -932,7 +930,6 @@ int apply_sigma(Ctx* c, const void* x, void* eps, bool normalised) {
 }
 
 int apply_lambda(Ctx* c, const void* eps, void* out, const void* sub_from, bool boundary) {
-  const int nz = c->nz, nO = c->nO, N = c->nnu;
   const double* dmu = (const double*)c->dmu.p;
   cudaEvent_t e0;
   stage_begin(c, ST_S7, &e0);
@@ -1087,8 +1084,7 @@ __global__ void cast_kernel(const S* __restrict__ in, D* __restrict__ out, long 
 
 template <typename T, typename A>
 static int emergent_T(Ctx* c, const T* x, int nlos, const double* mus, const double* chis, T* out) {
-  const int nz = c->nz, nO = c->nO, N = c->nnu, nti = c->ntile(), nuv = c->nu_st * c->nu_st, nl = c->nl_st;
-  const int nq = nuv * nl;
+  const int nz = c->nz, nO = c->nO, N = c->nnu, nti = c->ntile(), nuv = c->nu_st * c->nu_st;
   const long long npt = (long long)nz * nO * N;
   const size_t tz = (size_t)nO * nti * N * c->ld() * sizeof(T);   // tiles of one height, all LOS classes
   DBuf Icx, Icw, Jx, Jw, tiles, Yd, rout, ktd, ethd, kidx, ttd, es_bar, ew_bar, es, ew, M, eps, lam, fac, dmu, clsd,
