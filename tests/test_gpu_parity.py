@@ -242,7 +242,7 @@ def test_tensor_core_contraction(name):
 
 @pytest.mark.parametrize("name", ["mgii", "hi", "hi_aa"])
 def test_bf16x3_contraction_and_solve(name):
-    """Split-BF16 products (PRD_FP32_BF16X3; the benchmark spec's precision pattern):
+    """Split-BF16 products (PRD_FP32_BF16X3, the compensated bf16 precision mode):
     Sigma within 1e-4 of each height's largest emissivity (each product
     hi*hi + hi*lo + lo*hi of bf16 halves leaves <= 3 * 2^-18 = 1.1e-5; the
     3xTF32 path measures ~3x its own per-product bound, so 1e-4 leaves room),
