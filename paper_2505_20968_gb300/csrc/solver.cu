@@ -14,14 +14,13 @@
 // The stopping test is the unpreconditioned relative residual ||b - A x|| /
 // ||b|| of Sect. 5.1, recomputed in FP64 before returning.
 #include <cmath>
-#include <condition_variable>
 #include <cstring>
 #include <algorithm>
 #include <map>
-#include <mutex>
 #include <vector>
 #include "prd_internal.h"
 #include "device_common.cuh"
+#include "lockstep.h"
 
 namespace prd {
 
@@ -296,23 +295,19 @@ void invalidate_graphs(Ctx* c) {
     }
 }
 
-// ---- lockstep rounds of prd_solve_batch
+// ---- lockstep rounds of prd_solve_batch (the round logic: lockstep.h)
+using BatchReq = std::pair<Ctx*, int>;       // (context, graph key) waiting in a round
 struct BatchRound {
-  std::mutex mu;
-  std::condition_variable cv;
-  int live = 0;                              // contexts still taking part
-  long long gen = 0;                         // rounds launched
-  std::vector<std::pair<Ctx*, int>> req;     // (context, graph key) waiting in this round
-  cudaError_t err = cudaSuccess;             // status of the last round
+  explicit BatchRound(int n) : ls(n) {}
+  Lockstep<BatchReq> ls;
   cudaStream_t stream = nullptr;             // the rounds' launch stream
   cudaEvent_t ev = nullptr;
-  std::map<std::vector<std::pair<Ctx*, int>>, cudaGraphExec_t> cache;   // by the set of children
+  std::map<std::vector<BatchReq>, cudaGraphExec_t> cache;   // by the set of children
   long long launches = 0;
 };
 
 BatchRound* batch_round_create(int n) {
-  BatchRound* b = new BatchRound;
-  b->live = n;
+  BatchRound* b = new BatchRound(n);
   if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
     batch_round_destroy(b);
@@ -329,11 +324,11 @@ void batch_round_destroy(BatchRound* b) {
   delete b;
 }
 
-// Launch the round for the waiting contexts (caller holds the lock): the
+// Launch the round for the waiting contexts (run under the round's lock): the
 // launch stream waits for each context's stream, one launch of the graph with
-// their steps as children, then every context's stream waits for the round.
-static cudaError_t batch_round_launch(BatchRound* b) {
-  std::vector<std::pair<Ctx*, int>> key = b->req;
+// their steps as children, then the host waits for it.
+static int batch_round_launch(BatchRound* b, const std::vector<BatchReq>& req) {
+  std::vector<BatchReq> key = req;
   std::sort(key.begin(), key.end());
   cudaError_t e = cudaSuccess;
   auto it = b->cache.find(key);
@@ -347,7 +342,7 @@ static cudaError_t batch_round_launch(BatchRound* b) {
     cudaGraphExec_t ex = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, pg, 0);
     if (pg) cudaGraphDestroy(pg);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return (int)e;
     it = b->cache.emplace(key, ex).first;
   }
   for (auto& r : key) {
@@ -360,38 +355,21 @@ static cudaError_t batch_round_launch(BatchRound* b) {
     ++b->launches;
     for (auto& r : key) ++r.first->gk_launches;
   }
-  return e;
+  return (int)e;
 }
 
 // A context's Arnoldi step inside a batch round: wait for the round (the last
 // context to arrive launches it) and return its status.
 static cudaError_t batch_round_step(BatchRound* b, Ctx* c, int key) {
-  std::unique_lock<std::mutex> lk(b->mu);
-  const long long g = b->gen;
-  b->req.emplace_back(c, key);
-  if ((int)b->req.size() == b->live) {
-    b->err = batch_round_launch(b);
-    b->req.clear();
-    ++b->gen;
-    b->cv.notify_all();
-    return b->err;
-  }
-  b->cv.wait(lk, [&] { return b->gen != g; });
-  return b->err;
+  return (cudaError_t)b->ls.arrive(BatchReq(c, key),
+                                   [b](const std::vector<BatchReq>& req) { return batch_round_launch(b, req); });
 }
 
 // A context stops taking part (its solve ended, or it runs its steps one by
 // one from now on); if everyone left is waiting, their round is launched.
 void batch_round_leave(BatchRound* b) {
   if (!b) return;
-  std::unique_lock<std::mutex> lk(b->mu);
-  --b->live;
-  if (!b->req.empty() && (int)b->req.size() == b->live) {
-    b->err = batch_round_launch(b);
-    b->req.clear();
-    ++b->gen;
-    b->cv.notify_all();
-  }
+  b->ls.leave([b](const std::vector<BatchReq>& req) { return batch_round_launch(b, req); });
 }
 
 // GMRES workspace of restart length m, kept by the context (the captured step
