@@ -19,6 +19,12 @@ PRD_OK = 0
 ERRORS = {-1: "PRD_E_ARG", -2: "PRD_E_STATE", -3: "PRD_E_CUDA", -4: "PRD_E_NOMEM", -5: "PRD_E_NOCONV",
           -6: "PRD_E_BREAKDOWN", -7: "PRD_E_NAN", -8: "PRD_E_TIMEOUT"}
 PRD_FP64, PRD_FP32, PRD_FP32_BF16X3, PRD_FP32_BF16X2 = 0, 1, 2, 3
+# prd_set_option ids and values (include/prd.h)
+PRD_OPT_TENSOR_CORES, PRD_OPT_PRECOND_SWEEPS, PRD_OPT_WAIT_POLLS, PRD_OPT_TEST_ZERO_OPERATOR = 1, 2, 3, 4
+PRD_OPT_REFINE_FLOOR, PRD_OPT_FORMAL_SOLVER, PRD_OPT_CONTRACTION, PRD_OPT_TILE_STAGES = 5, 6, 7, 8
+PRD_OPT_GRAPH, PRD_OPT_STAGED_SWEEP, PRD_OPT_GRAD_FULL_SETUP = 9, 10, 11
+PRD_CONTRACTION_TF32X3, PRD_CONTRACTION_BF16X3 = 0, 1
+PRD_DELO_LINEAR, PRD_DELOPAR = 0, 1
 
 
 class PrdError(RuntimeError):
@@ -268,22 +274,23 @@ class PRD:
         return out
 
     def set_tensor_cores(self, on=True):
-        self._check(lib().prd_set_option(self.h, 1, 1 if on else 0))
+        self._check(lib().prd_set_option(self.h, PRD_OPT_TENSOR_CORES, 1 if on else 0))
 
     def set_tile_stages(self, n):
         """Depth of the contraction's tile ring (0: the deepest that fits)."""
-        self._check(lib().prd_set_option(self.h, 8, int(n)))
+        self._check(lib().prd_set_option(self.h, PRD_OPT_TILE_STAGES, int(n)))
 
     def set_contraction(self, kind):
         """Split products of the tensor-core contraction: "tf32x3" or "bf16x3"."""
-        self._check(lib().prd_set_option(self.h, 7, {"tf32x3": 0, "bf16x3": 1}[kind]))
+        self._check(lib().prd_set_option(self.h, PRD_OPT_CONTRACTION,
+                                         {"tf32x3": PRD_CONTRACTION_TF32X3, "bf16x3": PRD_CONTRACTION_BF16X3}[kind]))
 
     def device_status(self):
         self._check(lib().prd_device_status(self.h))
 
     def set_graph(self, on):
         """Run each GMRES iteration as one CUDA-graph launch (default) or not."""
-        self._check(lib().prd_set_option(self.h, 9, 1 if on else 0))
+        self._check(lib().prd_set_option(self.h, PRD_OPT_GRAPH, 1 if on else 0))
 
     def graph_launches(self):
         """CUDA-graph launches of the GMRES step made by this context so far."""
