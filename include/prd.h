@@ -8,7 +8,7 @@
  * Omega = i_mu * N_chi + i_chi with mu ascending, frequencies ascending in the
  * reduced frequency u = (nu0 - nu)/dnu_D.  The library solves
  *     (Id - Lambda Sigma) I = Lambda eps_th + t                (Eq. linear_system)
- * with Lambda the DELO-linear formal solution (Sect. 3) and Sigma the
+ * with Lambda the DELO-linear (or DELOPAR) formal solution (Sect. 3) and Sigma the
  * comoving-frame R_II-AD + R_III scattering operator (Eqs. eps_sc_l,
  * RQIIKKp, RIIIQKKp, eps_sc_bar; Sect. 4; App. B, E).
  *
@@ -18,13 +18,13 @@
  *   - host arrays are read during the call and copied; the caller keeps them.
  *   - "device" pointers are caller-owned CUDA allocations on the ctx's device,
  *     contiguous, layout [z][Omega][nu][4], element type double for
- *     PRD_FP64 and float for PRD_FP32, starting on a whole Stokes point
+ *     PRD_FP64 and float for the FP32 precisions, starting on a whole Stokes point
  *     (address a multiple of 4 elements: 32 bytes in FP64, 16 in FP32;
  *     otherwise PRD_E_ARG, as the kernels move one point per access).  The
  *     library never frees them.
- *   - the library owns its workspace (cudaMalloc at prd_setup, or the
- *     caller's allocator of prd_set_allocator; freed at prd_destroy or at the
- *     next prd_setup).
+ *   - the library owns its workspace (cudaMalloc at prd_setup and at the
+ *     first solve, or the caller's allocator of prd_set_allocator; freed at
+ *     prd_destroy or at the next prd_setup).
  *   - work is issued on the ctx stream (prd_set_stream, default: the legacy
  *     stream) and is asynchronous, except prd_setup, prd_solve and calls that
  *     return host scalars, which synchronise the stream.
@@ -67,7 +67,9 @@ enum {
  * (half the bytes of FP32) and two products per element, hi(B)*hi(A) +
  * lo(B)*hi(A): the tile's rounding to bf16 (<= 2^-9 relative) is kept, so the
  * contraction is a ~1e-3-accurate inner operator; prd_solve's FP64 residuals
- * (FP64 table copy) still fix the solution's accuracy. */
+ * (FP64 table copy) still check the solution, and where the scattering
+ * amplifies that error by more than its inverse (the Mg II case) the
+ * refinement stalls and prd_solve returns PRD_E_NOCONV. */
 enum { PRD_FP64 = 0, PRD_FP32 = 1, PRD_FP32_BF16X3 = 2, PRD_FP32_BF16X2 = 3 };
 enum { PRD_TWO_LEVEL = 0, PRD_TWO_TERM = 1 };
 enum { PRD_GRID_LAMBDA = 0, PRD_GRID_X = 1 };
